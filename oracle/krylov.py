@@ -1,0 +1,249 @@
+"""k-truncated Arnoldi, Householder QR, sGMRES (Algorithm 1) and GMRES.
+
+Test infrastructure only (see oracle/__init__.py).
+
+Everything is float64.  ``A`` is any object with ``A @ x`` (a scipy sparse
+matrix or a dense array).  ``sketch`` is a callable mapping an n-vector or an
+n x c array to its s-row sketch (oracle.sketch.*).
+"""
+import numpy as np
+
+
+# ---------------------------------------------------------------------------
+# Basis generation: §1.2.2 eq. (partorth), Algorithm 1 (truncated Arnoldi
+# loop, "double Gram-Schmidt" implementation note), §4.2.
+# ---------------------------------------------------------------------------
+def trunc_arnoldi(A, r, d, k, passes=2, breakdown=1e-13):
+    """Basis B = [b_1..b_d] and reduced matrix AB = [m_1..m_d].
+
+    b_1 = r/||r||, m_1 = A b_1; for j = 2..d
+        w_j = (I - b_{j-1}b_{j-1}^T - ... - b_{j-k}b_{j-k}^T) m_{j-1}
+    with b_{-i} = 0 (only existing vectors), applied as ``passes`` classical
+    Gram-Schmidt passes against the same vectors (2 = double Gram-Schmidt);
+    b_j = w_j/||w_j||, m_j = A b_j.
+
+    If ||w_j|| <= breakdown*||m_{j-1}||, A b_{j-1} lies (numerically) in the
+    span of the basis: the Krylov space is invariant and the basis stops at
+    d_used = j-1 columns.
+
+    Returns B (n x d_used), M = AB (n x d_used), Hc (d_used+1 x d_used) with
+    m_j = sum_i Hc[i, j] b_i (the truncated Hessenberg coefficients), d_used.
+    """
+    n = r.shape[0]
+    B = np.zeros((n, d))
+    M = np.zeros((n, d))
+    Hc = np.zeros((d + 1, d))
+    beta = np.linalg.norm(r)
+    B[:, 0] = r / beta
+    M[:, 0] = A @ B[:, 0]
+    d_used = d
+    for j in range(1, d):
+        lo = max(0, j - k)
+        W = B[:, lo:j]
+        w = M[:, j - 1].copy()
+        h = np.zeros(j - lo)
+        for _ in range(passes):
+            c = W.T @ w
+            w = w - W @ c
+            h += c
+        nu = np.linalg.norm(w)
+        if nu <= breakdown * np.linalg.norm(M[:, j - 1]):
+            d_used = j
+            break
+        Hc[lo:j, j - 1] = h
+        Hc[j, j - 1] = nu
+        B[:, j] = w / nu
+        M[:, j] = A @ B[:, j]
+    return B[:, :d_used], M[:, :d_used], Hc[: d_used + 1, :d_used], d_used
+
+
+# ---------------------------------------------------------------------------
+# Dense Householder QR and the sketched least-squares solve: §3.3 eqs.
+# (sgmres-yhat), (sgmres-rhat); Algorithm 1 (QR, triangular substitution).
+# ---------------------------------------------------------------------------
+def householder_qr(C):
+    """Thin QR C = U T by Householder reflectors (no pivoting).
+
+    Reflector j maps R[j:, j] to alpha e_1 with alpha = -sign(x_0)||x||.
+    Returns (V, T): V[j] the unit reflector vector acting on rows j.., T the
+    d x d upper triangle.
+    """
+    R = np.array(C, dtype=np.float64, copy=True)
+    s, d = R.shape
+    V = []
+    for j in range(d):
+        x = R[j:, j]
+        nx = np.linalg.norm(x)
+        alpha = -nx if x[0] >= 0 else nx
+        v = x.copy()
+        v[0] -= alpha
+        nv = np.linalg.norm(v)
+        if nv == 0.0:
+            V.append(np.zeros_like(v))
+            continue
+        v /= nv
+        R[j:, j:] -= 2.0 * np.outer(v, v @ R[j:, j:])
+        V.append(v)
+    return V, np.triu(R[:d, :d])
+
+
+def apply_qt(V, g):
+    """Q^T g for the reflectors of householder_qr (all s entries)."""
+    z = np.array(g, dtype=np.float64, copy=True)
+    for j, v in enumerate(V):
+        z[j:] -= 2.0 * v * (v @ z[j:])
+    return z
+
+
+def form_u(V, s):
+    """The s x d orthonormal factor U = H_1 ... H_d [I; 0]."""
+    d = len(V)
+    U = np.zeros((s, d))
+    U[:d, :d] = np.eye(d)
+    for j in reversed(range(d)):
+        v = V[j]
+        U[j:, :] -= 2.0 * np.outer(v, v @ U[j:, :])
+    return U
+
+
+def back_substitute(T, z):
+    """Solve T y = z for upper-triangular T by substitution."""
+    d = T.shape[0]
+    y = np.zeros(d)
+    for i in reversed(range(d)):
+        y[i] = (z[i] - T[i, i + 1:] @ y[i + 1:]) / T[i, i]
+    return y
+
+
+def cond2(T):
+    sv = np.linalg.svd(T, compute_uv=False)
+    return np.inf if sv[-1] == 0 else sv[0] / sv[-1]
+
+
+def sketched_ls(C, g, stab_tol=np.inf):
+    """min ||C y - g|| via C = U T: y = T^{-1}(U^T g), rhat = ||(I-UU^T)g||.
+
+    §3.3 eqs. (sgmres-yhat), (sgmres-rhat).  If kappa_2(T) > stab_tol the
+    solve keeps only the longest leading block of columns whose triangle has
+    kappa_2 <= stab_tol (§5.3: restart from the residual of the last
+    acceptable basis; kappa_2 of a leading block is non-decreasing in its
+    width, so the block is found by bisection).
+    Returns y (length of C's columns, zero-padded), rhat, kappa_2(T), width.
+    """
+    s, d = C.shape
+    V, T = householder_qr(C)
+    z = apply_qt(V, g)
+    kappa = cond2(T)
+    width = d
+    if kappa > stab_tol:
+        lo, hi = 0, d  # cond(T[:lo,:lo]) <= tol < cond(T[:hi,:hi])
+        while hi - lo > 1:
+            mid = (lo + hi) // 2
+            if cond2(T[:mid, :mid]) <= stab_tol:
+                lo = mid
+            else:
+                hi = mid
+        width = max(lo, 1)
+    y = np.zeros(d)
+    y[:width] = back_substitute(T[:width, :width], z[:width])
+    rhat = np.sqrt(np.sum(z[width:] ** 2))
+    return y, rhat, kappa, width
+
+
+# ---------------------------------------------------------------------------
+# sGMRES: Algorithm 1 with the solution built from B (§3.2 eq. (sgmres),
+# §3.3: x-hat = x_0 + B y-hat), restarted as in §3.5.
+# ---------------------------------------------------------------------------
+def sgmres_cycle(A, f, x, d, k, sketch, passes=2, stab_tol=1e14, breakdown=1e-13):
+    """One cycle of Algorithm 1 from the current iterate x."""
+    r = f - A @ x
+    g = sketch(r)
+    B, M, _, d_used = trunc_arnoldi(A, r, d, k, passes=passes, breakdown=breakdown)
+    C = sketch(M)
+    y, rhat, kappa, width = sketched_ls(C, g, stab_tol)
+    x_new = x + B @ y
+    return x_new, dict(rhat=rhat, kappa=kappa, d_used=d_used, width=width, r0norm=np.linalg.norm(r))
+
+
+def sgmres(A, f, x0, d, k, sketch, tol, maxit=10000, passes=2, stab_tol=1e14, breakdown=1e-13):
+    """Restarted sGMRES (§3.5) until ||f - A x||/||f|| <= tol or maxit cycles.
+
+    Returns x, relres history (one entry per cycle, after the cycle), infos.
+    """
+    x = np.array(x0, dtype=np.float64, copy=True)
+    fn = np.linalg.norm(f)
+    hist = []
+    infos = []
+    rel = np.linalg.norm(f - A @ x) / fn
+    cycles = 0
+    while rel > tol and cycles < maxit:
+        x, info = sgmres_cycle(A, f, x, d, k, sketch, passes, stab_tol, breakdown)
+        rel = np.linalg.norm(f - A @ x) / fn
+        hist.append(rel)
+        infos.append(info)
+        cycles += 1
+    return x, hist, infos
+
+
+# ---------------------------------------------------------------------------
+# GMRES with the Householder Arnoldi process (§3.1, §4.2; Walker 1988): the
+# classic O(nd^2) method sGMRES is compared with.
+# ---------------------------------------------------------------------------
+def _reflector(x):
+    nx = np.linalg.norm(x)
+    alpha = -nx if x[0] >= 0 else nx
+    v = x.copy()
+    v[0] -= alpha
+    nv = np.linalg.norm(v)
+    return (v / nv if nv > 0 else v), alpha
+
+
+def gmres_householder(A, f, x0, d):
+    """d steps of GMRES from x0; returns x_d and ||f - A x_d||.
+
+    Householder Arnoldi: P_1 r_0 = beta e_1; for j = 1..d, q_j = P_1..P_j e_j,
+    z = P_j..P_1 A q_j, P_{j+1} zeroes z below entry j+1, and column j of the
+    (d+1) x d Hessenberg H is the top j+1 entries of P_{j+1} z.  Then
+    y = argmin ||beta e_1 - H y|| and x_d = x_0 + [q_1..q_d] y.
+    """
+    f = np.asarray(f, dtype=np.float64)
+    n = f.shape[0]
+    x0 = np.asarray(x0, dtype=np.float64)
+    r0 = f - A @ x0
+    refl = []  # (offset, v)
+
+    def apply_p(z, upto):  # P_upto ... P_1 z
+        z = z.copy()
+        for off, v in refl[:upto]:
+            z[off:] -= 2.0 * v * (v @ z[off:])
+        return z
+
+    def apply_p_rev(z, upto):  # P_1 ... P_upto z
+        z = z.copy()
+        for off, v in reversed(refl[:upto]):
+            z[off:] -= 2.0 * v * (v @ z[off:])
+        return z
+
+    v, beta = _reflector(r0)
+    refl.append((0, v))
+    m = min(d, n)
+    H = np.zeros((m + 1, m))
+    Q = np.zeros((n, m))
+    for j in range(m):
+        e = np.zeros(n)
+        e[j] = 1.0
+        q = apply_p_rev(e, j + 1)
+        Q[:, j] = q
+        z = apply_p(A @ q, j + 1)
+        if j + 1 < n:
+            v, alpha = _reflector(z[j + 1:])
+            refl.append((j + 1, v))
+            z[j + 1:] = 0.0
+            z[j + 1] = alpha
+        top = min(j + 2, n)
+        H[:top, j] = z[:top]
+    rhs = np.zeros(m + 1)
+    rhs[0] = beta
+    y = np.linalg.lstsq(H, rhs, rcond=None)[0]
+    x = x0 + Q @ y
+    return x, np.linalg.norm(f - A @ x)
