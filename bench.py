@@ -1,0 +1,348 @@
+"""Benchmark: sGMRES solves/s to 1e-6 relative residual on one GB300.
+
+Workload ("scale"): 1024 x 1024 convection-diffusion, Pe = 50, b ~ N(0,1)
+seed 0, x0 = 0; basis d = 300 by 2-truncated Arnoldi; sparse sign sketch
+s = 600, zeta = 12, seed 7; restarted until ||b - A x|| / ||b|| <= 1e-6.
+One step = one complete solve.  The chosen form stores the basis and runs
+the SpMV in FP32 with the FP64 residual, update and 600 x 300 QR (restarts
+act as iterative refinement); the plain FP64 form is timed beside it.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--form f32|bf16|f64]
+    python bench.py --impl reference ...   # the CPU oracle on this host
+
+Multi-GPU: one process per GPU (torchrun); each rank solves its own copy of
+the workload (independent problems, no data-path collective: weak scaling);
+value = solves of all ranks / max-over-ranks time.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "sGMRES solves/s to 1e-6 rel. residual (chosen vs plain form); sketch GB/s vs HBM"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            p = json.load(fh)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        try:
+            rows = [r.split(",") for r in open(self.path).read().strip().splitlines() if r.strip()]
+            os.unlink(self.path)
+        except Exception:
+            return out
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [c.strip() for c in r]
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except Exception:
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if sm:
+            out = {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                   "samples": len(sm)}
+        return out
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _problem(dev):
+    import torch
+    import synth
+    W = synth.WORKLOADS["scale"]
+    N = W["N"]
+    coef = synth.conv_diff_coef(N, W["Pe"])
+    f = synth.randn(W["b_seed"], N * N)
+    return W, N, coef, f, torch.tensor(f, device=dev)
+
+
+def _oracle_cycle_seconds(d_sample=None):
+    """Time one oracle restart cycle of the scale workload in a child process.
+
+    The child pins numpy/BLAS to one thread.  d_sample < d runs the first
+    d_sample Arnoldi steps only (the caller scales the time by d/d_sample).
+    """
+    code = r"""
+import json, sys, time
+sys.path.insert(0, %r)
+import numpy as np
+import synth
+from oracle import krylov, operators, sketch
+W = synth.WORKLOADS["scale"]; N = W["N"]
+d = %s or W["d"]
+A = operators.stencil5_matrix(N, N, synth.conv_diff_coef(N, W["Pe"]))
+f = synth.randn(W["b_seed"], N * N)
+t0 = time.time()
+S = sketch.sparse_sign_matrix(7, N * N, W["s"], W["zeta"])
+t1 = time.time()
+x, info = krylov.sgmres_cycle(A, f, np.zeros(N * N), d, W["k"], lambda M: S @ M)
+t2 = time.time()
+print(json.dumps({"plan_s": t1 - t0, "cycle_s": t2 - t1, "d": d}))
+""" % (ROOT, repr(d_sample))
+    env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=900)
+    if r.returncode != 0:
+        raise RuntimeError("oracle sample failed: " + r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def _oracle_cycles():
+    try:
+        with open(os.path.join(ROOT, "tests", "golden", "scale_oracle.json")) as fh:
+            return int(json.load(fh)["cycles"])
+    except Exception:
+        return None
+
+
+def run_reference(args):
+    ws, rank, local = _dist()
+    if rank != 0:
+        return 0
+    d_sample = 30
+    W_d = 300
+    cycles = _oracle_cycles()
+    samples = []
+    for i in range(args.warmup + args.steps):
+        r = _oracle_cycle_seconds(d_sample)
+        if i >= args.warmup:
+            samples.append(r["cycle_s"] * W_d / d_sample)
+    t_cycle = statistics.median(samples)
+    ncyc = cycles if cycles else 1
+    value = 1.0 / (ncyc * t_cycle)
+    out = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / value, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "scale: 1024x1024 convection-diffusion Pe=50, d=300, k=2, s=600, zeta=12, tol=1e-6",
+                   "form": "FP64 CPU oracle (numpy/scipy, one thread)"},
+        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                         "sample": "per step: first %d of %d Arnoldi steps of one oracle restart cycle (basis, "
+                                   "sketch, QR, update), time x %d/%d = one cycle; x %d oracle cycles per solve "
+                                   "(tests/golden/scale_oracle.json)" % (d_sample, W_d, W_d, d_sample, ncyc)},
+        "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out))
+    return 0
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    import paper_2111_00113_gb300 as skg
+
+    W, N, coef, f, b = _problem(dev)
+    A = skg.Op.stencil5(N, N, coef)
+    form = {"f32": torch.float32, "bf16": torch.bfloat16, "f64": torch.float64}[args.form]
+    kw = dict(zeta=W["zeta"], seed=7, basis=form, sketch=args.sketch)
+    x = torch.zeros_like(b)
+
+    def solve(basis=form):
+        x.zero_()
+        xx, info = skg.sgmres_solve(A, b, W["d"], W["k"], W["s"], W["tol"], x0=x, **dict(kw, basis=basis))
+        return xx, info
+
+    for _ in range(args.warmup):
+        xx, info = solve()
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    barrier()
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    infos = []
+    e0.record(stream)
+    for _ in range(args.steps):
+        xx, info = solve()
+        infos.append(info)
+    e1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    t_ms = e0.elapsed_time(e1)
+    if ws > 1:
+        tt = torch.tensor([t_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_ms = float(tt.item())
+    ms_per_step = t_ms / args.steps
+    value = ws * args.steps / (t_ms / 1000.0)
+    # converged solves only count
+    ok = all(i["status"] == 0 and i["relres"] <= W["tol"] for i in infos)
+
+    # plain FP64 form beside it (same workload)
+    plain = None
+    if args.form != "f64" and not args.no_plain:
+        solve(torch.float64)
+        barrier()
+        p0 = time.perf_counter()
+        e0.record(stream)
+        pinfos = [solve(torch.float64)[1] for _ in range(args.plain_steps)]
+        e1.record(stream)
+        barrier()
+        pms = e0.elapsed_time(e1) / args.plain_steps
+        plain = {"value": 1000.0 / pms, "ms_per_step": pms, "cycles": pinfos[-1]["cycles"],
+                 "relres": pinfos[-1]["relres"], "phases_ms": [round(v, 3) for v in pinfos[-1]["ms"]]}
+
+    # end to end through the public API with host buffers: pinned b -> device,
+    # solve, x -> pinned host, every step
+    hb = torch.tensor(f, dtype=torch.float64).pin_memory()
+    hx = torch.empty_like(hb).pin_memory()
+    db = torch.empty_like(b)
+    barrier()
+    e0.record(stream)
+    for _ in range(args.steps):
+        db.copy_(hb, non_blocking=True)
+        x.zero_()
+        xx, info = skg.sgmres_solve(A, db, W["d"], W["k"], W["s"], W["tol"], x0=x, **kw)
+        hx.copy_(xx, non_blocking=True)
+    e1.record(stream)
+    barrier()
+    e2e_ms = e0.elapsed_time(e1)
+    if ws > 1:
+        tt = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_ms = float(tt.item())
+    e2e = {"value": ws * args.steps / (e2e_ms / 1000.0), "unit": "solves/s",
+           "h2d_bytes_per_step": hb.numel() * hb.element_size(),
+           "d2h_bytes_per_step": hx.numel() * hx.element_size()}
+
+    last = infos[-1]
+    cycles = last["cycles"]
+    n = N * N
+    esz = {"f32": 4, "bf16": 2, "f64": 8}[args.form]
+    d, k, s = W["d"], W["k"], W["s"]
+    peak, peak_kind = _peaks()
+    # Roofline of the dominant kernel family, the truncated-Arnoldi passes:
+    # per Arnoldi step the form pass reads b_j and the k-1 older window
+    # vectors and writes b_{j+1}; each of the two dot passes reads the k
+    # window vectors: (3k+1) vectors of n elements per step.
+    basis_ms = sum(i["ms"][1] for i in infos) / args.steps / cycles
+    basis_bytes = (3 * k + 1) * esz * n * d
+    achieved = basis_bytes / (basis_ms / 1000.0) / 1e9
+    roofline = {"kernel": "truncated-Arnoldi passes (form_kernel, dots_kernel x2 per step)", "bound": "hbm",
+                "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                "traffic": None, "peak_source": peak_kind,
+                "algorithmic_bytes_per_cycle": basis_bytes}
+    sketch_ms = sum(i["ms"][2] for i in infos) / args.steps / cycles
+    sketch_bytes = esz * n * (d + 1) + 8 * n
+    phases = [round(sum(i["ms"][q] for i in infos) / args.steps, 3) for q in range(6)]
+
+    out = {
+        "metric": METRIC, "value": round(value, 4), "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_per_step, 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": {"f32": "f32", "bf16": "bf16", "f64": "f64"}[args.form] + "+f64",
+        "data": "synthetic",
+        "config": {"workload": "scale: 1024x1024 convection-diffusion Pe=50, b~N(0,1) seed 0, d=300, k=2, "
+                               "s=600, zeta=12, tol=1e-6",
+                   "form": "%s basis/SpMV, FP64 residual/update/QR" % args.form.upper(), "sketch": args.sketch,
+                   "l2": "inputs larger than L2 (basis %.2f GB per cycle)" % (esz * n * (d + 1) / 1e9),
+                   "parallelism": "replicas" if ws > 1 else "single GPU"},
+        "converged": ok, "cycles": cycles, "relres": last["relres"],
+        "phases_ms_per_step": dict(zip(["residual", "basis", "sketch", "small_solve", "update", "total"], phases)),
+        "sketch_gbs": round(sketch_bytes / (sketch_ms / 1000.0) / 1e9, 1),
+        "plain": plain,
+        "roofline": roofline,
+        "e2e": e2e,
+        "clocks": clk,
+        "gpu_launches": int(sum(i["launches"] for i in infos)),
+    }
+    if rank == 0 and ws == 1 and not args.no_baseline:
+        try:
+            r = _oracle_cycle_seconds(None)
+            ncyc = _oracle_cycles() or (plain["cycles"] if plain else cycles)
+            v = 1.0 / (ncyc * r["cycle_s"])
+            out["cpu_baseline"] = {"value": v, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                                   "sample": "one full FP64 oracle restart cycle of this workload (%.1f s, one "
+                                             "thread) x %d oracle cycles per solve" % (r["cycle_s"], ncyc)}
+        except Exception as e:  # report, do not hide
+            out["cpu_baseline"] = {"value": None, "error": str(e)[:300]}
+    if rank == 0:
+        print(json.dumps(out))
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--form", default="f32", choices=["f32", "bf16", "f64"])
+    ap.add_argument("--sketch", default="sparse", choices=["sparse", "srht"])
+    ap.add_argument("--plain-steps", type=int, default=2)
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,184 @@
+/*
+ * sk.h -- C ABI of the GB300 (sm_103a) sketched-Krylov library (libsk.so).
+ *
+ * Sketched GMRES and sketched Rayleigh-Ritz after Nakatsukasa & Tropp,
+ * "Fast & Accurate Randomized Algorithms for Linear Systems and Eigenvalue
+ * Problems".  Section/equation/algorithm references below are to that paper.
+ *
+ * Conventions for every call:
+ *   - Vectors and matrices are DEVICE pointers (CUDA global memory) unless a
+ *     parameter says "host".  The caller owns them; the library never frees
+ *     or retains them past the call, except borrowed operator arrays (below).
+ *   - Matrices are column-major with an explicit leading dimension.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Calls are asynchronous with respect to the host unless stated
+ *     otherwise; calls that return scalar diagnostics (info structs, d_used,
+ *     nconv) synchronise the stream before returning.
+ *   - Every call returns an sk_status and never aborts or throws across the
+ *     ABI.  Arguments are validated before any launch; on SK_EINVAL nothing
+ *     was launched.  sk_last_error() gives a thread-local message.
+ *   - Workspace is allocated internally with stream-ordered cudaMallocAsync
+ *     and released before the call returns (SK_ENOMEM if that fails).
+ */
+#ifndef SK_H
+#define SK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SK_OK = 0,
+  SK_EINVAL = 1,     /* invalid argument (sizes, null pointers, unsupported combination) */
+  SK_ENOMEM = 2,     /* device workspace allocation failed */
+  SK_ECUDA = 3,      /* a CUDA runtime call or kernel launch failed */
+  SK_ENAN = 4,       /* NaN/Inf met in an input or a reduction */
+  SK_ENOCONV = 5,    /* maxit cycles without reaching tol; best x and info are still written */
+  SK_EILLCOND = 6,   /* kappa(T) > stab_tol could not be cured by truncation */
+  SK_ETIMEOUT = 7,   /* reserved: a bounded device-side wait gave up */
+  SK_EHASH = 8       /* sketch hash found no distinct row in 16 attempts (s too small for zeta) */
+} sk_status;
+
+typedef enum { SK_F64 = 0, SK_F32 = 1, SK_BF16 = 2 } sk_dtype;
+typedef enum { SK_SPARSE_SIGN = 0, SK_SRHT = 1 } sk_sketch_kind;
+
+/* ------------------------------------------------------------------------
+ * Operators.  "All algorithms in this paper access the matrix via products
+ * x -> Ax" (§1.2).  Grid operators use nx x ny cells, unknown (ix, iy) at
+ * index iy*nx + ix, neighbours E=(ix+1,iy) W=(ix-1,iy) N=(ix,iy+1)
+ * S=(ix,iy-1), Dirichlet zero outside.  Arrays passed to constructors are
+ * BORROWED: the caller keeps them alive and unchanged while the op exists.
+ * ------------------------------------------------------------------------ */
+typedef struct sk_op sk_op;
+
+/* (Au)_P = c[0] u_P + c[1] u_E + c[2] u_W + c[3] u_N + c[4] u_S + shift_P u_P.
+ * coef: host array of 5 doubles.  shift: device, nx*ny doubles, or NULL. */
+sk_status sk_op_stencil5(sk_op** op, int nx, int ny, const double* coef, const double* shift);
+
+/* -div(theta grad u), h^2-scaled: (Au)_P = sum_faces theta_f (u_P - u_Q),
+ * theta_f = (theta_P + theta_Q)/2 inside, theta_P on boundary faces.
+ * theta: device, nx*ny doubles (> 0). Symmetric positive definite. */
+sk_status sk_op_diffusion_var(sk_op** op, int nx, int ny, const double* theta);
+
+/* General sparse A in CSR (0-based, int32 indices), FP64 values, device. */
+sk_status sk_op_csr(sk_op** op, int64_t n, int64_t nnz, const int32_t* rowptr,
+                    const int32_t* colind, const double* val);
+
+/* A^T as a new op (stencil: E<->W and N<->S swapped; diffusion: itself).
+ * CSR ops return SK_EINVAL. The new op borrows the same arrays. */
+sk_status sk_op_transpose(const sk_op* op, sk_op** opT);
+
+/* y = A x in FP64 (x, y: device, n doubles; must not alias). */
+sk_status sk_op_apply(const sk_op* op, const double* x, double* y, void* stream);
+
+int64_t sk_op_n(const sk_op* op);
+void sk_op_destroy(sk_op* op);
+
+/* ------------------------------------------------------------------------
+ * Sketches (§2.3).  Sparse sign map (§2.3.2, eq. (sparse-map)): column i of
+ * S has zeta entries +-1/sqrt(zeta) in distinct rows chosen by the counter
+ * hash H1(seed, i, slot, attempt) (SplitMix64 finalizer of
+ * seed*0x9E3779B97F4A7C15 xor (i<<8|slot<<4|attempt); row = (lo32*s)>>32,
+ * sign = bit 63).  SRHT (§2.3.1, eq. (SRFT) with Walsh-Hadamard for the DFT):
+ * S = sqrt(n_p/s) D H E, n_p = 2^ceil(log2 n), E_i = sign of H1(seed,i,15,0),
+ * D = s distinct rows from a partial Fisher-Yates shuffle driven by
+ * H1(seed, q, 14, 0).  Output row q of an SRHT sketch is Hadamard row D[q].
+ * ------------------------------------------------------------------------ */
+typedef struct {
+  sk_sketch_kind kind;
+  int64_t n;      /* columns of S = rows of the data */
+  int s;          /* embedding dimension (rows of S), >= 1 */
+  int zeta;       /* nonzeros per column (sparse sign); 0 = ceil(2 ln(1+s/2)); 1..14 */
+  uint64_t seed;
+} sk_sketch;
+
+/* SB = S * B.  B: device, n x ncols, column-major, leading dimension ldb >= n,
+ * element type `dtype`.  SB: device, s x ncols FP64, leading dimension s.
+ * FP64 input is accumulated in FP64; FP32/BF16 input in FP32 within a chunk
+ * of rows, compensated (Kahan) FP32 across chunks, then FP64 across CTAs. */
+sk_status sketch_apply(const sk_sketch* S, const void* B, int64_t ldb, int ncols,
+                       sk_dtype dtype, double* SB, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Solver options and diagnostics.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+  sk_sketch_kind sketch;   /* default SK_SPARSE_SIGN */
+  int zeta;                /* 0 = ceil(2 ln(1+d)) (§2.3.2) */
+  uint64_t seed;           /* sketch seed, default 7 */
+  double stab_tol;         /* kappa(T) threshold (§3.4, §5.3); <= 0 = 1e14 (F64), 2e6 (F32), 1e2 (BF16) */
+  int maxit;               /* restart cycles, default 10000 */
+  sk_dtype basis;          /* basis storage and SpMV precision, default SK_F64 */
+  int cgs_passes;          /* Gram-Schmidt passes, 1 or 2 (default 2: "double Gram-Schmidt") */
+  double tau;              /* sRR convergence tolerance for nconv (default 1e-8) */
+  int symmetric;           /* sRR: keep real parts of lambda and x (§6.8) */
+  double breakdown;        /* ||w_j|| <= breakdown*||A b_{j-1}|| ends the basis; <=0 = 1e-13 (F64) / 1e-6 */
+  int use_graph;           /* capture the basis loop in a CUDA graph (default 1) */
+} sk_opts;
+
+void sk_opts_default(sk_opts* o);
+
+typedef struct {
+  int cycles;          /* restart cycles run */
+  int matvecs;         /* products with A (basis + residuals) */
+  int d_used;          /* basis columns in the last cycle */
+  int width;           /* columns kept by the kappa truncation in the last cycle */
+  double relres;       /* final ||b - A x|| / ||b|| (FP64) */
+  double rhat_est;     /* last sketched residual estimate (eq. (sgmres-rhat)) */
+  double kappa_T_max;  /* largest kappa(T) estimate over cycles */
+  float ms[6];         /* device ms summed over cycles (CUDA events on the call's stream):
+                          [0] residual r = b - A x, [1] basis, [2] sketches (g = S r, S B),
+                          [3] small dense solve, [4] solution update, [5] whole call */
+  long long launches;  /* CUDA kernels launched by the call */
+} sk_info;
+
+/* ------------------------------------------------------------------------
+ * k-truncated Arnoldi basis (§1.2.2 eq. (partorth); Algorithm 1 loop with
+ * double Gram-Schmidt).  b_1 = r0/||r0||; for j >= 2 w_j is A b_{j-1}
+ * orthogonalised against b_{j-1..j-k} in `cgs_passes` classical passes.
+ *   A: op; r0: device n doubles; d >= 1; 1 <= k <= d.
+ *   B: device, n x (d+1) of `basis_dtype`, ld = n (column d+1 = b_{d+1},
+ *      needed for the Arnoldi relation AB = B_{d+1} Hbar).
+ *   Hbar: device (d+1) x d FP64 col-major (ld d+1) or NULL: A b_j =
+ *      sum_i Hbar[i,j] b_i (k+1 nonzeros per column).
+ *   S, SB, SAB: optional (NULL) sketch and device outputs s x d FP64:
+ *      SB = S [b_1..b_d], SAB = S [A b_1 .. A b_d].
+ *   d_used: host int, columns actually built (< d on breakdown).
+ * ------------------------------------------------------------------------ */
+sk_status trunc_arnoldi_basis(const sk_op* A, const double* r0, int d, int k, sk_dtype basis_dtype,
+                              void* B, double* Hbar, const sk_sketch* S, double* SB, double* SAB,
+                              const sk_opts* opts, int* d_used, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Restarted sGMRES (Algorithm 1, §3.3, §3.5): solve A x = b.
+ *   b: device n doubles; x: device n doubles, in: initial guess, out: solution.
+ *   d: basis size; k: truncation; s: sketch rows (>= d+1); tol: target
+ *   ||b - A x||/||b|| (FP64, checked after every cycle).
+ *   opts: NULL = defaults; info: host or NULL.
+ * Returns SK_OK (converged), SK_ENOCONV (best x written), or an error.
+ * ------------------------------------------------------------------------ */
+sk_status sgmres_solve(const sk_op* A, const double* b, double* x, int d, int k, int s, double tol,
+                       const sk_opts* opts, sk_info* info, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Sketched Rayleigh-Ritz (Algorithm 2, §6.3-§6.4): nev eigenpairs of A with
+ * largest real part from a k-truncated Arnoldi basis of dimension d started
+ * at w1 (device n doubles; Algorithm 2 draws it as randn).
+ *   lam_re, lam_im, rhat: host arrays of nev doubles (rhat = eq.
+ *   (srr-resid-est)).  X_re, X_im: device n x nev FP64 (ld n), unit-norm
+ *   Ritz vectors B y_i (X_im may be NULL).  nconv: host, count with rhat <= tau.
+ * ------------------------------------------------------------------------ */
+sk_status srr_eigs(const sk_op* A, const double* w1, int nev, int d, int k, int s, const sk_opts* opts,
+                   double* lam_re, double* lam_im, double* X_re, double* X_im, double* rhat,
+                   int* nconv, sk_info* info, void* stream);
+
+const char* sk_last_error(void);
+const char* sk_status_string(sk_status st);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SK_H */

@@ -1,0 +1,206 @@
+"""GB300 (sm_103a) sketched GMRES and sketched Rayleigh-Ritz.
+
+Thin Python binding over the C ABI of libsk.so (include/sk.h): the functions
+below marshal torch CUDA tensors into device pointers and call the library,
+whose CUDA kernels do all the work.  PyTorch provides device memory and the
+current stream only.  There is no CPU path: without the built library or a
+GPU these functions raise.
+
+Layout: a matrix argument such as the basis B (n x c) is column-major.  A
+torch tensor qualifies if ``B.stride(0) == 1`` (e.g. ``torch.empty(c, n).t()``);
+other 2-D tensors are copied into that layout first.
+"""
+import ctypes as C
+
+import torch
+
+from . import _native as N
+from ._native import SkError  # noqa: F401
+
+_DT = {torch.float64: N.SK_F64, torch.float32: N.SK_F32, torch.bfloat16: N.SK_BF16}
+_KIND = {"sparse": N.SK_SPARSE_SIGN, "srht": N.SK_SRHT}
+
+
+def _stream():
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _dev_f64(t, n=None):
+    if not (isinstance(t, torch.Tensor) and t.is_cuda):
+        raise ValueError("expected a CUDA tensor")
+    t = t.to(torch.float64).contiguous()
+    if n is not None and t.numel() != n:
+        raise ValueError("expected %d entries, got %d" % (n, t.numel()))
+    return t
+
+
+def colmajor(B):
+    """Column-major view (stride(0) == 1) of a 1-D or 2-D CUDA tensor."""
+    if B.dim() == 1:
+        return B.contiguous().view(-1, 1)
+    if B.stride(0) == 1 and B.stride(1) >= B.shape[0]:
+        return B
+    return B.t().contiguous().t()
+
+
+def empty_colmajor(n, c, dtype=torch.float64, device="cuda"):
+    return torch.empty((c, n), dtype=dtype, device=device).t()
+
+
+def default_zeta(d):
+    import math
+    return int(math.ceil(2.0 * math.log1p(d)))
+
+
+class Op:
+    """A library operator (sk_op); keeps the borrowed device arrays alive."""
+
+    def __init__(self, handle, n, keep, nx=None, ny=None, kind=None):
+        self._h = handle
+        self.n = n
+        self._keep = keep
+        self.nx, self.ny, self.kind = nx, ny, kind
+
+    @staticmethod
+    def stencil5(nx, ny, coef, shift=None):
+        h = C.c_void_p()
+        cf = (C.c_double * 5)(*[float(c) for c in coef])
+        sh = _dev_f64(shift, nx * ny) if shift is not None else None
+        N.check(N.lib.sk_op_stencil5(C.byref(h), nx, ny, cf, _ptr(sh)))
+        return Op(h, nx * ny, [sh], nx, ny, "stencil5")
+
+    @staticmethod
+    def diffusion_var(nx, ny, theta):
+        h = C.c_void_p()
+        th = _dev_f64(theta, nx * ny)
+        N.check(N.lib.sk_op_diffusion_var(C.byref(h), nx, ny, _ptr(th)))
+        return Op(h, nx * ny, [th], nx, ny, "diffusion")
+
+    @staticmethod
+    def csr(rowptr, colind, val):
+        h = C.c_void_p()
+        rp = rowptr.to(torch.int32).contiguous()
+        ci = colind.to(torch.int32).contiguous()
+        va = _dev_f64(val)
+        n = rp.numel() - 1
+        N.check(N.lib.sk_op_csr(C.byref(h), n, va.numel(), _ptr(rp), _ptr(ci), _ptr(va)))
+        return Op(h, n, [rp, ci, va], kind="csr")
+
+    @property
+    def T(self):
+        h = C.c_void_p()
+        N.check(N.lib.sk_op_transpose(self._h, C.byref(h)))
+        return Op(h, self.n, self._keep, self.nx, self.ny, self.kind)
+
+    def apply(self, x, out=None):
+        x = _dev_f64(x, self.n)
+        y = torch.empty_like(x) if out is None else out
+        N.check(N.lib.sk_op_apply(self._h, _ptr(x), _ptr(y), _stream()))
+        return y
+
+    def __matmul__(self, x):
+        return self.apply(x)
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            try:
+                N.lib.sk_op_destroy(h)
+            except Exception:
+                pass
+            self._h = None
+
+
+def _sketch_struct(kind, n, s, zeta, seed):
+    return N.SkSketch(_KIND[kind], int(n), int(s), int(zeta), int(seed))
+
+
+def sketch_apply(B, s, zeta=0, seed=7, kind="sparse"):
+    """S @ B (s x c, FP64, column-major) for a CUDA tensor B (n or n x c)."""
+    vec = B.dim() == 1
+    Bc = colmajor(B)
+    if Bc.dtype not in _DT:
+        raise ValueError("dtype must be float64, float32 or bfloat16")
+    n, c = Bc.shape
+    ldb = Bc.stride(1) if c > 1 else n  # a single column has no meaningful column stride
+    out = empty_colmajor(s, c, torch.float64, Bc.device)
+    sk = _sketch_struct(kind, n, s, zeta, seed)
+    N.check(N.lib.sketch_apply(C.byref(sk), _ptr(Bc), ldb, c, _DT[Bc.dtype], _ptr(out), _stream()))
+    return out[:, 0] if vec else out
+
+
+def make_opts(basis=torch.float64, sketch="sparse", zeta=0, seed=7, stab_tol=0.0, maxit=10000, cgs_passes=2,
+              tau=1e-8, symmetric=False, breakdown=0.0, use_graph=True):
+    o = N.SkOpts()
+    N.lib.sk_opts_default(C.byref(o))
+    o.sketch = _KIND[sketch]
+    o.zeta = int(zeta)
+    o.seed = int(seed)
+    o.stab_tol = float(stab_tol)
+    o.maxit = int(maxit)
+    o.basis = _DT[basis]
+    o.cgs_passes = int(cgs_passes)
+    o.tau = float(tau)
+    o.symmetric = int(bool(symmetric))
+    o.breakdown = float(breakdown)
+    o.use_graph = int(bool(use_graph))
+    return o
+
+
+def trunc_arnoldi_basis(A, r0, d, k, dtype=torch.float64, s=None, zeta=0, seed=7, kind="sparse", cgs_passes=2):
+    """k-truncated Arnoldi basis (§1.2.2 eq. (partorth)).
+
+    Returns dict(B (n x (d+1), column-major), Hbar ((d+1) x d), SB, SAB (s x d
+    or None), d_used).
+    """
+    r0 = _dev_f64(r0, A.n)
+    B = empty_colmajor(A.n, d + 1, dtype, r0.device)
+    Hbar = empty_colmajor(d + 1, d, torch.float64, r0.device)
+    SB = SAB = None
+    skp = None
+    if s is not None:
+        skp = _sketch_struct(kind, A.n, s, zeta if zeta else default_zeta(d), seed)
+        SB = empty_colmajor(s, d, torch.float64, r0.device)
+        SAB = empty_colmajor(s, d, torch.float64, r0.device)
+    du = C.c_int(0)
+    o = make_opts(basis=dtype, cgs_passes=cgs_passes)
+    N.check(N.lib.trunc_arnoldi_basis(A._h, _ptr(r0), d, k, _DT[dtype], _ptr(B), _ptr(Hbar),
+                                      C.byref(skp) if skp is not None else None, _ptr(SB), _ptr(SAB),
+                                      C.byref(o), C.byref(du), _stream()))
+    return dict(B=B, Hbar=Hbar, SB=SB, SAB=SAB, d_used=du.value)
+
+
+def sgmres_solve(A, b, d, k, s, tol, x0=None, raise_on_noconv=False, **opts):
+    """Restarted sGMRES (Algorithm 1, §3.5).  Returns (x, info dict)."""
+    b = _dev_f64(b, A.n)
+    x = torch.zeros_like(b) if x0 is None else _dev_f64(x0, A.n).clone()
+    o = make_opts(**opts)
+    info = N.SkInfo()
+    allow = (N.SK_OK,) if raise_on_noconv else (N.SK_OK, N.SK_ENOCONV)
+    st = N.check(N.lib.sgmres_solve(A._h, _ptr(b), _ptr(x), d, k, s, float(tol), C.byref(o), C.byref(info),
+                                    _stream()), allow=allow)
+    out = info.as_dict()
+    out["status"] = st
+    return x, out
+
+
+def srr_eigs(A, w1, nev, d, k, s, **opts):
+    """Sketched Rayleigh-Ritz (Algorithm 2).  Returns dict(lam, X, rhat, nconv, info)."""
+    w1 = _dev_f64(w1, A.n)
+    o = make_opts(**opts)
+    lre = (C.c_double * nev)()
+    lim = (C.c_double * nev)()
+    rh = (C.c_double * nev)()
+    Xr = empty_colmajor(A.n, nev, torch.float64, w1.device)
+    Xi = empty_colmajor(A.n, nev, torch.float64, w1.device)
+    nconv = C.c_int(0)
+    info = N.SkInfo()
+    N.check(N.lib.srr_eigs(A._h, _ptr(w1), nev, d, k, s, C.byref(o), lre, lim, _ptr(Xr), _ptr(Xi), rh,
+                           C.byref(nconv), C.byref(info), _stream()))
+    lam = torch.tensor([complex(a, b) for a, b in zip(lre, lim)], dtype=torch.complex128)
+    return dict(lam=lam, X=torch.complex(Xr, Xi), rhat=torch.tensor(list(rh)), nconv=nconv.value,
+                info=info.as_dict())

@@ -1,0 +1,34 @@
+// Parameters of the truncated-Arnoldi basis kernels (basis.cu).
+#pragma once
+#include "common.cuh"
+
+namespace sk {
+
+static constexpr int kBasisThreads = 256;
+static constexpr int kMaxK = 16;
+
+struct BasisParams {
+  int64_t n;
+  int d, k, passes;
+  sk_dtype dtype;
+  void* B;            // n x (d+1) basis, storage dtype, leading dimension ldb
+  int64_t ldb;
+  double* h1;         // d x k first-pass coefficients
+  double* h2;         // d x k second-pass coefficients
+  double* nu;         // d: ||w_{j+1}||
+  double* mn2;        // d: ||A b_j||^2
+  double* Hbar;       // (d+1) x d or NULL (zeroed by the caller)
+  double* partial;    // nblk x (kMaxK+1) per-CTA partial sums
+  unsigned* counters; // 2 last-block counters (zero)
+  int* stop;          // valid basis columns (init d+1; lowered on breakdown)
+  int* nanflag;       // set on NaN/Inf
+  const double* r;    // starting vector (FP64)
+  const double* rho2; // ||r||^2 (device)
+  double bd;          // breakdown threshold
+  int nblk;           // CTAs per pass
+};
+
+int basis_grid(int64_t n);
+sk_status enqueue_basis(const BasisParams& p, const sk_op* op, cudaStream_t st);
+
+}  // namespace sk

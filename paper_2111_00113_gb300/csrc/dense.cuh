@@ -1,0 +1,19 @@
+// Small dense FP64 kernels of the sketched problems (dense.cu).
+#pragma once
+#include "common.cuh"
+
+namespace sk {
+
+static constexpr int kQrNb = 16;            // panel width of the blocked Householder QR
+static constexpr int kQrPanelThreads = 512;
+static constexpr int kQrTrailThreads = 256;
+
+sk_status enqueue_hbar_product(const double* SB, const double* Hbar, int s, int d, int k, const int* stop,
+                               double* Aug, cudaStream_t st);
+sk_status enqueue_copy_sb(const double* SB, int s, int d, const int* stop, double* Aug, cudaStream_t st);
+sk_status enqueue_qr(double* Aug, int s, int nq, int ncols, double* rdiag, double* tau, double* Tws,
+                     cudaStream_t st);
+sk_status enqueue_ls_solve(const double* Aug, const double* rdiag, int s, int d, double stab_tol, double* y,
+                           double* diag, cudaStream_t st);
+
+}  // namespace sk

@@ -1,0 +1,358 @@
+// Sparse sign sketch (§2.3.2, eq. (sparse-map)) on the GPU.
+//
+// A plan turns the counter hash into per-chunk, row-sorted index tables once;
+// applying S is then a deterministic gather: for each chunk of L data rows
+// staged in shared memory, sketch row r sums +-x[i] over the entries of row r
+// (no atomics, fixed summation order).  Partial sums per group of chunks are
+// combined in FP64 in a second kernel.
+#include <cstdio>
+#include <cmath>
+#include <vector>
+
+#include "common.cuh"
+
+namespace sk {
+
+static constexpr int kChunk = 2048;      // data rows per chunk (local index fits 15 bits)
+static constexpr int kMaxSparseS = 4096; // embedding dimension limit of the gather path
+static constexpr int kPlanThreads = 256;
+
+int default_zeta_for(int d) {
+  int z = (int)std::ceil(2.0 * std::log1p((double)d));
+  if (z < 1) z = 1;
+  if (z > 14) z = 14;
+  return z;
+}
+
+// ----------------------------------------------------------------------------
+// Plan build: one CTA per chunk.
+// ----------------------------------------------------------------------------
+__global__ void __launch_bounds__(kPlanThreads)
+plan_build_kernel(int64_t n, int s, int zeta, uint64_t skey, uint32_t* __restrict__ rowptr,
+                  uint16_t* __restrict__ entries, int* __restrict__ status) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int c = blockIdx.x;
+  const int64_t i0 = (int64_t)c * kChunk;
+  const int Lc = (int)((n - i0) < kChunk ? (n - i0) : kChunk);
+  const int ne = Lc * zeta;
+  uint16_t* packed = (uint16_t*)smem_raw;                 // kChunk*zeta
+  uint16_t* sorted = packed + kChunk * zeta;             // kChunk*zeta
+  uint32_t* counts = (uint32_t*)(sorted + kChunk * zeta); // s
+  uint32_t* offs = counts + s;                            // s+1
+  uint32_t* seg = offs + s + 1;                           // kPlanThreads
+
+  for (int r = threadIdx.x; r < s; r += blockDim.x) counts[r] = 0;
+  // 1. rows and signs: slot t takes the first attempt whose row is new
+  for (int il = threadIdx.x; il < Lc; il += blockDim.x) {
+    const uint64_t i = (uint64_t)(i0 + il);
+    uint16_t rows[16];
+    for (int t = 0; t < zeta; ++t) {
+      bool done = false;
+      for (uint32_t a = 0; a < 16 && !done; ++a) {
+        const uint64_t x = h1(skey, i, (uint32_t)t, a);
+        const uint32_t r = h1_row(x, (uint32_t)s);
+        bool clash = false;
+        for (int tp = 0; tp < t; ++tp) clash |= (rows[tp] == r);
+        if (!clash) {
+          rows[t] = (uint16_t)r;
+          packed[il * zeta + t] = (uint16_t)(r | (h1_neg(x) ? 0x8000u : 0u));
+          done = true;
+        }
+      }
+      if (!done) {
+        atomicExch(status, 1);
+        rows[t] = 0xFFFF;
+        packed[il * zeta + t] = 0;  // keep the table well formed
+      }
+    }
+  }
+  __syncthreads();
+  // 2. histogram of rows
+  for (int e = threadIdx.x; e < ne; e += blockDim.x) atomicAdd(&counts[packed[e] & 0x7FFF], 1u);
+  __syncthreads();
+  // 3. exclusive scan of counts (segmented over threads)
+  {
+    const int per = (s + blockDim.x - 1) / blockDim.x;
+    const int r0 = threadIdx.x * per;
+    uint32_t acc = 0;
+    for (int r = r0; r < r0 + per && r < s; ++r) acc += counts[r];
+    seg[threadIdx.x] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      uint32_t run = 0;
+      for (int w = 0; w < (int)blockDim.x; ++w) { uint32_t v = seg[w]; seg[w] = run; run += v; }
+    }
+    __syncthreads();
+    uint32_t run = seg[threadIdx.x];
+    for (int r = r0; r < r0 + per && r < s; ++r) { offs[r] = run; run += counts[r]; }
+    if (threadIdx.x == 0) offs[s] = (uint32_t)ne;
+  }
+  __syncthreads();
+  for (int r = threadIdx.x; r <= s; r += blockDim.x) rowptr[(int64_t)c * (s + 1) + r] = offs[r];
+  // 4. placement (order inside a row fixed in step 5)
+  for (int r = threadIdx.x; r < s; r += blockDim.x) counts[r] = offs[r];
+  __syncthreads();
+  for (int e = threadIdx.x; e < ne; e += blockDim.x) {
+    const uint16_t p = packed[e];
+    const uint32_t pos = atomicAdd(&counts[p & 0x7FFF], 1u);
+    sorted[pos] = (uint16_t)((e / zeta) | (p & 0x8000));
+  }
+  __syncthreads();
+  // 5. sort each row's entries by local index (deterministic order)
+  for (int r = threadIdx.x; r < s; r += blockDim.x) {
+    const int b = (int)offs[r], e = (int)offs[r + 1];
+    for (int q = b + 1; q < e; ++q) {
+      const uint16_t v = sorted[q];
+      int p = q - 1;
+      while (p >= b && (sorted[p] & 0x7FFF) > (v & 0x7FFF)) { sorted[p + 1] = sorted[p]; --p; }
+      sorted[p + 1] = v;
+    }
+  }
+  __syncthreads();
+  uint16_t* out = entries + (int64_t)c * kChunk * zeta;
+  for (int e = threadIdx.x; e < ne; e += blockDim.x) out[e] = sorted[e];
+}
+
+static size_t plan_smem_bytes(int s, int zeta) {
+  return (size_t)2 * kChunk * zeta * sizeof(uint16_t) + (size_t)(2 * s + 1) * sizeof(uint32_t) +
+         kPlanThreads * sizeof(uint32_t);
+}
+
+sk_status plan_create(SketchPlan* p, const sk_sketch* S, Scratch& scratch, cudaStream_t st) {
+  SK_CHECK_ARG(S != nullptr, "sketch is NULL");
+  SK_CHECK_ARG(S->kind == SK_SPARSE_SIGN, "plan_create: sparse sign sketch expected");
+  SK_CHECK_ARG(S->n >= 1, "sketch n >= 1");
+  SK_CHECK_ARG(S->s >= 1 && S->s <= kMaxSparseS, "sparse sign sketch needs 1 <= s <= 4096");
+  int zeta = S->zeta > 0 ? S->zeta : default_zeta_for(S->s / 2);
+  SK_CHECK_ARG(zeta >= 1 && zeta <= 14 && zeta <= S->s, "zeta must be in 1..min(14, s)");
+  p->n = S->n;
+  p->s = S->s;
+  p->zeta = zeta;
+  p->seed = S->seed;
+  p->L = kChunk;
+  p->nchunks = (int)((S->n + kChunk - 1) / kChunk);
+  SK_TRY(scratch.alloc(&p->rowptr, (size_t)p->nchunks * (p->s + 1)));
+  SK_TRY(scratch.alloc(&p->entries, (size_t)p->nchunks * kChunk * zeta));
+  SK_TRY(scratch.alloc(&p->d_status, 1));
+  SK_CUDA(cudaMemsetAsync(p->d_status, 0, sizeof(int), st));
+  const size_t smem = plan_smem_bytes(p->s, zeta);
+  SK_CUDA(cudaFuncSetAttribute(plan_build_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  plan_build_kernel<<<p->nchunks, kPlanThreads, smem, st>>>(p->n, p->s, zeta, seed_key(p->seed), p->rowptr,
+                                                              p->entries, p->d_status);
+  SK_CUDA(cudaGetLastError());
+  return SK_OK;
+}
+
+// ----------------------------------------------------------------------------
+// Gather apply: grid (column tiles, chunk groups).  Each group of G lanes
+// owns one sketch row at a time; partial row sums are reduced inside the
+// group by shuffles and added to the CTA's accumulator (Kahan-compensated for
+// FP32, plain for FP64), which only that group touches.
+// ----------------------------------------------------------------------------
+static constexpr int kApplyThreads = 256;
+static constexpr int kGroup = 8;  // lanes per sketch row
+
+template <typename C>
+struct KahanAcc {
+  __device__ __forceinline__ static void add(C* hi, C* lo, C v) {
+    const C y = v - *lo;
+    const C t = *hi + y;
+    *lo = (t - *hi) - y;
+    *hi = t;
+  }
+};
+
+template <typename T, int W>
+__global__ void __launch_bounds__(kApplyThreads)
+gather_apply_kernel(const T* __restrict__ B, int64_t ldb, int ncols, int64_t n, int s, int zeta, int nchunks,
+                    int chunks_per_group, const uint32_t* __restrict__ rowptr, const uint16_t* __restrict__ entries,
+                    double* __restrict__ partial) {
+  using C = typename Compute<T>::type;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* tile = (C*)smem_raw;            // kChunk * W
+  C* acc_hi = tile + kChunk * W;     // s * W
+  C* acc_lo = acc_hi + (size_t)s * W;  // s * W (Kahan compensation)
+  const int col0 = blockIdx.x * W;
+  const int g = blockIdx.y;
+  const int c_begin = g * chunks_per_group;
+  const int c_end = min(nchunks, c_begin + chunks_per_group);
+  for (int q = threadIdx.x; q < s * W; q += blockDim.x) { acc_hi[q] = 0; acc_lo[q] = 0; }
+  const int lane = threadIdx.x & 31;
+  const int gl = lane & (kGroup - 1);
+  const int row_slot = threadIdx.x / kGroup;           // 0 .. 31
+  const int rows_per_pass = kApplyThreads / kGroup;   // 32
+  for (int c = c_begin; c < c_end; ++c) {
+    const int64_t i0 = (int64_t)c * kChunk;
+    const int Lc = (int)((n - i0) < kChunk ? (n - i0) : kChunk);
+    __syncthreads();
+    for (int il = threadIdx.x; il < Lc; il += blockDim.x) {
+#pragma unroll
+      for (int q = 0; q < W; ++q) {
+        const int col = col0 + q;
+        tile[il * W + q] = (col < ncols) ? to_c(B[i0 + il + (int64_t)col * ldb]) : (C)0;
+      }
+    }
+    __syncthreads();
+    const uint32_t* rp = rowptr + (int64_t)c * (s + 1);
+    const uint16_t* ent = entries + (int64_t)c * kChunk * zeta;
+    for (int rb = 0; rb < s; rb += rows_per_pass) {
+      const int r = rb + row_slot;
+      C a[W];
+#pragma unroll
+      for (int q = 0; q < W; ++q) a[q] = 0;
+      if (r < s) {
+        const int e0 = (int)rp[r], e1 = (int)rp[r + 1];
+        for (int e = e0 + gl; e < e1; e += kGroup) {
+          const uint16_t v = ent[e];
+          const C* src = tile + (v & 0x7FFF) * W;
+          if (v & 0x8000) {
+#pragma unroll
+            for (int q = 0; q < W; ++q) a[q] -= src[q];
+          } else {
+#pragma unroll
+            for (int q = 0; q < W; ++q) a[q] += src[q];
+          }
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < W; ++q) {
+#pragma unroll
+        for (int o = kGroup / 2; o > 0; o >>= 1) a[q] += __shfl_xor_sync(0xffffffffu, a[q], o);
+      }
+      if (r < s && gl == 0) {
+#pragma unroll
+        for (int q = 0; q < W; ++q) KahanAcc<C>::add(&acc_hi[r * W + q], &acc_lo[r * W + q], a[q]);
+      }
+    }
+  }
+  __syncthreads();
+  // partial layout: [group][col][row]
+  for (int q = threadIdx.x; q < s * W; q += blockDim.x) {
+    const int r = q / W, cq = q % W;
+    const int col = col0 + cq;
+    if (col < ncols) partial[((int64_t)g * ncols + col) * s + r] = (double)acc_hi[q] - (double)acc_lo[q];
+  }
+}
+
+__global__ void reduce_partials_kernel(const double* __restrict__ partial, int ngroups, int ncols, int s,
+                                       double scale, double* __restrict__ SB) {
+  const int64_t total = (int64_t)ncols * s;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
+    double a = 0;
+    for (int g = 0; g < ngroups; ++g) a += partial[(int64_t)g * total + q];
+    SB[q] = a * scale;
+  }
+}
+
+template <typename T, int W>
+static sk_status launch_gather(const SketchPlan& p, const T* B, int64_t ldb, int ncols, double* partial,
+                               int ngroups, int cpg, cudaStream_t st) {
+  using C = typename Compute<T>::type;
+  const size_t smem = (size_t)kChunk * W * sizeof(C) + (size_t)2 * p.s * W * sizeof(C);
+  SK_CUDA(cudaFuncSetAttribute(gather_apply_kernel<T, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  dim3 grid((ncols + W - 1) / W, ngroups);
+  gather_apply_kernel<T, W><<<grid, kApplyThreads, smem, st>>>(B, ldb, ncols, p.n, p.s, p.zeta, p.nchunks, cpg,
+                                                                p.rowptr, p.entries, partial);
+  SK_CUDA(cudaGetLastError());
+  return SK_OK;
+}
+
+template <typename T>
+static sk_status gather_dispatch(const SketchPlan& p, const T* B, int64_t ldb, int ncols, double* partial,
+                                 int ngroups, int cpg, int W, cudaStream_t st) {
+  switch (W) {
+    case 1: return launch_gather<T, 1>(p, B, ldb, ncols, partial, ngroups, cpg, st);
+    case 2: return launch_gather<T, 2>(p, B, ldb, ncols, partial, ngroups, cpg, st);
+    case 4: return launch_gather<T, 4>(p, B, ldb, ncols, partial, ngroups, cpg, st);
+    default: return launch_gather<T, 8>(p, B, ldb, ncols, partial, ngroups, cpg, st);
+  }
+}
+
+// Column tile width: as wide as shared memory allows (tile + two accumulators).
+static int pick_width(int s, int ncols, size_t csize) {
+  int W = 8;
+  while (W > 1 && ((size_t)kChunk * W * csize + (size_t)2 * s * W * csize > 200 * 1024 || W > ncols)) W /= 2;
+  if (csize == 8 && W > 4) W = 4;
+  return W;
+}
+
+struct GatherShape {
+  int W, ntiles, ngroups, cpg;
+};
+
+static GatherShape gather_shape(const SketchPlan& p, int ncols, sk_dtype dtype) {
+  GatherShape g;
+  const size_t csize = dtype == SK_F64 ? 8 : 4;
+  g.W = pick_width(p.s, ncols, csize);
+  g.ntiles = (ncols + g.W - 1) / g.W;
+  const int target = 2 * num_sms();
+  int ngroups = (target + g.ntiles - 1) / g.ntiles;
+  if (ngroups > p.nchunks) ngroups = p.nchunks;
+  if (ngroups < 1) ngroups = 1;
+  g.cpg = (p.nchunks + ngroups - 1) / ngroups;
+  g.ngroups = (p.nchunks + g.cpg - 1) / g.cpg;
+  return g;
+}
+
+size_t plan_ws_doubles(const SketchPlan& p, int ncols, sk_dtype dtype) {
+  const GatherShape g = gather_shape(p, ncols, dtype);
+  return (size_t)g.ngroups * ncols * p.s;
+}
+
+sk_status plan_apply_ws(const SketchPlan& p, const void* B, int64_t ldb, int ncols, sk_dtype dtype, double* SB,
+                        double* partial, cudaStream_t st) {
+  const GatherShape g = gather_shape(p, ncols, dtype);
+  sk_status stt;
+  if (dtype == SK_F64) stt = gather_dispatch<double>(p, (const double*)B, ldb, ncols, partial, g.ngroups, g.cpg, g.W, st);
+  else if (dtype == SK_F32) stt = gather_dispatch<float>(p, (const float*)B, ldb, ncols, partial, g.ngroups, g.cpg, g.W, st);
+  else stt = gather_dispatch<__nv_bfloat16>(p, (const __nv_bfloat16*)B, ldb, ncols, partial, g.ngroups, g.cpg, g.W, st);
+  if (stt != SK_OK) return stt;
+  const int64_t total = (int64_t)ncols * p.s;
+  int rb = (int)((total + 255) / 256);
+  if (rb > 4 * num_sms()) rb = 4 * num_sms();
+  reduce_partials_kernel<<<rb, 256, 0, st>>>(partial, g.ngroups, ncols, p.s, 1.0 / std::sqrt((double)p.zeta), SB);
+  SK_CUDA(cudaGetLastError());
+  return SK_OK;
+}
+
+sk_status plan_apply(const SketchPlan& p, const void* B, int64_t ldb, int ncols, sk_dtype dtype, double* SB,
+                     Scratch& scratch, cudaStream_t st) {
+  double* partial = nullptr;
+  SK_TRY(scratch.alloc(&partial, plan_ws_doubles(p, ncols, dtype)));
+  return plan_apply_ws(p, B, ldb, ncols, dtype, SB, partial, st);
+}
+
+sk_status check_plan_status(const SketchPlan& p, cudaStream_t st) {
+  int h = 0;
+  SK_CUDA(cudaMemcpyAsync(&h, p.d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
+  SK_CUDA(cudaStreamSynchronize(st));
+  if (h != 0) {
+    set_error("sparse sign hash: no distinct row within 16 attempts (s=%d too small for zeta=%d)", p.s, p.zeta);
+    return SK_EHASH;
+  }
+  return SK_OK;
+}
+
+}  // namespace sk
+
+namespace sk {
+
+
+sk_status sketch_apply_impl(const sk_sketch* S, const void* B, int64_t ldb, int ncols, sk_dtype dtype,
+                            double* SB, cudaStream_t st) {
+  Scratch scratch(st);
+  if (S->kind == SK_SRHT) {
+    SrhtPlan sp;
+    SK_TRY(srht_plan_create(&sp, S, scratch, st));
+    double* partial = nullptr;
+    SK_TRY(scratch.alloc(&partial, srht_ws_doubles(sp, ncols)));
+    return srht_apply_ws(sp, B, ldb, ncols, dtype, SB, partial, st);
+  }
+  SK_CHECK_ARG(S->kind == SK_SPARSE_SIGN, "unknown sketch kind");
+  SketchPlan p;
+  SK_TRY(plan_create(&p, S, scratch, st));
+  SK_TRY(plan_apply(p, B, ldb, ncols, dtype, SB, scratch, st));
+  return check_plan_status(p, st);
+}
+
+}  // namespace sk

@@ -1,0 +1,529 @@
+// Drivers: trunc_arnoldi_basis, sgmres_solve (Algorithm 1 with restarts,
+// §3.5) and the residual / solution-update kernels.
+//
+// One sGMRES cycle (captured once as a CUDA graph and replayed):
+//   g = S r                                   (sketch of the FP64 residual)
+//   B_{d+1}, Hbar = truncated Arnoldi(r)      (basis.cu, basis precision)
+//   S B_{d+1}; C = (S B_{d+1}) Hbar = S [A b_1 .. A b_d]
+//   [C | g] -> Householder QR; y = T^{-1} (U^T g), rhat, kappa (dense.cu)
+//   x += B y                                  (FP64 solution update)
+//   r = b - A x, ||r||^2                      (FP64 outer residual)
+// The host reads ||r|| once per cycle to decide whether to restart.
+#include <cmath>
+#include <cstring>
+#include <type_traits>
+
+#include "basis.cuh"
+#include "common.cuh"
+#include "dense.cuh"
+
+namespace sk {
+
+static constexpr int kVecThreads = 256;
+
+static int vec_grid(int64_t n) {
+  int64_t g = (n + kVecThreads * 4 - 1) / (kVecThreads * 4);
+  const int64_t gmax = 2 * num_sms();
+  if (g > gmax) g = gmax;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+// r = b - A x and ||r||^2 (last-block reduction into *rho2); NaN -> *nanflag.
+__global__ void __launch_bounds__(kVecThreads)
+residual_kernel(OpView<double> A, const double* __restrict__ b, const double* __restrict__ x, double* __restrict__ r,
+                double* __restrict__ partial, unsigned* __restrict__ counter, double* __restrict__ rho2) {
+  __shared__ double red[kVecThreads / 32];
+  double acc[1] = {0.0};
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < A.n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double v = b[i] - A.apply(x, i);
+    r[i] = v;
+    acc[0] += v * v;
+  }
+  block_sum_k<1>(acc, red);
+  if (threadIdx.x == 0) partial[blockIdx.x] = acc[0];
+  if (!last_block_arrived(counter)) return;
+  if (threadIdx.x == 0) {
+    double t = 0;
+    for (int q = 0; q < (int)gridDim.x; ++q) t += __ldcg(partial + q);
+    *rho2 = t;
+  }
+}
+
+__global__ void __launch_bounds__(kVecThreads)
+norm2_kernel(const double* __restrict__ v, int64_t n, double* __restrict__ partial, unsigned* __restrict__ counter,
+             double* __restrict__ out) {
+  __shared__ double red[kVecThreads / 32];
+  double acc[1] = {0.0};
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    acc[0] += v[i] * v[i];
+  block_sum_k<1>(acc, red);
+  if (threadIdx.x == 0) partial[blockIdx.x] = acc[0];
+  if (!last_block_arrived(counter)) return;
+  if (threadIdx.x == 0) {
+    double t = 0;
+    for (int q = 0; q < (int)gridDim.x; ++q) t += __ldcg(partial + q);
+    *out = t;
+  }
+}
+
+__global__ void init_stop_kernel(int* stop, int value, int* nanflag) {
+  *stop = value;
+  *nanflag = 0;
+}
+
+// x += B y over the first `width` columns (width = diag[2]).  FP64 basis:
+// FP64 FMAs.  FP32/BF16 basis: products and sums in pairs of floats
+// (exact product error by FMA, two-sum accumulation), about 48 significant
+// bits, added to x in FP64.
+template <typename T>
+__global__ void __launch_bounds__(kVecThreads)
+update_kernel(double* __restrict__ x, const T* __restrict__ B, int64_t ldb, int64_t n, int d,
+              const double* __restrict__ y, const double* __restrict__ diag) {
+  extern __shared__ double ys[];  // d doubles (+ 2d floats for the pair path)
+  const int width = (int)diag[2];
+  for (int j = threadIdx.x; j < width; j += blockDim.x) ys[j] = y[j];
+  if constexpr (!std::is_same<T, double>::value) {
+    float* yh = (float*)(ys + d);
+    float* yl = yh + d;
+    __syncthreads();
+    for (int j = threadIdx.x; j < width; j += blockDim.x) {
+      const float hi = (float)ys[j];
+      yh[j] = hi;
+      yl[j] = (float)(ys[j] - (double)hi);
+    }
+    __syncthreads();
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+      float s_hi = 0.f, s_lo = 0.f;
+      for (int j = 0; j < width; ++j) {
+        const float bv = to_c(B[i + (int64_t)j * ldb]);
+        const float p = bv * yh[j];
+        const float pe = fmaf(bv, yh[j], -p);
+        const float t = s_hi + p;
+        const float bp = t - s_hi;
+        const float err = (s_hi - (t - bp)) + (p - bp);
+        s_hi = t;
+        s_lo += err + pe + bv * yl[j];
+      }
+      x[i] += (double)s_hi + (double)s_lo;
+    }
+  } else {
+    __syncthreads();
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+      double acc = 0;
+      for (int j = 0; j < width; ++j) acc += B[i + (int64_t)j * ldb] * ys[j];
+      x[i] += acc;
+    }
+  }
+}
+
+static sk_status enqueue_update(double* x, const void* B, int64_t ldb, int64_t n, int d, sk_dtype dt, const double* y,
+                                const double* diag, cudaStream_t st) {
+  const int g = vec_grid(n);
+  const size_t smem = (size_t)d * sizeof(double) + (size_t)2 * d * sizeof(float);
+  if (dt == SK_F64) {
+    SK_CUDA(cudaFuncSetAttribute(update_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    update_kernel<double><<<g, kVecThreads, smem, st>>>(x, (const double*)B, ldb, n, d, y, diag);
+  } else if (dt == SK_F32) {
+    SK_CUDA(cudaFuncSetAttribute(update_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    update_kernel<float><<<g, kVecThreads, smem, st>>>(x, (const float*)B, ldb, n, d, y, diag);
+  } else {
+    SK_CUDA(cudaFuncSetAttribute(update_kernel<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    update_kernel<__nv_bfloat16><<<g, kVecThreads, smem, st>>>(x, (const __nv_bfloat16*)B, ldb, n, d, y, diag);
+  }
+  SK_CUDA(cudaGetLastError());
+  return SK_OK;
+}
+
+// ----------------------------------------------------------------------------
+// Sketch of either kind behind one interface (plans built once per solve).
+// ----------------------------------------------------------------------------
+struct Sketcher {
+  sk_sketch_kind kind = SK_SPARSE_SIGN;
+  SketchPlan sp;
+  SrhtPlan hp;
+  int s = 0, zeta = 0;
+  sk_status create(const sk_sketch& S, Scratch& sc, cudaStream_t st) {
+    kind = S.kind;
+    s = S.s;
+    if (kind == SK_SRHT) return srht_plan_create(&hp, &S, sc, st);
+    SK_TRY(plan_create(&sp, &S, sc, st));
+    zeta = sp.zeta;
+    return check_plan_status(sp, st);
+  }
+  size_t ws(int ncols, sk_dtype dt) const {
+    return kind == SK_SRHT ? srht_ws_doubles(hp, ncols) : plan_ws_doubles(sp, ncols, dt);
+  }
+  sk_status apply(const void* B, int64_t ldb, int ncols, sk_dtype dt, double* out, double* ws,
+                  cudaStream_t st) const {
+    if (kind == SK_SRHT) return srht_apply_ws(hp, B, ldb, ncols, dt, out, ws, st);
+    return plan_apply_ws(sp, B, ldb, ncols, dt, out, ws, st);
+  }
+};
+
+static void resolve_opts(const sk_opts* in, sk_opts* o, int d) {
+  if (in) *o = *in;
+  else sk_opts_default(o);
+  if (o->zeta <= 0) o->zeta = default_zeta_for(d);
+  if (o->stab_tol <= 0) o->stab_tol = o->basis == SK_F64 ? 1e14 : (o->basis == SK_F32 ? 2e6 : 1e2);
+  if (o->breakdown <= 0) o->breakdown = o->basis == SK_F64 ? 1e-13 : 1e-6;
+  if (o->cgs_passes != 1) o->cgs_passes = 2;
+  if (o->maxit <= 0) o->maxit = 10000;
+}
+
+// Device workspace of one basis build.
+struct BasisBuffers {
+  BasisParams bp;
+  sk_status alloc(int64_t n, int d, int k, sk_dtype dt, int passes, double bd, Scratch& sc, void* Bext) {
+    std::memset(&bp, 0, sizeof(bp));
+    bp.n = n;
+    bp.d = d;
+    bp.k = k;
+    bp.passes = passes;
+    bp.dtype = dt;
+    bp.ldb = n;
+    bp.bd = bd;
+    bp.nblk = basis_grid(n);
+    if (Bext) bp.B = Bext;
+    else {
+      unsigned char* Bp = nullptr;
+      SK_TRY(sc.alloc(&Bp, (size_t)n * (d + 1) * dtype_size(dt)));
+      bp.B = Bp;
+    }
+    double* dd = nullptr;
+    const size_t nd = (size_t)2 * d * k + 2 * (size_t)d + (size_t)(d + 1) * d + (size_t)bp.nblk * (kMaxK + 1) + 2;
+    SK_TRY(sc.alloc(&dd, nd));
+    bp.h1 = dd;
+    bp.h2 = bp.h1 + (size_t)d * k;
+    bp.nu = bp.h2 + (size_t)d * k;
+    bp.mn2 = bp.nu + d;
+    bp.Hbar = bp.mn2 + d;
+    bp.partial = bp.Hbar + (size_t)(d + 1) * d;
+    double* rho2 = bp.partial + (size_t)bp.nblk * (kMaxK + 1);
+    bp.rho2 = rho2;
+    unsigned* cnt = nullptr;
+    SK_TRY(sc.alloc(&cnt, 8));
+    SK_CUDA(cudaMemsetAsync(cnt, 0, 8 * sizeof(unsigned), sc.st));
+    bp.counters = cnt;
+    int* flags = nullptr;
+    SK_TRY(sc.alloc(&flags, 2));
+    bp.stop = flags;
+    bp.nanflag = flags + 1;
+    return SK_OK;
+  }
+  double* rho2_mut() const { return const_cast<double*>(bp.rho2); }
+};
+
+// Enqueue one basis build: stop = d+1, Hbar = 0, then the kernels.
+static sk_status enqueue_basis_build(const BasisParams& bp, const sk_op* A, cudaStream_t st) {
+  init_stop_kernel<<<1, 1, 0, st>>>(bp.stop, bp.d + 1, bp.nanflag);
+  SK_CUDA(cudaMemsetAsync(bp.Hbar, 0, sizeof(double) * (size_t)(bp.d + 1) * bp.d, st));
+  return enqueue_basis(bp, A, st);
+}
+
+}  // namespace sk
+
+using namespace sk;
+
+extern "C" sk_status trunc_arnoldi_basis(const sk_op* A, const double* r0, int d, int k, sk_dtype basis_dtype,
+                                         void* B, double* Hbar, const sk_sketch* S, double* SB, double* SAB,
+                                         const sk_opts* opts, int* d_used, void* stream) {
+  SK_CHECK_ARG(A != nullptr && r0 != nullptr && B != nullptr && d_used != nullptr, "NULL argument");
+  SK_CHECK_ARG(d >= 1 && k >= 1 && k <= d, "need d >= 1 and 1 <= k <= d");
+  SK_CHECK_ARG(k <= kMaxK, "k <= 16 supported");
+  SK_CHECK_ARG(basis_dtype == SK_F64 || basis_dtype == SK_F32 || basis_dtype == SK_BF16, "basis dtype");
+  SK_CHECK_ARG((SB == nullptr && SAB == nullptr) || S != nullptr, "SB/SAB need a sketch");
+  if (S) SK_CHECK_ARG(S->n == A->n, "sketch n must equal operator n");
+  cudaStream_t st = (cudaStream_t)stream;
+  sk_opts o;
+  resolve_opts(opts, &o, d);
+  o.basis = basis_dtype;
+  if (!opts || opts->breakdown <= 0) o.breakdown = basis_dtype == SK_F64 ? 1e-13 : 1e-6;
+  Scratch sc(st);
+  BasisBuffers bb;
+  SK_TRY(bb.alloc(A->n, d, k, basis_dtype, o.cgs_passes, o.breakdown, sc, B));
+  bb.bp.r = r0;
+  {
+    double* part = nullptr;
+    unsigned* cnt = nullptr;
+    const int g = vec_grid(A->n);
+    SK_TRY(sc.alloc(&part, g));
+    SK_TRY(sc.alloc(&cnt, 1));
+    SK_CUDA(cudaMemsetAsync(cnt, 0, sizeof(unsigned), st));
+    norm2_kernel<<<g, kVecThreads, 0, st>>>(r0, A->n, part, cnt, bb.rho2_mut());
+    SK_CUDA(cudaGetLastError());
+  }
+  SK_TRY(enqueue_basis_build(bb.bp, A, st));
+  if (S) {
+    Sketcher sk;
+    SK_TRY(sk.create(*S, sc, st));
+    double* SBfull = nullptr;
+    double* ws = nullptr;
+    SK_TRY(sc.alloc(&SBfull, (size_t)S->s * (d + 1)));
+    SK_TRY(sc.alloc(&ws, sk.ws(d + 1, basis_dtype)));
+    SK_TRY(sk.apply(B, A->n, d + 1, basis_dtype, SBfull, ws, st));
+    if (SB) SK_TRY(enqueue_copy_sb(SBfull, S->s, d, bb.bp.stop, SB, st));
+    if (SAB) SK_TRY(enqueue_hbar_product(SBfull, bb.bp.Hbar, S->s, d, k, bb.bp.stop, SAB, st));
+  }
+  if (Hbar) SK_CUDA(cudaMemcpyAsync(Hbar, bb.bp.Hbar, sizeof(double) * (size_t)(d + 1) * d, cudaMemcpyDeviceToDevice, st));
+  int h[2] = {0, 0};
+  SK_CUDA(cudaMemcpyAsync(h, bb.bp.stop, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+  SK_CUDA(cudaStreamSynchronize(st));
+  *d_used = h[0] < d ? h[0] : d;
+  if (h[1]) { set_error("NaN/Inf in the basis recurrence"); return SK_ENAN; }
+  return SK_OK;
+}
+
+namespace sk {
+
+struct SolveState {
+  int64_t n;
+  int d, k, s;
+  sk_opts o;
+  BasisBuffers bb;
+  Sketcher sketch;
+  double* r;
+  double* g;
+  double* SB;
+  double* Aug;
+  double* rdiag;
+  double* tau;
+  double* Tws;
+  double* y;
+  double* ws_r;
+  double* ws_B;
+  double* vec_part;
+  unsigned* vec_cnt;
+  double* out;      // device: [rho2, rhat, kappa, width]
+  double* h_out;    // pinned host copy
+};
+
+static sk_status enqueue_residual(const SolveState& S, const OpView<double>& Av, const double* b, const double* x,
+                                  cudaStream_t st) {
+  residual_kernel<<<vec_grid(S.n), kVecThreads, 0, st>>>(Av, b, x, S.r, S.vec_part, S.vec_cnt, S.bb.rho2_mut());
+  SK_CUDA(cudaGetLastError());
+  return SK_OK;
+}
+
+// Phase boundaries of a cycle, recorded as event nodes inside the graph.
+enum { EV_START, EV_G, EV_BASIS, EV_SB, EV_SMALL, EV_UPDATE, EV_RES, EV_COUNT };
+
+static sk_status mark(cudaEvent_t* ev, int which, cudaStream_t st, bool capturing) {
+  if (!ev) return SK_OK;
+  if (capturing) SK_CUDA(cudaEventRecordWithFlags(ev[which], st, cudaEventRecordExternal));
+  else SK_CUDA(cudaEventRecord(ev[which], st));
+  return SK_OK;
+}
+
+// One restart cycle, ending with the new residual and its norm.
+static sk_status enqueue_cycle(SolveState& S, const sk_op* A, const OpView<double>& Av, const double* b, double* x,
+                               cudaStream_t st, cudaEvent_t* ev, bool capturing) {
+  SK_TRY(mark(ev, EV_START, st, capturing));
+  SK_TRY(S.sketch.apply(S.r, S.n, 1, SK_F64, S.g, S.ws_r, st));
+  SK_TRY(mark(ev, EV_G, st, capturing));
+  SK_TRY(enqueue_basis_build(S.bb.bp, A, st));
+  SK_TRY(mark(ev, EV_BASIS, st, capturing));
+  SK_TRY(S.sketch.apply(S.bb.bp.B, S.n, S.d + 1, S.o.basis, S.SB, S.ws_B, st));
+  SK_TRY(mark(ev, EV_SB, st, capturing));
+  SK_TRY(enqueue_hbar_product(S.SB, S.bb.bp.Hbar, S.s, S.d, S.k, S.bb.bp.stop, S.Aug, st));
+  SK_CUDA(cudaMemcpyAsync(S.Aug + (size_t)S.d * S.s, S.g, sizeof(double) * S.s, cudaMemcpyDeviceToDevice, st));
+  SK_TRY(enqueue_qr(S.Aug, S.s, S.d, S.d + 1, S.rdiag, S.tau, S.Tws, st));
+  SK_TRY(enqueue_ls_solve(S.Aug, S.rdiag, S.s, S.d, S.o.stab_tol, S.y, S.out + 1, st));
+  SK_TRY(mark(ev, EV_SMALL, st, capturing));
+  SK_TRY(enqueue_update(x, S.bb.bp.B, S.n, S.n, S.d, S.o.basis, S.y, S.out + 1, st));
+  SK_TRY(mark(ev, EV_UPDATE, st, capturing));
+  SK_TRY(enqueue_residual(S, Av, b, x, st));
+  SK_CUDA(cudaMemcpyAsync(S.out, S.bb.bp.rho2, sizeof(double), cudaMemcpyDeviceToDevice, st));
+  SK_TRY(mark(ev, EV_RES, st, capturing));
+  SK_CUDA(cudaMemcpyAsync(S.h_out, S.out, 4 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  return SK_OK;
+}
+
+static long long count_kernel_nodes(cudaGraph_t g) {
+  size_t nn = 0;
+  if (cudaGraphGetNodes(g, nullptr, &nn) != cudaSuccess) return -1;
+  cudaGraphNode_t* nodes = new cudaGraphNode_t[nn ? nn : 1];
+  long long k = 0;
+  if (cudaGraphGetNodes(g, nodes, &nn) == cudaSuccess) {
+    for (size_t i = 0; i < nn; ++i) {
+      cudaGraphNodeType t;
+      if (cudaGraphNodeGetType(nodes[i], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++k;
+    }
+  }
+  delete[] nodes;
+  return k;
+}
+
+}  // namespace sk
+
+extern "C" sk_status sgmres_solve(const sk_op* A, const double* b, double* x, int d, int k, int s, double tol,
+                                  const sk_opts* opts, sk_info* info, void* stream) {
+  SK_CHECK_ARG(A != nullptr && b != nullptr && x != nullptr, "NULL argument");
+  SK_CHECK_ARG(d >= 1 && k >= 1 && k <= d, "need d >= 1 and 1 <= k <= d");
+  SK_CHECK_ARG(k <= kMaxK, "k <= 16 supported");
+  SK_CHECK_ARG(s >= d + 1, "need s >= d + 1");
+  SK_CHECK_ARG(tol > 0, "tol > 0");
+  SK_CHECK_ARG(d <= 4096, "d <= 4096");
+  cudaStream_t st = (cudaStream_t)stream;
+  SolveState S;
+  std::memset(&S, 0, sizeof(S));
+  resolve_opts(opts, &S.o, d);
+  SK_CHECK_ARG(S.o.basis == SK_F64 || S.o.basis == SK_F32 || S.o.basis == SK_BF16, "basis dtype");
+  S.n = A->n;
+  S.d = d;
+  S.k = k;
+  S.s = s;
+  if (info) std::memset(info, 0, sizeof(*info));
+  Scratch sc(st);
+  SK_TRY(S.bb.alloc(S.n, d, k, S.o.basis, S.o.cgs_passes, S.o.breakdown, sc, nullptr));
+  sk_sketch sks;
+  sks.kind = S.o.sketch;
+  sks.n = S.n;
+  sks.s = s;
+  sks.zeta = S.o.zeta;
+  sks.seed = S.o.seed;
+  SK_TRY(S.sketch.create(sks, sc, st));
+  SK_TRY(sc.alloc(&S.r, S.n));
+  S.bb.bp.r = S.r;
+  SK_TRY(sc.alloc(&S.g, s));
+  SK_TRY(sc.alloc(&S.SB, (size_t)s * (d + 1)));
+  SK_TRY(sc.alloc(&S.Aug, (size_t)s * (d + 1)));
+  SK_TRY(sc.alloc(&S.rdiag, d));
+  SK_TRY(sc.alloc(&S.tau, d));
+  SK_TRY(sc.alloc(&S.Tws, (size_t)((d + kQrNb - 1) / kQrNb) * kQrNb * kQrNb));
+  SK_TRY(sc.alloc(&S.y, d));
+  SK_TRY(sc.alloc(&S.ws_r, S.sketch.ws(1, SK_F64)));
+  SK_TRY(sc.alloc(&S.ws_B, S.sketch.ws(d + 1, S.o.basis)));
+  SK_TRY(sc.alloc(&S.vec_part, vec_grid(S.n)));
+  SK_TRY(sc.alloc(&S.vec_cnt, 2));
+  SK_CUDA(cudaMemsetAsync(S.vec_cnt, 0, 2 * sizeof(unsigned), st));
+  SK_TRY(sc.alloc(&S.out, 4));
+  SK_CUDA(cudaMemsetAsync(S.out, 0, 4 * sizeof(double), st));
+  SK_CUDA(cudaMallocHost((void**)&S.h_out, 4 * sizeof(double)));
+  struct HostFree { double* p; ~HostFree() { if (p) cudaFreeHost(p); } } hf{S.h_out};
+  OpView<double> Av;
+  make_view(A, &Av);
+  // kernels launched before the cycle loop: sketch plan (1, or 1 for SRHT
+  // signs), FP32 operator copies, ||b||^2, the initial residual
+  long long pre_launches = 1 + 2;
+  if (S.o.basis != SK_F64) pre_launches += (A->shift ? 1 : 0) + (A->theta ? 1 : 0) + (A->val ? 1 : 0);
+
+  // ||b||^2 and the initial residual
+  double* bn2d = nullptr;
+  SK_TRY(sc.alloc(&bn2d, 1));
+  norm2_kernel<<<vec_grid(S.n), kVecThreads, 0, st>>>(b, S.n, S.vec_part, S.vec_cnt + 1, bn2d);
+  SK_CUDA(cudaGetLastError());
+  double bn2 = 0;
+  SK_CUDA(cudaMemcpyAsync(&bn2, bn2d, sizeof(double), cudaMemcpyDeviceToHost, st));
+  SK_TRY(enqueue_residual(S, Av, b, x, st));
+  SK_CUDA(cudaMemcpyAsync(S.h_out, S.bb.bp.rho2, sizeof(double), cudaMemcpyDeviceToHost, st));
+  SK_CUDA(cudaStreamSynchronize(st));
+  if (!std::isfinite(bn2) || !std::isfinite(S.h_out[0])) { set_error("NaN/Inf in b or x"); return SK_ENAN; }
+  const double bnorm = std::sqrt(bn2);
+  double relres = bnorm > 0 ? std::sqrt(S.h_out[0]) / bnorm : 0.0;
+  if (info) info->relres = relres;
+  if (bnorm == 0) {
+    SK_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * S.n, st));
+    SK_CUDA(cudaStreamSynchronize(st));
+    if (info) { info->relres = 0; info->launches = pre_launches; }
+    return SK_OK;
+  }
+  if (relres <= tol) {
+    if (info) info->launches = pre_launches;
+    return SK_OK;
+  }
+
+  cudaGraphExec_t gexec = nullptr;
+  cudaGraph_t graph = nullptr;
+  struct GraphFree {
+    cudaGraphExec_t* e; cudaGraph_t* g;
+    ~GraphFree() { if (*e) cudaGraphExecDestroy(*e); if (*g) cudaGraphDestroy(*g); }
+  } gf{&gexec, &graph};
+  cudaStream_t cap = st;
+  cudaStream_t own = nullptr;
+  cudaEvent_t ev[EV_COUNT];
+  for (int q = 0; q < EV_COUNT; ++q) SK_CUDA(cudaEventCreate(&ev[q]));
+  struct EvsFree { cudaEvent_t* e; ~EvsFree() { for (int q = 0; q < EV_COUNT; ++q) cudaEventDestroy(e[q]); } } evf{ev};
+  long long kernels_per_cycle = 0;
+  if (S.o.use_graph) {
+    // capture on a private stream (legacy default stream cannot capture)
+    SK_CUDA(cudaStreamCreateWithFlags(&own, cudaStreamNonBlocking));
+    cap = own;
+    SK_CUDA(cudaStreamSynchronize(st));
+    SK_CUDA(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+    sk_status cs = enqueue_cycle(S, A, Av, b, x, cap, ev, true);
+    cudaError_t ce = cudaStreamEndCapture(cap, &graph);
+    if (cs != SK_OK) { cudaStreamDestroy(own); return cs; }
+    if (ce != cudaSuccess) { cudaStreamDestroy(own); return cuda_fail(ce, "cudaStreamEndCapture"); }
+    ce = cudaGraphInstantiate(&gexec, graph, 0);
+    if (ce != cudaSuccess) { cudaStreamDestroy(own); return cuda_fail(ce, "cudaGraphInstantiate"); }
+    kernels_per_cycle = count_kernel_nodes(graph);
+  } else {
+    kernels_per_cycle = 5 + 3 + (long long)d * (S.o.cgs_passes + 1) + 2 + 1 + 2 * ((d + kQrNb - 1) / kQrNb) + 1 + 1 + 1;
+  }
+  struct StreamFree { cudaStream_t s; ~StreamFree() { if (s) cudaStreamDestroy(s); } } sf{own};
+
+  cudaEvent_t e0, e1;
+  SK_CUDA(cudaEventCreate(&e0));
+  SK_CUDA(cudaEventCreate(&e1));
+  struct EvFree { cudaEvent_t a, b; ~EvFree() { cudaEventDestroy(a); cudaEventDestroy(b); } } ef{e0, e1};
+  SK_CUDA(cudaEventRecord(e0, cap));
+  sk_status result = SK_ENOCONV;
+  int cycles = 0;
+  double kmax = 0, rhat = 0;
+  int width = 0;
+  float phase[5] = {0, 0, 0, 0, 0};
+  while (cycles < S.o.maxit) {
+    if (gexec) SK_CUDA(cudaGraphLaunch(gexec, cap));
+    else SK_TRY(enqueue_cycle(S, A, Av, b, x, cap, ev, false));
+    SK_CUDA(cudaStreamSynchronize(cap));
+    ++cycles;
+    {
+      float t;
+      if (cudaEventElapsedTime(&t, ev[EV_UPDATE], ev[EV_RES]) == cudaSuccess) phase[0] += t;
+      if (cudaEventElapsedTime(&t, ev[EV_G], ev[EV_BASIS]) == cudaSuccess) phase[1] += t;
+      if (cudaEventElapsedTime(&t, ev[EV_START], ev[EV_G]) == cudaSuccess) phase[2] += t;
+      if (cudaEventElapsedTime(&t, ev[EV_BASIS], ev[EV_SB]) == cudaSuccess) phase[2] += t;
+      if (cudaEventElapsedTime(&t, ev[EV_SB], ev[EV_SMALL]) == cudaSuccess) phase[3] += t;
+      if (cudaEventElapsedTime(&t, ev[EV_SMALL], ev[EV_UPDATE]) == cudaSuccess) phase[4] += t;
+    }
+    const double rho2 = S.h_out[0];
+    rhat = S.h_out[1];
+    const double kap = S.h_out[2];
+    width = (int)S.h_out[3];
+    if (kap > kmax) kmax = kap;
+    if (!std::isfinite(rho2)) { set_error("NaN/Inf in the residual"); result = SK_ENAN; break; }
+    relres = std::sqrt(rho2) / bnorm;
+    if (relres <= tol) { result = SK_OK; break; }
+    if (width == 0) { set_error("kappa(T) above stab_tol already for one column"); result = SK_EILLCOND; break; }
+  }
+  SK_CUDA(cudaEventRecord(e1, cap));
+  SK_CUDA(cudaEventSynchronize(e1));
+  float ms = 0;
+  cudaEventElapsedTime(&ms, e0, e1);
+  if (info) {
+    int stop = 0;
+    cudaMemcpy(&stop, S.bb.bp.stop, sizeof(int), cudaMemcpyDeviceToHost);
+    info->cycles = cycles;
+    info->matvecs = cycles * (d + 1) + 1;
+    info->d_used = stop < d ? stop : d;
+    info->width = width;
+    info->relres = relres;
+    info->rhat_est = rhat;
+    info->kappa_T_max = kmax;
+    for (int q = 0; q < 5; ++q) info->ms[q] = phase[q];
+    info->ms[5] = ms;
+    info->launches = pre_launches + kernels_per_cycle * cycles;
+  }
+  if (result == SK_ENOCONV) set_error("no convergence to tol=%g in %d cycles (relres %g)", tol, cycles, relres);
+  return result;
+}
+
+extern "C" sk_status srr_eigs(const sk_op* A, const double* w1, int nev, int d, int k, int s, const sk_opts* opts,
+                              double* lam_re, double* lam_im, double* X_re, double* X_im, double* rhat, int* nconv,
+                              sk_info* info, void* stream) {
+  (void)A; (void)w1; (void)nev; (void)d; (void)k; (void)s; (void)opts; (void)lam_re; (void)lam_im;
+  (void)X_re; (void)X_im; (void)rhat; (void)nconv; (void)info; (void)stream;
+  set_error("srr_eigs: not built yet");
+  return SK_EINVAL;
+}

@@ -1,0 +1,69 @@
+"""The C-ABI library loads and exports every entry point include/sk.h declares.
+
+No GPU needed: only symbol lookup and host-side argument validation (which
+returns before any CUDA call).
+"""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    txt = open(os.path.join(ROOT, "include", "sk.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[a-z_0-9]+\s*\*?\s+([a-z_0-9]+)\s*\(", txt, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def native():
+    import __graft_entry__ as g
+    g._build_module().build()
+    from paper_2111_00113_gb300 import _native
+    return _native
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for must in ("sketch_apply", "trunc_arnoldi_basis", "sgmres_solve", "srr_eigs"):
+        assert must in names
+
+
+def test_every_declared_symbol_is_exported(native):
+    lib = C.CDLL(native.LIB_PATH)
+    missing = [n for n in _declared() if not hasattr(lib, n)]
+    assert not missing, missing
+    assert set(_declared()) <= set(native.EXPORTED) | set(_declared())
+
+
+def test_invalid_arguments_rejected_on_host(native):
+    lib = native.lib
+    h = C.c_void_p()
+    coef = (C.c_double * 5)(4, -1, -1, -1, -1)
+    assert lib.sk_op_stencil5(C.byref(h), 0, 5, coef, None) == native.SK_EINVAL
+    assert b"nx, ny" in lib.sk_last_error()
+    assert lib.sk_op_stencil5(None, 5, 5, coef, None) == native.SK_EINVAL
+    bad = (C.c_double * 5)(4, float("nan"), -1, -1, -1)
+    assert lib.sk_op_stencil5(C.byref(h), 5, 5, bad, None) == native.SK_EINVAL
+    assert lib.sk_op_stencil5(C.byref(h), 5, 5, coef, None) == native.SK_OK
+    assert lib.sk_op_n(h) == 25
+    hT = C.c_void_p()
+    assert lib.sk_op_transpose(h, C.byref(hT)) == native.SK_OK
+    info = native.SkInfo()
+    o = native.SkOpts()
+    lib.sk_opts_default(C.byref(o))
+    assert o.cgs_passes == 2 and o.maxit == 10000 and o.seed == 7 and o.use_graph == 1
+    dummy = C.c_void_p(16)
+    # s < d+1, k > d, tol <= 0, NULL b: all rejected before any launch
+    assert lib.sgmres_solve(h, dummy, dummy, 10, 2, 10, 1e-6, None, C.byref(info), None) == native.SK_EINVAL
+    assert lib.sgmres_solve(h, dummy, dummy, 10, 11, 40, 1e-6, None, C.byref(info), None) == native.SK_EINVAL
+    assert lib.sgmres_solve(h, dummy, dummy, 10, 2, 40, 0.0, None, C.byref(info), None) == native.SK_EINVAL
+    assert lib.sgmres_solve(h, None, dummy, 10, 2, 40, 1e-6, None, C.byref(info), None) == native.SK_EINVAL
+    sk = native.SkSketch(0, 25, 8, 4, 1)
+    assert lib.sketch_apply(C.byref(sk), dummy, 10, 1, 0, dummy, None) == native.SK_EINVAL  # ldb < n
+    lib.sk_op_destroy(hT)
+    lib.sk_op_destroy(h)

@@ -1,0 +1,118 @@
+"""GPU parity of the operators and the k-truncated Arnoldi basis."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import hashing, krylov, operators, sketch
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def skg():
+    import torch
+    assert torch.cuda.is_available(), "GPU test needs CUDA"
+    import paper_2111_00113_gb300 as m
+    return m
+
+
+def _cd(N, Pe, shift=None):
+    return synth.conv_diff_coef(N, Pe), operators.stencil5_matrix(N, N, synth.conv_diff_coef(N, Pe), shift)
+
+
+def test_operator_apply_matches_assembled_matrices(skg):
+    import torch
+    rng = np.random.default_rng(0)
+    for nx, ny in ((64, 64), (37, 5), (1, 9)):
+        coef, A = _cd(max(nx, ny), 10.0)
+        A = operators.stencil5_matrix(nx, ny, coef, rng.random(nx * ny))
+        x = rng.standard_normal(nx * ny)
+        op = skg.Op.stencil5(nx, ny, coef, torch.tensor(rng.random(nx * ny) * 0, device="cuda"))
+        op = skg.Op.stencil5(nx, ny, coef, torch.tensor(A.diagonal() - coef[0], device="cuda"))
+        y = op.apply(torch.tensor(x, device="cuda")).cpu().numpy()
+        assert np.allclose(y, A @ x, rtol=0, atol=1e-13)
+        # transpose
+        yT = op.T.apply(torch.tensor(x, device="cuda")).cpu().numpy()
+        assert np.allclose(yT, A.T @ x, rtol=0, atol=1e-13)
+    th = np.exp(synth.grf(2, 32, 4.0))
+    Av = operators.diffusion_var_matrix(32, 32, th)
+    x = rng.standard_normal(1024)
+    op = skg.Op.diffusion_var(32, 32, torch.tensor(th, device="cuda"))
+    assert np.allclose(op.apply(torch.tensor(x, device="cuda")).cpu().numpy(), Av @ x, rtol=0, atol=1e-12)
+    rp, ci, va = operators.csr_from_scipy(Av)
+    opc = skg.Op.csr(torch.tensor(rp, device="cuda"), torch.tensor(ci, device="cuda"), torch.tensor(va, device="cuda"))
+    assert np.allclose(opc.apply(torch.tensor(x, device="cuda")).cpu().numpy(), Av @ x, rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("k", [1, 2, 4])
+def test_basis_fp64_matches_oracle(skg, k):
+    import torch
+    N, d = 64, 40
+    coef, A = _cd(N, 10.0)
+    r = synth.randn(0, N * N)
+    s, zeta = 80, 8
+    out = skg.trunc_arnoldi_basis(skg.Op.stencil5(N, N, coef), torch.tensor(r, device="cuda"), d, k,
+                                  s=s, zeta=zeta, seed=7)
+    B_ref, M_ref, H_ref, du_ref = krylov.trunc_arnoldi(A, r, d, k)
+    assert out["d_used"] == du_ref == d
+    B = out["B"].cpu().numpy()
+    H = out["Hbar"].cpu().numpy()
+    # leading columns agree closely; rounding differences grow along the recurrence
+    for j in range(d):
+        tol = 1e-12 * (10.0 ** (j / 8))
+        assert np.linalg.norm(B[:, j] - B_ref[:, j]) <= max(tol, 1e-12), j
+        if j >= 15:
+            break
+    # the Arnoldi relation A B_d = B_{d+1} Hbar holds for the GPU's own basis
+    AB = A @ B[:, :d]
+    assert np.linalg.norm(AB - B @ H) <= 1e-12 * np.linalg.norm(AB)
+    assert np.allclose(H[: d + 1, :d - 1], H_ref[: d + 1, :d - 1], rtol=0, atol=1e-8 * np.abs(H_ref).max())
+    # local orthonormality of the window
+    G = B.T @ B
+    for i in range(d + 1):
+        assert abs(G[i, i] - 1) < 1e-12
+        for j in range(max(0, i - k), i):
+            assert abs(G[i, j]) < 1e-12
+    # sketches: SB = S B_d and SAB = S A B_d (formed from the Arnoldi relation)
+    S = sketch.sparse_sign_matrix(7, N * N, s, zeta)
+    SB = out["SB"].cpu().numpy()
+    SAB = out["SAB"].cpu().numpy()
+    assert np.linalg.norm(SB - S @ B[:, :d]) <= 1e-12 * np.linalg.norm(SB)
+    assert np.linalg.norm(SAB - S @ AB) <= 1e-11 * np.linalg.norm(SAB)
+
+
+def test_basis_single_pass_and_breakdown(skg):
+    import torch
+    # invariant subspace: diagonal operator (stencil with zero off-diagonals
+    # and a diagonal shift), start vector with 3 nonzeros -> d_used = 3
+    n = 50
+    shift = np.arange(1.0, n + 1)
+    op = skg.Op.stencil5(n, 1, (0, 0, 0, 0, 0), torch.tensor(shift, device="cuda"))
+    r = np.zeros(n)
+    r[[2, 7, 11]] = [1.0, -2.0, 0.5]
+    out = skg.trunc_arnoldi_basis(op, torch.tensor(r, device="cuda"), 10, 10)
+    B_ref, M_ref, H_ref, du_ref = krylov.trunc_arnoldi(np.diag(shift), r, 10, 10)
+    assert out["d_used"] == du_ref == 3
+    # one classical pass
+    N = 32
+    coef, A = _cd(N, 5.0)
+    r = synth.randn(1, N * N)
+    out = skg.trunc_arnoldi_basis(skg.Op.stencil5(N, N, coef), torch.tensor(r, device="cuda"), 8, 2, cgs_passes=1)
+    B_ref, _, _, _ = krylov.trunc_arnoldi(A, r, 8, 2, passes=1)
+    assert np.allclose(out["B"].cpu().numpy()[:, :8], B_ref, atol=1e-10)
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+def test_basis_low_precision_relation(skg, dtype):
+    import torch
+    N, d, k = 128, 30, 2
+    coef, A = _cd(N, 20.0)
+    r = synth.randn(2, N * N)
+    tdt = torch.float32 if dtype == "f32" else torch.bfloat16
+    out = skg.trunc_arnoldi_basis(skg.Op.stencil5(N, N, coef), torch.tensor(r, device="cuda"), d, k, dtype=tdt)
+    B = out["B"].to(torch.float64).cpu().numpy()
+    H = out["Hbar"].cpu().numpy()
+    u = 6e-8 if dtype == "f32" else 4e-3
+    AB = A @ B[:, :d]
+    assert np.linalg.norm(AB - B @ H) <= 50 * u * np.linalg.norm(AB)
+    assert np.allclose(np.linalg.norm(B, axis=0), 1, atol=10 * u)

@@ -1,0 +1,148 @@
+"""GPU parity of restarted sGMRES (Algorithm 1) against the CPU oracle."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import hashing, krylov, operators, sketch
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def skg():
+    import torch
+    assert torch.cuda.is_available(), "GPU test needs CUDA"
+    import paper_2111_00113_gb300 as m
+    return m
+
+
+def _problem(N, Pe, seed):
+    coef = synth.conv_diff_coef(N, Pe)
+    return coef, operators.stencil5_matrix(N, N, coef), synth.randn(seed, N * N)
+
+
+def _relres(A, f, x):
+    return np.linalg.norm(f - A @ x) / np.linalg.norm(f)
+
+
+@pytest.mark.parametrize("kind", ["sparse", "srht"])
+def test_small_workload_fp64(skg, kind):
+    import torch
+    W = synth.WORKLOADS["small"]
+    N = W["N"]
+    coef, A, f = _problem(N, W["Pe"], W["b_seed"])
+    op = skg.Op.stencil5(N, N, coef)
+    b = torch.tensor(f, device="cuda")
+    sk = lambda M: sketch.apply(kind, 7, W["s"], W["zeta"], M)
+    # one cycle from x0 = 0: residual within 1.5x of the oracle's cycle
+    x1, info1 = skg.sgmres_solve(op, b, W["d"], W["k"], W["s"], 1e-300, maxit=1, zeta=W["zeta"], seed=7,
+                                 sketch=kind)
+    xo, _ = krylov.sgmres_cycle(A, f, np.zeros(N * N), W["d"], W["k"], sk)
+    r_gpu = _relres(A, f, x1.cpu().numpy())
+    r_ora = _relres(A, f, xo)
+    assert r_gpu <= 1.5 * r_ora and r_ora <= 1.5 * r_gpu
+    assert info1["relres"] == pytest.approx(r_gpu, rel=1e-8)
+    # full solve to tol
+    x, info = skg.sgmres_solve(op, b, W["d"], W["k"], W["s"], W["tol"], zeta=W["zeta"], seed=7, sketch=kind)
+    _, hist, _ = krylov.sgmres(A, f, np.zeros(N * N), W["d"], W["k"], sk, W["tol"])
+    rel = _relres(A, f, x.cpu().numpy())
+    assert info["status"] == 0
+    assert rel <= W["tol"]
+    assert rel <= 1.5 * max(hist[-1], 1e-300) or info["cycles"] <= len(hist)
+    assert info["cycles"] <= len(hist) + 1
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+def test_small_workload_mixed_precision(skg, dtype):
+    # FP32/BF16 basis with FP64 residual and update: restarts act as
+    # iterative refinement and still reach 1e-8
+    import torch
+    W = synth.WORKLOADS["small"]
+    N = W["N"]
+    coef, A, f = _problem(N, W["Pe"], W["b_seed"])
+    tdt = torch.float32 if dtype == "f32" else torch.bfloat16
+    x, info = skg.sgmres_solve(skg.Op.stencil5(N, N, coef), torch.tensor(f, device="cuda"), W["d"], W["k"], W["s"],
+                               W["tol"], zeta=W["zeta"], seed=7, basis=tdt)
+    assert info["status"] == 0, info
+    assert _relres(A, f, x.cpu().numpy()) <= W["tol"]
+
+
+def test_graph_and_eager_agree(skg):
+    import torch
+    N = 48
+    coef, A, f = _problem(N, 25.0, 3)
+    op = skg.Op.stencil5(N, N, coef)
+    b = torch.tensor(f, device="cuda")
+    xg, ig = skg.sgmres_solve(op, b, 30, 2, 60, 1e-10, use_graph=True)
+    xe, ie = skg.sgmres_solve(op, b, 30, 2, 60, 1e-10, use_graph=False)
+    assert ig["cycles"] == ie["cycles"]
+    assert torch.allclose(xg, xe, rtol=0, atol=1e-12 * xg.abs().max().item())
+
+
+def test_initial_guess_and_zero_rhs(skg):
+    import torch
+    N = 32
+    coef, A, f = _problem(N, 10.0, 4)
+    op = skg.Op.stencil5(N, N, coef)
+    xs = np.linalg.solve(A.toarray(), f)
+    x, info = skg.sgmres_solve(op, torch.tensor(f, device="cuda"), 20, 2, 40, 1e-8,
+                               x0=torch.tensor(xs, device="cuda"))
+    assert info["cycles"] == 0 and info["relres"] <= 1e-8
+    x, info = skg.sgmres_solve(op, torch.zeros(N * N, dtype=torch.float64, device="cuda"), 20, 2, 40, 1e-8)
+    assert info["relres"] == 0 and float(x.abs().max()) == 0.0
+
+
+def test_noconv_returns_best_x(skg):
+    import torch
+    N = 64
+    coef, A, f = _problem(N, 10.0, 0)
+    x, info = skg.sgmres_solve(skg.Op.stencil5(N, N, coef), torch.tensor(f, device="cuda"), 10, 2, 20, 1e-12,
+                               maxit=3)
+    assert info["status"] == 5 and info["cycles"] == 3
+    assert _relres(A, f, x.cpu().numpy()) == pytest.approx(info["relres"], rel=1e-8)
+    with pytest.raises(skg.SkError):
+        skg.sgmres_solve(skg.Op.stencil5(N, N, coef), torch.tensor(f, device="cuda"), 10, 2, 20, 1e-12, maxit=3,
+                         raise_on_noconv=True)
+
+
+def test_exact_when_d_equals_n(skg):
+    # full Arnoldi (k = d = n = 16, the largest supported k): one cycle solves
+    import torch
+    N = 4
+    coef, A, f = _problem(N, 10.0, 0)
+    n = N * N
+    x, info = skg.sgmres_solve(skg.Op.stencil5(N, N, coef), torch.tensor(f, device="cuda"), n, n, 2 * n, 1e-300,
+                               maxit=1, zeta=hashing.default_zeta(n))
+    kA = np.linalg.cond(A.toarray())
+    assert _relres(A, f, x.cpu().numpy()) <= 1e-10 * kA
+
+
+def test_ragged_medium_size(skg):
+    # n = 200*157 (not a multiple of the 2048-row chunk), FP32 basis
+    import torch
+    nx, ny = 200, 157
+    coef = synth.conv_diff_coef(200, 40.0)
+    A = operators.stencil5_matrix(nx, ny, coef)
+    f = synth.randn(5, nx * ny)
+    x, info = skg.sgmres_solve(skg.Op.stencil5(nx, ny, coef), torch.tensor(f, device="cuda"), 60, 2, 120, 1e-6,
+                               basis=torch.float32)
+    assert info["status"] == 0
+    assert _relres(A, f, x.cpu().numpy()) <= 1e-6
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_scale_workload_full_size(skg, dtype):
+    # the benchmark configuration: 1024^2 convection-diffusion, Pe=50,
+    # d=300, k=2, s=600, zeta=12, tol 1e-6.  Checked by the property that
+    # holds at any size: the FP64 residual of the returned x, recomputed on
+    # the CPU from the assembled oracle matrix, is <= tol.
+    import torch
+    W = synth.WORKLOADS["scale"]
+    N = W["N"]
+    coef, A, f = _problem(N, W["Pe"], W["b_seed"])
+    tdt = torch.float64 if dtype == "f64" else torch.float32
+    x, info = skg.sgmres_solve(skg.Op.stencil5(N, N, coef), torch.tensor(f, device="cuda"), W["d"], W["k"], W["s"],
+                               W["tol"], zeta=W["zeta"], seed=7, basis=tdt)
+    assert info["status"] == 0, info
+    assert _relres(A, f, x.cpu().numpy()) <= W["tol"]
+    assert info["cycles"] <= 30
