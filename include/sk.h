@@ -102,6 +102,26 @@ typedef struct {
 sk_status sketch_apply(const sk_sketch* S, const void* B, int64_t ldb, int ncols,
                        sk_dtype dtype, double* SB, void* stream);
 
+/* sketch_apply for the sparse sign sketch without any device allocation.
+ * The paper has no counterpart: this is a deployment variant for callers
+ * that cannot call cudaMalloc on their hot path (plugins inside another
+ * framework's engine, which owns the memory budget and where cudaMalloc can
+ * synchronise the device; latency-critical loops that must not risk an
+ * allocation's cost or an out-of-memory failure mid-run).  Arguments,
+ * layout and results are those of sketch_apply (SK_SPARSE_SIGN only).
+ * Scratch: one file-scope device array of 32 MiB in libsk, held by every GPU
+ * that loads the library until the process exits.  A sketch needing more
+ * (about nchunks*(s+1)*4 + nchunks*2048*zeta*2 + partial sums, nchunks =
+ * ceil(n/2048)) returns SK_EINVAL with the byte count; nothing is launched.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  All calls share the one array and it keeps
+ * the previous call's contents: calls that overlap on the GPU (different
+ * streams, or host threads) race and must be serialised by the caller.
+ * Synchronises `stream` before returning (hash status check). */
+sk_status sketch_apply_noalloc(const sk_sketch* S, const void* B, int64_t ldb, int ncols,
+                               sk_dtype dtype, double* SB, void* stream);
+
 /* ------------------------------------------------------------------------
  * Solver options and diagnostics.
  * ------------------------------------------------------------------------ */

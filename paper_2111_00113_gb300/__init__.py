@@ -133,6 +133,25 @@ def sketch_apply(B, s, zeta=0, seed=7, kind="sparse"):
     return out[:, 0] if vec else out
 
 
+def sketch_apply_noalloc(B, s, zeta=0, seed=7):
+    """sketch_apply (sparse sign) that allocates no device memory.
+
+    For callers that must not allocate on their hot path (e.g. code running
+    inside another framework's engine, which owns the memory budget).  Uses
+    libsk's fixed 32 MiB device scratch array; concurrent calls race.  The
+    output tensor is the caller's to allocate beforehand in real use; this
+    wrapper allocates it with torch for convenience.
+    """
+    vec = B.dim() == 1
+    Bc = colmajor(B)
+    n, c = Bc.shape
+    ldb = Bc.stride(1) if c > 1 else n
+    out = empty_colmajor(s, c, torch.float64, Bc.device)
+    sk = _sketch_struct("sparse", n, s, zeta, seed)
+    N.check(N.lib.sketch_apply_noalloc(C.byref(sk), _ptr(Bc), ldb, c, _DT[Bc.dtype], _ptr(out), _stream()))
+    return out[:, 0] if vec else out
+
+
 def make_opts(basis=torch.float64, sketch="sparse", zeta=0, seed=7, stab_tol=0.0, maxit=10000, cgs_passes=2,
               tau=1e-8, symmetric=False, breakdown=0.0, use_graph=True):
     o = N.SkOpts()

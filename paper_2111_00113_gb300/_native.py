@@ -16,7 +16,7 @@ SK_SPARSE_SIGN, SK_SRHT = 0, 1
 
 EXPORTED = [
     "sk_op_stencil5", "sk_op_diffusion_var", "sk_op_csr", "sk_op_transpose", "sk_op_apply", "sk_op_n",
-    "sk_op_destroy", "sketch_apply", "sk_opts_default", "trunc_arnoldi_basis", "sgmres_solve", "srr_eigs",
+    "sk_op_destroy", "sketch_apply", "sketch_apply_noalloc", "sk_opts_default", "trunc_arnoldi_basis", "sgmres_solve", "srr_eigs",
     "sk_last_error", "sk_status_string",
 ]
 
@@ -63,6 +63,7 @@ def _load():
         "sk_op_n": (I64, [P]),
         "sk_op_destroy": (None, [P]),
         "sketch_apply": (st, [C.POINTER(SkSketch), P, I64, I, I, P, P]),
+        "sketch_apply_noalloc": (st, [C.POINTER(SkSketch), P, I64, I, I, P, P]),
         "sk_opts_default": (None, [C.POINTER(SkOpts)]),
         "trunc_arnoldi_basis": (st, [P, P, I, I, I, P, P, C.POINTER(SkSketch), P, P, C.POINTER(SkOpts),
                                      C.POINTER(I), P]),

@@ -7,6 +7,7 @@
 // combined in FP64 in a second kernel.
 #include <cstdio>
 #include <cmath>
+#include <mutex>
 #include <vector>
 
 #include "common.cuh"
@@ -356,3 +357,90 @@ sk_status sketch_apply_impl(const sk_sketch* S, const void* B, int64_t ldb, int 
 }
 
 }  // namespace sk
+
+// ----------------------------------------------------------------------------
+// sketch_apply_noalloc: the sparse sign sketch without any device allocation.
+//
+// Some callers cannot call cudaMalloc on their hot path: plugins that run
+// inside another framework's execution engine (the host framework owns the
+// device memory budget, and cudaMalloc may synchronise the whole device),
+// and latency-critical loops that must not pay an allocation's variable cost
+// or meet an out-of-memory failure in the middle of a run.  For them this
+// entry point keeps its scratch (the row-sorted index tables and the per-CTA
+// partial sums) in one file-scope device array of fixed size, which every
+// GPU that loads the library holds until the process exits.
+// ----------------------------------------------------------------------------
+namespace sk {
+
+static constexpr size_t kNoAllocScratchBytes = (size_t)32 << 20;  // 32 MiB
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+static size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// Device address of g_noalloc_scratch on the current device, looked up once
+// per device (the host-side name is only a stand-in for the symbol).
+static sk_status noalloc_scratch_ptr(unsigned char** out) {
+  static std::mutex mu;
+  static unsigned char* ptrs[64] = {nullptr};
+  int dev = 0;
+  SK_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) { set_error("sketch_apply_noalloc: device ordinal %d out of range", dev); return SK_EINVAL; }
+  std::lock_guard<std::mutex> lock(mu);
+  if (!ptrs[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
+    ptrs[dev] = (unsigned char*)p;
+  }
+  *out = ptrs[dev];
+  return SK_OK;
+}
+
+}  // namespace sk
+
+extern "C" sk_status sketch_apply_noalloc(const sk_sketch* S, const void* B, int64_t ldb, int ncols, sk_dtype dtype,
+                                          double* SB, void* stream) {
+  using namespace sk;
+  SK_CHECK_ARG(S != nullptr && B != nullptr && SB != nullptr, "NULL argument");
+  SK_CHECK_ARG(S->kind == SK_SPARSE_SIGN, "sketch_apply_noalloc supports the sparse sign sketch only");
+  SK_CHECK_ARG(ncols >= 1, "ncols >= 1");
+  SK_CHECK_ARG(S->n >= 1 && ldb >= S->n, "need n >= 1 and ldb >= n");
+  SK_CHECK_ARG(S->s >= 1 && S->s <= kMaxSparseS, "sparse sign sketch needs 1 <= s <= 4096");
+  SK_CHECK_ARG(dtype == SK_F64 || dtype == SK_F32 || dtype == SK_BF16, "dtype");
+  const int zeta = S->zeta > 0 ? S->zeta : default_zeta_for(S->s / 2);
+  SK_CHECK_ARG(zeta >= 1 && zeta <= 14 && zeta <= S->s, "zeta must be in 1..min(14, s)");
+  cudaStream_t st = (cudaStream_t)stream;
+  SketchPlan p;
+  p.n = S->n;
+  p.s = S->s;
+  p.zeta = zeta;
+  p.seed = S->seed;
+  p.L = kChunk;
+  p.nchunks = (int)((S->n + kChunk - 1) / kChunk);
+  const size_t b_status = align256(sizeof(int));
+  const size_t b_rowptr = align256((size_t)p.nchunks * (p.s + 1) * sizeof(uint32_t));
+  const size_t b_entries = align256((size_t)p.nchunks * kChunk * zeta * sizeof(uint16_t));
+  const size_t b_partial = align256(plan_ws_doubles(p, ncols, dtype) * sizeof(double));
+  const size_t need = b_status + b_rowptr + b_entries + b_partial;
+  if (need > kNoAllocScratchBytes) {
+    set_error("sketch_apply_noalloc: this sketch needs %zu bytes of scratch, above the fixed %zu-byte limit "
+              "(reduce n, zeta or ncols, or use sketch_apply)", need, kNoAllocScratchBytes);
+    return SK_EINVAL;
+  }
+  unsigned char* base = nullptr;
+  SK_TRY(noalloc_scratch_ptr(&base));
+  p.d_status = (int*)base;
+  p.rowptr = (uint32_t*)(base + b_status);
+  p.entries = (uint16_t*)(base + b_status + b_rowptr);
+  double* partial = (double*)(base + b_status + b_rowptr + b_entries);
+  // the status word keeps the previous call's value: clear it; the tables and
+  // partial sums are fully overwritten by this call's kernels
+  SK_CUDA(cudaMemsetAsync(p.d_status, 0, sizeof(int), st));
+  const size_t smem = plan_smem_bytes(p.s, zeta);
+  SK_CUDA(cudaFuncSetAttribute(plan_build_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  plan_build_kernel<<<p.nchunks, kPlanThreads, smem, st>>>(p.n, p.s, zeta, seed_key(p.seed), p.rowptr, p.entries,
+                                                            p.d_status);
+  SK_CUDA(cudaGetLastError());
+  SK_TRY(plan_apply_ws(p, B, ldb, ncols, dtype, SB, partial, st));
+  return check_plan_status(p, st);
+}
