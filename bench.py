@@ -193,7 +193,7 @@ def run_ours(args):
     W, N, coef, f, b = _problem(dev)
     A = skg.Op.stencil5(N, N, coef)
     form = {"f32": torch.float32, "bf16": torch.bfloat16, "f64": torch.float64}[args.form]
-    kw = dict(zeta=W["zeta"], seed=7, basis=form, sketch=args.sketch)
+    kw = dict(zeta=W["zeta"], seed=7, basis=form, sketch=args.sketch, persistent=args.persistent)
     x = torch.zeros_like(b)
 
     def solve(basis=form):
@@ -299,6 +299,7 @@ def run_ours(args):
         "config": {"workload": "scale: 1024x1024 convection-diffusion Pe=50, b~N(0,1) seed 0, d=300, k=2, "
                                "s=600, zeta=12, tol=1e-6",
                    "form": "%s basis/SpMV, FP64 residual/update/QR" % args.form.upper(), "sketch": args.sketch,
+                   "basis_kernel": "persistent" if args.persistent else "3 launches per Arnoldi step",
                    "l2": "inputs larger than L2 (basis %.2f GB per cycle)" % (esz * n * (d + 1) / 1e9),
                    "parallelism": "replicas" if ws > 1 else "single GPU"},
         "converged": ok, "cycles": cycles, "relres": last["relres"],
@@ -338,6 +339,7 @@ def main():
     ap.add_argument("--plain-steps", type=int, default=2)
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-baseline", action="store_true")
+    ap.add_argument("--persistent", action="store_true", help="one cooperative kernel per basis build")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

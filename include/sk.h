@@ -136,7 +136,9 @@ typedef struct {
   double tau;              /* sRR convergence tolerance for nconv (default 1e-8) */
   int symmetric;           /* sRR: keep real parts of lambda and x (§6.8) */
   double breakdown;        /* ||w_j|| <= breakdown*||A b_{j-1}|| ends the basis; <=0 = 1e-13 (F64) / 1e-6 */
-  int use_graph;           /* capture the basis loop in a CUDA graph (default 1) */
+  int use_graph;           /* capture each restart cycle in a CUDA graph (default 1) */
+  int persistent;          /* grid operators: build the basis in one cooperative kernel
+                              with bounded grid barriers (1), or 3 launches per step (0, default) */
 } sk_opts;
 
 void sk_opts_default(sk_opts* o);

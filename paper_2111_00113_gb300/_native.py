@@ -29,7 +29,7 @@ class SkOpts(C.Structure):
     _fields_ = [
         ("sketch", C.c_int), ("zeta", C.c_int), ("seed", C.c_uint64), ("stab_tol", C.c_double),
         ("maxit", C.c_int), ("basis", C.c_int), ("cgs_passes", C.c_int), ("tau", C.c_double),
-        ("symmetric", C.c_int), ("breakdown", C.c_double), ("use_graph", C.c_int),
+        ("symmetric", C.c_int), ("breakdown", C.c_double), ("use_graph", C.c_int), ("persistent", C.c_int),
     ]
 
 

@@ -115,6 +115,7 @@ void sk_opts_default(sk_opts* o) {
   o->symmetric = 0;
   o->breakdown = 0;
   o->use_graph = 1;
+  o->persistent = 0;
 }
 
 static sk_op* new_op() {

@@ -9,14 +9,20 @@
 //              nu_j = sqrt(||w||^2 - ||h2||^2)   (W_j is orthonormal: its
 //              vectors were orthogonalised against each other, |i-j| < k)
 //   form(j+1): b_{j+1} = (A b_j - W_j (h1 + h2)) / nu_j
-// m = A b_j is recomputed from the stored b_j in each pass instead of being
-// stored: a 5-point product costs less than writing and re-reading a vector.
+// With an FP32/BF16 basis, m = A b_j is recomputed from the stored b_j in
+// each pass (a 5-point product costs less than writing and re-reading a
+// vector).  With an FP64 basis the FP64 pipe is the bound on this part, so
+// dots1 stores m once (FP64) and the other passes read it.
 // The Arnoldi coefficients are kept: A b_j = sum_q (h1+h2)_q b_{j-q} +
 // nu_j b_{j+1}, i.e. AB_d = B_{d+1} Hbar with Hbar (d+1) x d, k+1 diagonals.
+//
+// Constant-coefficient stencils on grids with nx % 4 == 0 take a vector
+// path: each thread handles 4 consecutive cells of one grid row with 16-byte
+// loads; everything else takes the scalar path.
 #include <cmath>
 
-#include "common.cuh"
 #include "basis.cuh"
+#include "common.cuh"
 
 namespace sk {
 
@@ -25,18 +31,113 @@ __device__ __forceinline__ T* bcol(void* B, int64_t ldb, int c) {
   return (T*)B + (int64_t)c * ldb;
 }
 
-template <typename T, int KM>
+// ---- groups of G consecutive elements ---------------------------------------
+template <typename C>
+__device__ __forceinline__ void ld4(const float* p, C (&v)[4]) {
+  const float4 t = *reinterpret_cast<const float4*>(p);
+  v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+}
+template <typename C>
+__device__ __forceinline__ void ld4(const double* p, C (&v)[4]) {
+  const double2 a = *reinterpret_cast<const double2*>(p);
+  const double2 b = *reinterpret_cast<const double2*>(p + 2);
+  v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+template <typename C>
+__device__ __forceinline__ void ld4(const __nv_bfloat16* p, C (&v)[4]) {
+  const uint2 u = *reinterpret_cast<const uint2*>(p);
+  const __nv_bfloat162 a = *reinterpret_cast<const __nv_bfloat162*>(&u.x);
+  const __nv_bfloat162 b = *reinterpret_cast<const __nv_bfloat162*>(&u.y);
+  const float2 fa = __bfloat1622float2(a), fb = __bfloat1622float2(b);
+  v[0] = fa.x; v[1] = fa.y; v[2] = fb.x; v[3] = fb.y;
+}
+__device__ __forceinline__ void st4(float* p, const float (&v)[4]) {
+  *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void st4(double* p, const double (&v)[4]) {
+  *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
+  *reinterpret_cast<double2*>(p + 2) = make_double2(v[2], v[3]);
+}
+__device__ __forceinline__ void st4(__nv_bfloat16* p, const float (&v)[4]) {
+  uint2 u;
+  *reinterpret_cast<__nv_bfloat162*>(&u.x) = __floats2bfloat162_rn(v[0], v[1]);
+  *reinterpret_cast<__nv_bfloat162*>(&u.y) = __floats2bfloat162_rn(v[2], v[3]);
+  *reinterpret_cast<uint2*>(p) = u;
+}
+
+template <int G, typename T, typename C>
+__device__ __forceinline__ void gload(const T* p, int64_t i, C (&v)[G]) {
+  if constexpr (G == 4) ld4(p + i, v);
+  else v[0] = to_c(p[i]);
+}
+template <int G, typename T, typename C>
+__device__ __forceinline__ void gstore(T* p, int64_t i, const C (&v)[G]) {
+  if constexpr (G == 4) st4(p + i, v);
+  else p[i] = from_c<T>(v[0]);
+}
+
+// m[0..G) = (A x)[i0..i0+G); G = 4 only for constant-coefficient stencils
+// with nx % 4 == 0 (the 4 cells share one grid row).
+template <int G, typename T, typename C>
+__device__ __forceinline__ void op_apply(const OpView<C>& A, const T* __restrict__ x, int64_t i0, C (&m)[G]) {
+  if constexpr (G == 4) {
+    const int ii = (int)i0;
+    const int iy = ii / A.nx;
+    const int ix0 = ii - iy * A.nx;
+    C xc[4], up[4], dn[4];
+    ld4(x + i0, xc);
+    const C w = ix0 > 0 ? to_c(x[i0 - 1]) : (C)0;
+    const C e = ix0 + 4 < A.nx ? to_c(x[i0 + 4]) : (C)0;
+    if (iy + 1 < A.ny) ld4(x + i0 + A.nx, up);
+    else up[0] = up[1] = up[2] = up[3] = 0;
+    if (iy > 0) ld4(x + i0 - A.nx, dn);
+    else dn[0] = dn[1] = dn[2] = dn[3] = 0;
+    m[0] = A.cP * xc[0] + A.cE * xc[1] + A.cW * w + A.cN * up[0] + A.cS * dn[0];
+    m[1] = A.cP * xc[1] + A.cE * xc[2] + A.cW * xc[0] + A.cN * up[1] + A.cS * dn[1];
+    m[2] = A.cP * xc[2] + A.cE * xc[3] + A.cW * xc[1] + A.cN * up[2] + A.cS * dn[2];
+    m[3] = A.cP * xc[3] + A.cE * e + A.cW * xc[2] + A.cN * up[3] + A.cS * dn[3];
+    if (A.shift) {
+      C sh[4];
+      ld4(A.shift + i0, sh);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) m[q] += sh[q] * xc[q];
+    }
+  } else {
+    m[0] = A.apply(x, i0);
+  }
+}
+
+// Final reduction in the last block: thread t sums blocks t, t+T, ... (fixed
+// assignment), then a fixed-order block reduction.  Result in thread 0.
+template <int K>
+__device__ __forceinline__ void reduce_partials(const double* part, int nblocks, double (&tot)[K], double* sh) {
+#pragma unroll
+  for (int q = 0; q < K; ++q) tot[q] = 0;
+  for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
+#pragma unroll
+    for (int q = 0; q < K; ++q) tot[q] += __ldcg(part + b * K + q);
+  }
+  block_sum_k<K>(tot, sh);
+}
+
+// ---- kernels ------------------------------------------------------------------
+template <typename T, int KM, int G, bool STORE_M>
 __global__ void __launch_bounds__(kBasisThreads)
 form_kernel(BasisParams p, OpView<typename Compute<T>::type> A, int c) {
   using C = typename Compute<T>::type;
   if (c >= *p.stop) return;
   T* out = bcol<T>(p.B, p.ldb, c);
   const int64_t n = p.n;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  const int64_t i_begin = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x * G;
+  const int64_t i_begin = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * G;
   if (c == 0) {
     const double inv = 1.0 / sqrt(*p.rho2);
-    for (int64_t i = i_begin; i < n; i += stride) out[i] = from_c<T>((C)(p.r[i] * inv));
+    for (int64_t i = i_begin; i < n; i += stride) {
+      C v[G];
+#pragma unroll
+      for (int q = 0; q < G; ++q) v[q] = (C)(p.r[i + q] * inv);
+      gstore<G>(out, i, v);
+    }
     return;
   }
   const int j = c - 1;
@@ -47,20 +148,32 @@ form_kernel(BasisParams p, OpView<typename Compute<T>::type> A, int c) {
   const C inv = (C)(1.0 / p.nu[j]);
   const T* bj = bcol<T>(p.B, p.ldb, j);
   for (int64_t i = i_begin; i < n; i += stride) {
-    C m = A.apply(bj, i);
+    C m[G];
+    if constexpr (STORE_M) gload<G>(p.M, i, m);
+    else op_apply<G>(A, bj, i, m);
 #pragma unroll
-    for (int q = 0; q < KM; ++q)
-      if (q < kw) m -= h[q] * to_c(bcol<T>(p.B, p.ldb, j - q)[i]);
-    out[i] = from_c<T>(m * inv);
+    for (int q = 0; q < KM; ++q) {
+      if (q < kw) {
+        C bw[G];
+        gload<G>(bcol<T>(p.B, p.ldb, j - q), i, bw);
+#pragma unroll
+        for (int e = 0; e < G; ++e) m[e] -= h[q] * bw[e];
+      }
+    }
+#pragma unroll
+    for (int e = 0; e < G; ++e) m[e] *= inv;
+    gstore<G>(out, i, m);
   }
 }
 
-// pass = 1: dots with m;  pass = 2: dots with w = m - W h1.
-template <typename T, int KM, int PASS>
+// PASS = 1: dots with m (and m stored if STORE_M);  PASS = 2: dots with
+// w = m - W h1.
+template <typename T, int KM, int G, bool STORE_M, int PASS>
 __global__ void __launch_bounds__(kBasisThreads)
 dots_kernel(BasisParams p, OpView<typename Compute<T>::type> A, int j) {
   using C = typename Compute<T>::type;
   __shared__ C red[(KM + 1) * (kBasisThreads / 32)];
+  __shared__ double redd[(KM + 1) * (kBasisThreads / 32)];
   if (j >= *p.stop) return;
   const int kw = min(p.k, j + 1);
   const int64_t n = p.n;
@@ -73,19 +186,40 @@ dots_kernel(BasisParams p, OpView<typename Compute<T>::type> A, int j) {
   C acc[KM + 1];
 #pragma unroll
   for (int q = 0; q <= KM; ++q) acc[q] = 0;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride) {
-    C m = A.apply(bj, i);
-    C bw[KM];
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x * G;
+  for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * G; i < n; i += stride) {
+    C m[G];
+    if (STORE_M && PASS == 2) gload<G>(p.M, i, m);
+    else op_apply<G>(A, bj, i, m);
+    if (STORE_M && PASS == 1) {
+      double md[G];
 #pragma unroll
-    for (int q = 0; q < KM; ++q) bw[q] = (q < kw) ? to_c(bcol<T>(p.B, p.ldb, j - q)[i]) : (C)0;
+      for (int e = 0; e < G; ++e) md[e] = (double)m[e];
+      gstore<G>(p.M, i, md);
+    }
+    C bw[KM][G];
+#pragma unroll
+    for (int q = 0; q < KM; ++q) {
+      if (q < kw) gload<G>(bcol<T>(p.B, p.ldb, j - q), i, bw[q]);
+      else {
+#pragma unroll
+        for (int e = 0; e < G; ++e) bw[q][e] = 0;
+      }
+    }
     if (PASS == 2) {
 #pragma unroll
-      for (int q = 0; q < KM; ++q) m -= h[q] * bw[q];
+      for (int q = 0; q < KM; ++q) {
+#pragma unroll
+        for (int e = 0; e < G; ++e) m[e] -= h[q] * bw[q][e];
+      }
     }
 #pragma unroll
-    for (int q = 0; q < KM; ++q) acc[q] += bw[q] * m;
-    acc[KM] += m * m;
+    for (int q = 0; q < KM; ++q) {
+#pragma unroll
+      for (int e = 0; e < G; ++e) acc[q] += bw[q][e] * m[e];
+    }
+#pragma unroll
+    for (int e = 0; e < G; ++e) acc[KM] += m[e] * m[e];
   }
   block_sum_k<KM + 1>(acc, red);
   double* part = p.partial;
@@ -94,11 +228,9 @@ dots_kernel(BasisParams p, OpView<typename Compute<T>::type> A, int j) {
     for (int q = 0; q <= KM; ++q) part[blockIdx.x * (KM + 1) + q] = (double)acc[q];
   }
   if (!last_block_arrived(p.counters + (PASS - 1))) return;
-  if (threadIdx.x != 0) return;
   double tot[KM + 1];
-  for (int q = 0; q <= KM; ++q) tot[q] = 0;
-  for (int b = 0; b < (int)gridDim.x; ++b)
-    for (int q = 0; q <= KM; ++q) tot[q] += __ldcg(part + b * (KM + 1) + q);
+  reduce_partials<KM + 1>(part, (int)gridDim.x, tot, redd);
+  if (threadIdx.x != 0) return;
   if (PASS == 1) {
     for (int q = 0; q < kw; ++q) p.h1[j * p.k + q] = tot[q];
     p.mn2[j] = tot[KM];
@@ -130,31 +262,36 @@ dots_kernel(BasisParams p, OpView<typename Compute<T>::type> A, int j) {
   if (brk) *p.stop = j + 1;
 }
 
-template <typename T, int KM>
-static sk_status enqueue_basis_t(const BasisParams& p, const OpView<typename Compute<T>::type>& A,
-                                 cudaStream_t st) {
+template <typename T, int KM, int G, bool SM>
+static sk_status enqueue_basis_t(const BasisParams& p, const OpView<typename Compute<T>::type>& A, cudaStream_t st) {
   const int g = p.nblk;
-  form_kernel<T, KM><<<g, kBasisThreads, 0, st>>>(p, A, 0);
+  form_kernel<T, KM, G, SM><<<g, kBasisThreads, 0, st>>>(p, A, 0);
   for (int j = 0; j < p.d; ++j) {
-    dots_kernel<T, KM, 1><<<g, kBasisThreads, 0, st>>>(p, A, j);
-    if (p.passes == 2) dots_kernel<T, KM, 2><<<g, kBasisThreads, 0, st>>>(p, A, j);
-    form_kernel<T, KM><<<g, kBasisThreads, 0, st>>>(p, A, j + 1);
+    dots_kernel<T, KM, G, SM, 1><<<g, kBasisThreads, 0, st>>>(p, A, j);
+    if (p.passes == 2) dots_kernel<T, KM, G, SM, 2><<<g, kBasisThreads, 0, st>>>(p, A, j);
+    form_kernel<T, KM, G, SM><<<g, kBasisThreads, 0, st>>>(p, A, j + 1);
   }
   SK_CUDA(cudaGetLastError());
   return SK_OK;
 }
 
-template <typename T, typename C>
+template <typename T, int G, bool SM, typename C>
 static sk_status enqueue_basis_k(const BasisParams& p, const OpView<C>& A, cudaStream_t st) {
-  if (p.k <= 2) return enqueue_basis_t<T, 2>(p, A, st);
-  if (p.k <= 4) return enqueue_basis_t<T, 4>(p, A, st);
-  if (p.k <= 8) return enqueue_basis_t<T, 8>(p, A, st);
-  return enqueue_basis_t<T, 16>(p, A, st);
+  if (p.k <= 2) return enqueue_basis_t<T, 2, G, SM>(p, A, st);
+  if (p.k <= 4) return enqueue_basis_t<T, 4, G, SM>(p, A, st);
+  if (p.k <= 8) return enqueue_basis_t<T, 8, G, SM>(p, A, st);
+  return enqueue_basis_t<T, 16, G, SM>(p, A, st);
+}
+
+bool basis_vector_path(const sk_op* op, int64_t ldb, const void* B) {
+  return op->kind == OP_STENCIL5 && op->nx % 4 == 0 && ldb % 8 == 0 && op->n < (1ll << 31) &&
+         ((uintptr_t)B % 16) == 0;
 }
 
 int basis_grid(int64_t n) {
-  int64_t g = (n + kBasisThreads * 4 - 1) / (kBasisThreads * 4);
-  const int64_t gmax = 2 * num_sms();
+  // about 2 groups of 4 elements per thread; at most 8 CTAs per SM
+  int64_t g = (n + kBasisThreads * 8 - 1) / (kBasisThreads * 8);
+  const int64_t gmax = 8 * num_sms();
   if (g > gmax) g = gmax;
   if (g < 1) g = 1;
   return (int)g;
@@ -162,15 +299,18 @@ int basis_grid(int64_t n) {
 
 sk_status enqueue_basis(const BasisParams& p, const sk_op* op, cudaStream_t st) {
   if (p.k > kMaxK) { set_error("k <= %d supported", kMaxK); return SK_EINVAL; }
+  const bool vec = basis_vector_path(op, p.ldb, p.B) && (p.r == nullptr || ((uintptr_t)p.r % 16) == 0);
   if (p.dtype == SK_F64) {
     OpView<double> A;
     make_view(op, &A);
-    return enqueue_basis_k<double>(p, A, st);
+    if (!p.M) { set_error("FP64 basis needs the m workspace"); return SK_EINVAL; }
+    return vec ? enqueue_basis_k<double, 4, true>(p, A, st) : enqueue_basis_k<double, 1, true>(p, A, st);
   }
   OpView<float> A;
   SK_TRY(make_view(op, &A, st));
-  if (p.dtype == SK_F32) return enqueue_basis_k<float>(p, A, st);
-  return enqueue_basis_k<__nv_bfloat16>(p, A, st);
+  if (p.dtype == SK_F32)
+    return vec ? enqueue_basis_k<float, 4, false>(p, A, st) : enqueue_basis_k<float, 1, false>(p, A, st);
+  return vec ? enqueue_basis_k<__nv_bfloat16, 4, false>(p, A, st) : enqueue_basis_k<__nv_bfloat16, 1, false>(p, A, st);
 }
 
 }  // namespace sk

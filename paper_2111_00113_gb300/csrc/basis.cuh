@@ -18,6 +18,7 @@ struct BasisParams {
   double* nu;         // d: ||w_{j+1}||
   double* mn2;        // d: ||A b_j||^2
   double* Hbar;       // (d+1) x d or NULL (zeroed by the caller)
+  double* M;          // n: A b_j in FP64 (FP64 basis only; NULL otherwise)
   double* partial;    // nblk x (kMaxK+1) per-CTA partial sums
   unsigned* counters; // 2 last-block counters (zero)
   int* stop;          // valid basis columns (init d+1; lowered on breakdown)
@@ -28,7 +29,19 @@ struct BasisParams {
   int nblk;           // CTAs per pass
 };
 
+// Workspace of the persistent (cooperative) basis kernel.
+struct PersistWork {
+  unsigned* bar;         // 2: barrier count and generation (reset before each launch)
+  int* err;              // SK_ETIMEOUT if a grid barrier gave up
+  double* part;          // 2 x grid x (kMaxK+1) partial sums
+  long long spin_limit;  // barrier spin iterations before giving up
+};
+
+bool persist_shape(const sk_op* op, sk_dtype dt, int* grid, int* ept, size_t* smem);
+sk_status enqueue_basis_persistent(const BasisParams& bp, const sk_op* op, PersistWork& w, cudaStream_t st);
+
 int basis_grid(int64_t n);
+bool basis_vector_path(const sk_op* op, int64_t ldb, const void* B);
 sk_status enqueue_basis(const BasisParams& p, const sk_op* op, cudaStream_t st);
 
 }  // namespace sk

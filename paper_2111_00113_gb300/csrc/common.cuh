@@ -34,6 +34,12 @@ sk_status cuda_fail(cudaError_t e, const char* what);
     if (!(cond)) { ::sk::set_error("invalid argument: %s", msg); return SK_EINVAL; } \
   } while (0)
 
+// Opt-in dynamic shared memory limit set on every kernel that uses more than
+// 48 KB.  One fixed value (not the size of a particular launch): a captured
+// graph keeps its launches' sizes while the attribute is per function, so
+// the attribute must cover every launch of the function.
+static constexpr int kDynSmemLimit = 200 * 1024;
+
 inline int num_sms() {
   static int n = 0;
   if (n == 0) {

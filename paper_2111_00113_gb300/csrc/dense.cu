@@ -59,9 +59,10 @@ __device__ __forceinline__ double block_sum1(double v, double* sh) {
   return a;
 }
 
-// One CTA factors panel columns [p0, p0+nbc) of Aug (s rows, ld s).
+// One CTA factors panel columns [p0, p0+nbc) of Aug (s rows, ld s) in place
+// in global memory (fallback for panels too tall for shared memory).
 __global__ void __launch_bounds__(kQrPanelThreads)
-qr_panel_kernel(double* __restrict__ Aug, int s, int p0, int nbc, double* __restrict__ rdiag,
+qr_panel_global_kernel(double* __restrict__ Aug, int s, int p0, int nbc, double* __restrict__ rdiag,
                 double* __restrict__ tau, double* __restrict__ Tws) {
   __shared__ double sh[32];
   __shared__ double s_tau[kQrNb];
@@ -125,6 +126,88 @@ qr_panel_kernel(double* __restrict__ Aug, int s, int p0, int nbc, double* __rest
   for (int q = threadIdx.x; q < kQrNb * kQrNb; q += blockDim.x) Tws[q] = s_T[q];
 }
 
+// One CTA factors panel columns [p0, p0+nbc) of Aug: the panel's rows p0..s-1
+// are staged in shared memory, factored column by column (norm, reflector,
+// dots of all remaining panel columns in parallel, rank-1 update by the
+// whole block), and written back with the compact-WY factor T.
+__global__ void __launch_bounds__(kQrPanelThreads)
+qr_panel_kernel(double* __restrict__ Aug, int s, int p0, int nbc, double* __restrict__ rdiag,
+                double* __restrict__ tau, double* __restrict__ Tws) {
+  extern __shared__ double P[];  // len x nbc, column-major, ld = len
+  __shared__ double sh[32];
+  __shared__ double s_tau[kQrNb];
+  __shared__ double s_dot[kQrNb];
+  __shared__ double s_T[kQrNb * kQrNb];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int len = s - p0;
+  for (int q = threadIdx.x; q < len * nbc; q += blockDim.x) {
+    const int c = q / len, r = q - c * len;
+    P[q] = Aug[(int64_t)(p0 + c) * s + p0 + r];
+  }
+  __syncthreads();
+  for (int jj = 0; jj < nbc; ++jj) {
+    double* v = P + (int64_t)jj * len;
+    double part = 0;
+    for (int r = jj + threadIdx.x; r < len; r += blockDim.x) part += v[r] * v[r];
+    const double nrm2 = block_sum1(part, sh);
+    const double x0 = v[jj];
+    const double nrm = sqrt(nrm2);
+    const double alpha = (x0 >= 0) ? -nrm : nrm;
+    const double v0 = x0 - alpha;
+    const double vtv = nrm2 - x0 * x0 + v0 * v0;
+    const double t = (vtv > 0) ? 2.0 / vtv : 0.0;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      v[jj] = v0;
+      rdiag[p0 + jj] = (vtv > 0) ? alpha : x0;
+      tau[p0 + jj] = t;
+      s_tau[jj] = t;
+    }
+    __syncthreads();
+    for (int c = jj + 1 + wid; c < nbc; c += nw) {
+      const double* y = P + (int64_t)c * len;
+      double dot = 0;
+      for (int r = jj + lane; r < len; r += 32) dot += v[r] * y[r];
+      dot = warp_sum(dot);
+      if (lane == 0) s_dot[c] = dot * t;
+    }
+    __syncthreads();
+    const int rows = len - jj, cols = nbc - jj - 1;
+    for (int q = threadIdx.x; q < rows * cols; q += blockDim.x) {
+      const int c = jj + 1 + q / rows, r = jj + q % rows;
+      P[(int64_t)c * len + r] -= s_dot[c] * v[r];
+    }
+    __syncthreads();
+  }
+  for (int q = threadIdx.x; q < kQrNb * kQrNb; q += blockDim.x) s_T[q] = 0;
+  __syncthreads();
+  for (int jj = 0; jj < nbc; ++jj) {
+    const double* vj = P + (int64_t)jj * len;
+    for (int i = wid; i < jj; i += nw) {
+      const double* vi = P + (int64_t)i * len;
+      double dot = 0;
+      for (int r = jj + lane; r < len; r += 32) dot += vi[r] * vj[r];
+      dot = warp_sum(dot);
+      if (lane == 0) sh[i] = dot;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int i = 0; i < jj; ++i) {
+        double a = 0;
+        for (int l = i; l < jj; ++l) a += s_T[i * kQrNb + l] * sh[l];
+        s_T[i * kQrNb + jj] = -s_tau[jj] * a;
+      }
+      s_T[jj * kQrNb + jj] = s_tau[jj];
+    }
+    __syncthreads();
+  }
+  for (int q = threadIdx.x; q < kQrNb * kQrNb; q += blockDim.x) Tws[q] = s_T[q];
+  for (int q = threadIdx.x; q < len * nbc; q += blockDim.x) {
+    const int c = q / len, r = q - c * len;
+    Aug[(int64_t)(p0 + c) * s + p0 + r] = P[q];
+  }
+}
+
 // Column c = c0 + blockIdx.x of Aug gets Q_p^T: a <- a - V T^T (V^T a).
 __global__ void __launch_bounds__(kQrTrailThreads)
 qr_trailing_kernel(double* __restrict__ Aug, int s, int p0, int nbc, int c0, const double* __restrict__ Tws) {
@@ -167,7 +250,13 @@ sk_status enqueue_qr(double* Aug, int s, int nq, int ncols, double* rdiag, doubl
   for (int p0 = 0; p0 < nq; p0 += kQrNb) {
     const int nbc = (nq - p0) < kQrNb ? (nq - p0) : kQrNb;
     double* T = Tws + (int64_t)(p0 / kQrNb) * kQrNb * kQrNb;
-    qr_panel_kernel<<<1, kQrPanelThreads, 0, st>>>(Aug, s, p0, nbc, rdiag, tau, T);
+    const size_t smem = (size_t)(s - p0) * nbc * sizeof(double);
+    if (smem <= 200 * 1024) {
+      SK_CUDA(cudaFuncSetAttribute(qr_panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kDynSmemLimit));
+      qr_panel_kernel<<<1, kQrPanelThreads, smem, st>>>(Aug, s, p0, nbc, rdiag, tau, T);
+    } else {
+      qr_panel_global_kernel<<<1, kQrPanelThreads, 0, st>>>(Aug, s, p0, nbc, rdiag, tau, T);
+    }
     const int c0 = p0 + nbc;
     if (ncols > c0) qr_trailing_kernel<<<ncols - c0, kQrTrailThreads, 0, st>>>(Aug, s, p0, nbc, c0, T);
   }
@@ -178,13 +267,17 @@ sk_status enqueue_qr(double* Aug, int s, int nq, int ncols, double* rdiag, doubl
 // Back substitution for the sketched LS with the kappa truncation.
 // Aug: R above the diagonal of columns [0, d), rdiag its diagonal; column d
 // holds Q^T g.  Writes y (d, zero past width) and diag = {rhat, kappa, width}.
+// Blocked from the bottom: for each block of 32 unknowns, warp 0 solves the
+// 32 x 32 triangle from shared memory with shuffles, then the whole CTA
+// subtracts the block's contribution from the rows above it.
 __global__ void __launch_bounds__(1024)
 ls_solve_kernel(const double* __restrict__ Aug, const double* __restrict__ rdiag, int s, int d, double stab_tol,
                 double* __restrict__ y, double* __restrict__ diag) {
-  extern __shared__ double zz[];  // d
+  extern __shared__ double zz[];  // d right-hand side entries, then the 32 x d block of R
+  double* Rb = zz + d;             // Rb[c * d + t] = R[t, i0 + c]
   __shared__ double sh[32];
   __shared__ int s_width;
-  __shared__ double s_kappa, s_yi;
+  __shared__ double s_kappa;
   const double* z = Aug + (int64_t)d * s;
   if (threadIdx.x == 0) {
     double mx = 0, mn = INFINITY, kap = 1.0;
@@ -198,7 +291,6 @@ ls_solve_kernel(const double* __restrict__ Aug, const double* __restrict__ rdiag
       if (kap > stab_tol) break;
       width = j + 1;
     }
-    // full-basis estimate for reporting (inf if a column vanished)
     double mxa = 0, mna = INFINITY;
     for (int j = 0; j < d; ++j) { const double a = fabs(rdiag[j]); mxa = fmax(mxa, a); mna = fmin(mna, a); }
     s_kappa = (mna > 0) ? mxa / mna : INFINITY;
@@ -211,13 +303,34 @@ ls_solve_kernel(const double* __restrict__ Aug, const double* __restrict__ rdiag
   for (int i = width + threadIdx.x; i < s; i += blockDim.x) part += z[i] * z[i];
   const double rh2 = block_sum1(part, sh);
   __syncthreads();
-  for (int i = width - 1; i >= 0; --i) {
-    if (threadIdx.x == 0) s_yi = zz[i] / rdiag[i];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int i1 = width; i1 > 0; i1 -= 32) {
+    const int i0 = max(0, i1 - 32);
+    const int nb = i1 - i0;
+    // stage R[0:i1, i0:i1]
+    for (int q = threadIdx.x; q < nb * i1; q += blockDim.x) {
+      const int c = q / i1, t = q - c * i1;
+      Rb[c * d + t] = (t == i0 + c) ? rdiag[i0 + c] : Aug[(int64_t)(i0 + c) * s + t];
+    }
     __syncthreads();
-    const double yi = s_yi;
-    const double* Ri = Aug + (int64_t)i * s;
-    for (int t = threadIdx.x; t < i; t += blockDim.x) zz[t] -= yi * Ri[t];
-    if (threadIdx.x == 0) zz[i] = yi;
+    if (wid == 0) {
+      // lane l holds unknown i0 + l; solve bottom-up within the block
+      double zl = (lane < nb) ? zz[i0 + lane] : 0.0;
+      double yl = 0.0;
+      for (int c = nb - 1; c >= 0; --c) {
+        const double yc = __shfl_sync(0xffffffffu, zl, c) / Rb[c * d + i0 + c];
+        if (lane == c) yl = yc;
+        if (lane < c) zl -= yc * Rb[c * d + i0 + lane];
+      }
+      if (lane < nb) zz[i0 + lane] = yl;
+    }
+    __syncthreads();
+    // rows above the block: zz[t] -= sum_c R[t, i0+c] y[i0+c]
+    for (int t = threadIdx.x; t < i0; t += blockDim.x) {
+      double a = zz[t];
+      for (int c = 0; c < nb; ++c) a -= Rb[c * d + t] * zz[i0 + c];
+      zz[t] = a;
+    }
     __syncthreads();
   }
   for (int i = threadIdx.x; i < d; i += blockDim.x) y[i] = (i < width) ? zz[i] : 0.0;
@@ -230,8 +343,9 @@ ls_solve_kernel(const double* __restrict__ Aug, const double* __restrict__ rdiag
 
 sk_status enqueue_ls_solve(const double* Aug, const double* rdiag, int s, int d, double stab_tol, double* y,
                            double* diag, cudaStream_t st) {
-  const size_t smem = (size_t)d * sizeof(double);
-  SK_CUDA(cudaFuncSetAttribute(ls_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const size_t smem = (size_t)d * 33 * sizeof(double);
+  if (smem > (size_t)kDynSmemLimit) { set_error("ls_solve: d too large"); return SK_EINVAL; }
+  SK_CUDA(cudaFuncSetAttribute(ls_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kDynSmemLimit));
   ls_solve_kernel<<<1, 1024, smem, st>>>(Aug, rdiag, s, d, stab_tol, y, diag);
   SK_CUDA(cudaGetLastError());
   return SK_OK;

@@ -137,7 +137,7 @@ sk_status plan_create(SketchPlan* p, const sk_sketch* S, Scratch& scratch, cudaS
   SK_TRY(scratch.alloc(&p->d_status, 1));
   SK_CUDA(cudaMemsetAsync(p->d_status, 0, sizeof(int), st));
   const size_t smem = plan_smem_bytes(p->s, zeta);
-  SK_CUDA(cudaFuncSetAttribute(plan_build_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  SK_CUDA(cudaFuncSetAttribute(plan_build_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kDynSmemLimit));
   plan_build_kernel<<<p->nchunks, kPlanThreads, smem, st>>>(p->n, p->s, zeta, seed_key(p->seed), p->rowptr,
                                                               p->entries, p->d_status);
   SK_CUDA(cudaGetLastError());
@@ -145,12 +145,15 @@ sk_status plan_create(SketchPlan* p, const sk_sketch* S, Scratch& scratch, cudaS
 }
 
 // ----------------------------------------------------------------------------
-// Gather apply: grid (column tiles, chunk groups).  Each group of G lanes
-// owns one sketch row at a time; partial row sums are reduced inside the
-// group by shuffles and added to the CTA's accumulator (Kahan-compensated for
-// FP32, plain for FP64), which only that group touches.
+// Gather apply: grid (column tiles, chunk groups).  For each chunk the CTA
+// stages the data tile (kChunk rows x W columns), the chunk's row-sorted
+// entries and its row offsets in shared memory; then each group of G lanes
+// owns one sketch row at a time, sums +-tile[local] over the row's entries,
+// reduces inside the group by shuffles and adds the result to the CTA's
+// accumulator for that row (Kahan-compensated), which only that group
+// touches.
 // ----------------------------------------------------------------------------
-static constexpr int kApplyThreads = 256;
+static constexpr int kApplyThreads = 512;
 static constexpr int kGroup = 8;  // lanes per sketch row
 
 template <typename C>
@@ -163,6 +166,9 @@ struct KahanAcc {
   }
 };
 
+__host__ __device__ static inline size_t entries_bytes(int zeta) { return (((size_t)kChunk * zeta * sizeof(uint16_t)) + 15) & ~(size_t)15; }
+__host__ __device__ static inline size_t rowptr_bytes(int s) { return (((size_t)(s + 1) * sizeof(uint32_t)) + 15) & ~(size_t)15; }
+
 template <typename T, int W>
 __global__ void __launch_bounds__(kApplyThreads)
 gather_apply_kernel(const T* __restrict__ B, int64_t ldb, int ncols, int64_t n, int s, int zeta, int nchunks,
@@ -170,9 +176,11 @@ gather_apply_kernel(const T* __restrict__ B, int64_t ldb, int ncols, int64_t n, 
                     double* __restrict__ partial) {
   using C = typename Compute<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* tile = (C*)smem_raw;            // kChunk * W
-  C* acc_hi = tile + kChunk * W;     // s * W
-  C* acc_lo = acc_hi + (size_t)s * W;  // s * W (Kahan compensation)
+  C* tile = (C*)smem_raw;                                                     // kChunk * W
+  uint16_t* ent_s = (uint16_t*)(smem_raw + (size_t)kChunk * W * sizeof(C));  // kChunk * zeta
+  uint32_t* rp_s = (uint32_t*)((unsigned char*)ent_s + entries_bytes(zeta)); // s + 1
+  C* acc_hi = (C*)((unsigned char*)rp_s + rowptr_bytes(s));                   // s * W
+  C* acc_lo = acc_hi + (size_t)s * W;                                         // s * W
   const int col0 = blockIdx.x * W;
   const int g = blockIdx.y;
   const int c_begin = g * chunks_per_group;
@@ -180,11 +188,12 @@ gather_apply_kernel(const T* __restrict__ B, int64_t ldb, int ncols, int64_t n, 
   for (int q = threadIdx.x; q < s * W; q += blockDim.x) { acc_hi[q] = 0; acc_lo[q] = 0; }
   const int lane = threadIdx.x & 31;
   const int gl = lane & (kGroup - 1);
-  const int row_slot = threadIdx.x / kGroup;           // 0 .. 31
-  const int rows_per_pass = kApplyThreads / kGroup;   // 32
+  const int row_slot = threadIdx.x / kGroup;
+  const int rows_per_pass = kApplyThreads / kGroup;
   for (int c = c_begin; c < c_end; ++c) {
     const int64_t i0 = (int64_t)c * kChunk;
     const int Lc = (int)((n - i0) < kChunk ? (n - i0) : kChunk);
+    const int ne = Lc * zeta;
     __syncthreads();
     for (int il = threadIdx.x; il < Lc; il += blockDim.x) {
 #pragma unroll
@@ -193,18 +202,23 @@ gather_apply_kernel(const T* __restrict__ B, int64_t ldb, int ncols, int64_t n, 
         tile[il * W + q] = (col < ncols) ? to_c(B[i0 + il + (int64_t)col * ldb]) : (C)0;
       }
     }
+    {
+      const uint4* src = reinterpret_cast<const uint4*>(entries + (int64_t)c * kChunk * zeta);
+      uint4* dst = reinterpret_cast<uint4*>(ent_s);
+      for (int q = threadIdx.x; q < (ne + 7) / 8; q += blockDim.x) dst[q] = __ldg(src + q);
+      const uint32_t* rp = rowptr + (int64_t)c * (s + 1);
+      for (int q = threadIdx.x; q <= s; q += blockDim.x) rp_s[q] = __ldg(rp + q);
+    }
     __syncthreads();
-    const uint32_t* rp = rowptr + (int64_t)c * (s + 1);
-    const uint16_t* ent = entries + (int64_t)c * kChunk * zeta;
     for (int rb = 0; rb < s; rb += rows_per_pass) {
       const int r = rb + row_slot;
       C a[W];
 #pragma unroll
       for (int q = 0; q < W; ++q) a[q] = 0;
       if (r < s) {
-        const int e0 = (int)rp[r], e1 = (int)rp[r + 1];
+        const int e0 = (int)rp_s[r], e1 = (int)rp_s[r + 1];
         for (int e = e0 + gl; e < e1; e += kGroup) {
-          const uint16_t v = ent[e];
+          const uint16_t v = ent_s[e];
           const C* src = tile + (v & 0x7FFF) * W;
           if (v & 0x8000) {
 #pragma unroll
@@ -249,8 +263,9 @@ template <typename T, int W>
 static sk_status launch_gather(const SketchPlan& p, const T* B, int64_t ldb, int ncols, double* partial,
                                int ngroups, int cpg, cudaStream_t st) {
   using C = typename Compute<T>::type;
-  const size_t smem = (size_t)kChunk * W * sizeof(C) + (size_t)2 * p.s * W * sizeof(C);
-  SK_CUDA(cudaFuncSetAttribute(gather_apply_kernel<T, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const size_t smem = (size_t)kChunk * W * sizeof(C) + entries_bytes(p.zeta) + rowptr_bytes(p.s) +
+                      (size_t)2 * p.s * W * sizeof(C);
+  SK_CUDA(cudaFuncSetAttribute(gather_apply_kernel<T, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, kDynSmemLimit));
   dim3 grid((ncols + W - 1) / W, ngroups);
   gather_apply_kernel<T, W><<<grid, kApplyThreads, smem, st>>>(B, ldb, ncols, p.n, p.s, p.zeta, p.nchunks, cpg,
                                                                 p.rowptr, p.entries, partial);
@@ -269,10 +284,14 @@ static sk_status gather_dispatch(const SketchPlan& p, const T* B, int64_t ldb, i
   }
 }
 
-// Column tile width: as wide as shared memory allows (tile + two accumulators).
-static int pick_width(int s, int ncols, size_t csize) {
+// Column tile width: as wide as shared memory allows (tile, staged entries
+// and row offsets, two accumulators).
+static int pick_width(int s, int zeta, int ncols, size_t csize) {
   int W = 8;
-  while (W > 1 && ((size_t)kChunk * W * csize + (size_t)2 * s * W * csize > 200 * 1024 || W > ncols)) W /= 2;
+  const size_t fixed = entries_bytes(zeta) + rowptr_bytes(s);
+  while (W > 1 && ((size_t)kChunk * W * csize + fixed + (size_t)2 * s * W * csize > (size_t)kDynSmemLimit ||
+                   W > ncols))
+    W /= 2;
   if (csize == 8 && W > 4) W = 4;
   return W;
 }
@@ -284,9 +303,9 @@ struct GatherShape {
 static GatherShape gather_shape(const SketchPlan& p, int ncols, sk_dtype dtype) {
   GatherShape g;
   const size_t csize = dtype == SK_F64 ? 8 : 4;
-  g.W = pick_width(p.s, ncols, csize);
+  g.W = pick_width(p.s, p.zeta, ncols, csize);
   g.ntiles = (ncols + g.W - 1) / g.W;
-  const int target = 2 * num_sms();
+  const int target = num_sms();
   int ngroups = (target + g.ntiles - 1) / g.ntiles;
   if (ngroups > p.nchunks) ngroups = p.nchunks;
   if (ngroups < 1) ngroups = 1;
@@ -437,7 +456,7 @@ extern "C" sk_status sketch_apply_noalloc(const sk_sketch* S, const void* B, int
   // partial sums are fully overwritten by this call's kernels
   SK_CUDA(cudaMemsetAsync(p.d_status, 0, sizeof(int), st));
   const size_t smem = plan_smem_bytes(p.s, zeta);
-  SK_CUDA(cudaFuncSetAttribute(plan_build_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  SK_CUDA(cudaFuncSetAttribute(plan_build_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kDynSmemLimit));
   plan_build_kernel<<<p.nchunks, kPlanThreads, smem, st>>>(p.n, p.s, zeta, seed_key(p.seed), p.rowptr, p.entries,
                                                             p.d_status);
   SK_CUDA(cudaGetLastError());

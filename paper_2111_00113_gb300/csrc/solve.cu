@@ -21,6 +21,27 @@ namespace sk {
 
 static constexpr int kVecThreads = 256;
 
+// G consecutive entries of one column, converted to the compute type.
+template <int G, typename T, typename C>
+__device__ __forceinline__ void gload_rows(const T* __restrict__ col, int64_t i, C (&v)[G]) {
+  if constexpr (G == 4 && std::is_same<T, float>::value) {
+    const float4 t = __ldg(reinterpret_cast<const float4*>(col + i));
+    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+  } else if constexpr (G == 4 && std::is_same<T, double>::value) {
+    const double2 a = __ldg(reinterpret_cast<const double2*>(col + i));
+    const double2 b = __ldg(reinterpret_cast<const double2*>(col + i + 2));
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+  } else if constexpr (G == 4) {
+    const uint2 u = __ldg(reinterpret_cast<const uint2*>(col + i));
+    const float2 fa = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.x));
+    const float2 fb = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.y));
+    v[0] = fa.x; v[1] = fa.y; v[2] = fb.x; v[3] = fb.y;
+  } else {
+#pragma unroll
+    for (int e = 0; e < G; ++e) v[e] = to_c(col[i + e]);
+  }
+}
+
 static int vec_grid(int64_t n) {
   int64_t g = (n + kVecThreads * 4 - 1) / (kVecThreads * 4);
   const int64_t gmax = 2 * num_sms();
@@ -75,14 +96,17 @@ __global__ void init_stop_kernel(int* stop, int value, int* nanflag) {
 // x += B y over the first `width` columns (width = diag[2]).  FP64 basis:
 // FP64 FMAs.  FP32/BF16 basis: products and sums in pairs of floats
 // (exact product error by FMA, two-sum accumulation), about 48 significant
-// bits, added to x in FP64.
-template <typename T>
+// bits, added to x in FP64.  G = 4 consecutive rows per thread (16-byte
+// loads) when the leading dimension and n allow it.
+template <typename T, int G>
 __global__ void __launch_bounds__(kVecThreads)
 update_kernel(double* __restrict__ x, const T* __restrict__ B, int64_t ldb, int64_t n, int d,
               const double* __restrict__ y, const double* __restrict__ diag) {
   extern __shared__ double ys[];  // d doubles (+ 2d floats for the pair path)
   const int width = (int)diag[2];
   for (int j = threadIdx.x; j < width; j += blockDim.x) ys[j] = y[j];
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x * G;
+  const int64_t i_begin = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * G;
   if constexpr (!std::is_same<T, double>::value) {
     float* yh = (float*)(ys + d);
     float* yl = yh + d;
@@ -93,46 +117,72 @@ update_kernel(double* __restrict__ x, const T* __restrict__ B, int64_t ldb, int6
       yl[j] = (float)(ys[j] - (double)hi);
     }
     __syncthreads();
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-      float s_hi = 0.f, s_lo = 0.f;
+    for (int64_t i = i_begin; i < n; i += stride) {
+      float s_hi[G], s_lo[G];
+#pragma unroll
+      for (int e = 0; e < G; ++e) { s_hi[e] = 0.f; s_lo[e] = 0.f; }
+#pragma unroll 4
       for (int j = 0; j < width; ++j) {
-        const float bv = to_c(B[i + (int64_t)j * ldb]);
-        const float p = bv * yh[j];
-        const float pe = fmaf(bv, yh[j], -p);
-        const float t = s_hi + p;
-        const float bp = t - s_hi;
-        const float err = (s_hi - (t - bp)) + (p - bp);
-        s_hi = t;
-        s_lo += err + pe + bv * yl[j];
+        float bv[G];
+        gload_rows<G>(B + (int64_t)j * ldb, i, bv);
+        const float yhj = yh[j], ylj = yl[j];
+#pragma unroll
+        for (int e = 0; e < G; ++e) {
+          const float p = bv[e] * yhj;
+          const float pe = fmaf(bv[e], yhj, -p);
+          const float t = s_hi[e] + p;
+          const float bp = t - s_hi[e];
+          const float err = (s_hi[e] - (t - bp)) + (p - bp);
+          s_hi[e] = t;
+          s_lo[e] += err + pe + bv[e] * ylj;
+        }
       }
-      x[i] += (double)s_hi + (double)s_lo;
+#pragma unroll
+      for (int e = 0; e < G; ++e) x[i + e] += (double)s_hi[e] + (double)s_lo[e];
     }
   } else {
     __syncthreads();
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-      double acc = 0;
-      for (int j = 0; j < width; ++j) acc += B[i + (int64_t)j * ldb] * ys[j];
-      x[i] += acc;
+    for (int64_t i = i_begin; i < n; i += stride) {
+      double acc[G];
+#pragma unroll
+      for (int e = 0; e < G; ++e) acc[e] = 0;
+#pragma unroll 4
+      for (int j = 0; j < width; ++j) {
+        double bv[G];
+        gload_rows<G>(B + (int64_t)j * ldb, i, bv);
+#pragma unroll
+        for (int e = 0; e < G; ++e) acc[e] += bv[e] * ys[j];
+      }
+#pragma unroll
+      for (int e = 0; e < G; ++e) x[i + e] += acc[e];
     }
   }
 }
 
-static sk_status enqueue_update(double* x, const void* B, int64_t ldb, int64_t n, int d, sk_dtype dt, const double* y,
-                                const double* diag, cudaStream_t st) {
-  const int g = vec_grid(n);
+template <typename T, int G>
+static sk_status launch_update(double* x, const T* B, int64_t ldb, int64_t n, int d, const double* y,
+                               const double* diag, cudaStream_t st) {
   const size_t smem = (size_t)d * sizeof(double) + (size_t)2 * d * sizeof(float);
-  if (dt == SK_F64) {
-    SK_CUDA(cudaFuncSetAttribute(update_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    update_kernel<double><<<g, kVecThreads, smem, st>>>(x, (const double*)B, ldb, n, d, y, diag);
-  } else if (dt == SK_F32) {
-    SK_CUDA(cudaFuncSetAttribute(update_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    update_kernel<float><<<g, kVecThreads, smem, st>>>(x, (const float*)B, ldb, n, d, y, diag);
-  } else {
-    SK_CUDA(cudaFuncSetAttribute(update_kernel<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    update_kernel<__nv_bfloat16><<<g, kVecThreads, smem, st>>>(x, (const __nv_bfloat16*)B, ldb, n, d, y, diag);
-  }
+  int64_t g = (n + (int64_t)kVecThreads * G - 1) / ((int64_t)kVecThreads * G);
+  if (g > 16 * num_sms()) g = 16 * num_sms();
+  if (g < 1) g = 1;
+  SK_CUDA(cudaFuncSetAttribute(update_kernel<T, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, kDynSmemLimit));
+  update_kernel<T, G><<<(int)g, kVecThreads, smem, st>>>(x, B, ldb, n, d, y, diag);
   SK_CUDA(cudaGetLastError());
   return SK_OK;
+}
+
+static sk_status enqueue_update(double* x, const void* B, int64_t ldb, int64_t n, int d, sk_dtype dt, const double* y,
+                                const double* diag, cudaStream_t st) {
+  const bool vec = (n % 4 == 0) && (ldb % 8 == 0) && ((uintptr_t)B % 16 == 0) && ((uintptr_t)x % 32 == 0);
+  if (dt == SK_F64)
+    return vec ? launch_update<double, 4>(x, (const double*)B, ldb, n, d, y, diag, st)
+               : launch_update<double, 1>(x, (const double*)B, ldb, n, d, y, diag, st);
+  if (dt == SK_F32)
+    return vec ? launch_update<float, 4>(x, (const float*)B, ldb, n, d, y, diag, st)
+               : launch_update<float, 1>(x, (const float*)B, ldb, n, d, y, diag, st);
+  return vec ? launch_update<__nv_bfloat16, 4>(x, (const __nv_bfloat16*)B, ldb, n, d, y, diag, st)
+             : launch_update<__nv_bfloat16, 1>(x, (const __nv_bfloat16*)B, ldb, n, d, y, diag, st);
 }
 
 // ----------------------------------------------------------------------------
@@ -171,24 +221,43 @@ static void resolve_opts(const sk_opts* in, sk_opts* o, int d) {
   if (o->maxit <= 0) o->maxit = 10000;
 }
 
+static constexpr long long kBarrierSpinLimit = 1ll << 22;
+
 // Device workspace of one basis build.
 struct BasisBuffers {
   BasisParams bp;
-  sk_status alloc(int64_t n, int d, int k, sk_dtype dt, int passes, double bd, Scratch& sc, void* Bext) {
+  PersistWork pw;
+  bool persistent = false;
+  sk_status alloc(int64_t n, int d, int k, sk_dtype dt, int passes, double bd, Scratch& sc, void* Bext,
+                  const sk_op* op = nullptr, bool want_persistent = false) {
     std::memset(&bp, 0, sizeof(bp));
     bp.n = n;
     bp.d = d;
     bp.k = k;
     bp.passes = passes;
     bp.dtype = dt;
-    bp.ldb = n;
+    // internal bases pad the leading dimension to 8 elements (16-byte
+    // aligned columns for every storage type); a caller's basis has ld = n
+    bp.ldb = Bext ? n : ((n + 7) / 8) * 8;
     bp.bd = bd;
     bp.nblk = basis_grid(n);
     if (Bext) bp.B = Bext;
     else {
       unsigned char* Bp = nullptr;
-      SK_TRY(sc.alloc(&Bp, (size_t)n * (d + 1) * dtype_size(dt)));
+      SK_TRY(sc.alloc(&Bp, (size_t)bp.ldb * (d + 1) * dtype_size(dt)));
       bp.B = Bp;
+    }
+    if (dt == SK_F64) SK_TRY(sc.alloc(&bp.M, (size_t)n));
+    int pg = 0, pe = 0;
+    size_t psm = 0;
+    persistent = want_persistent && op != nullptr && persist_shape(op, dt, &pg, &pe, &psm);
+    std::memset(&pw, 0, sizeof(pw));
+    if (persistent) {
+      SK_TRY(sc.alloc(&pw.bar, 2));
+      SK_TRY(sc.alloc(&pw.err, 1));
+      SK_CUDA(cudaMemsetAsync(pw.err, 0, sizeof(int), sc.st));
+      SK_TRY(sc.alloc(&pw.part, (size_t)2 * pg * (kMaxK + 1)));
+      pw.spin_limit = kBarrierSpinLimit;
     }
     double* dd = nullptr;
     const size_t nd = (size_t)2 * d * k + 2 * (size_t)d + (size_t)(d + 1) * d + (size_t)bp.nblk * (kMaxK + 1) + 2;
@@ -215,9 +284,11 @@ struct BasisBuffers {
 };
 
 // Enqueue one basis build: stop = d+1, Hbar = 0, then the kernels.
-static sk_status enqueue_basis_build(const BasisParams& bp, const sk_op* A, cudaStream_t st) {
+static sk_status enqueue_basis_build(BasisBuffers& bb, const sk_op* A, cudaStream_t st) {
+  const BasisParams& bp = bb.bp;
   init_stop_kernel<<<1, 1, 0, st>>>(bp.stop, bp.d + 1, bp.nanflag);
   SK_CUDA(cudaMemsetAsync(bp.Hbar, 0, sizeof(double) * (size_t)(bp.d + 1) * bp.d, st));
+  if (bb.persistent) return enqueue_basis_persistent(bp, A, bb.pw, st);
   return enqueue_basis(bp, A, st);
 }
 
@@ -241,7 +312,7 @@ extern "C" sk_status trunc_arnoldi_basis(const sk_op* A, const double* r0, int d
   if (!opts || opts->breakdown <= 0) o.breakdown = basis_dtype == SK_F64 ? 1e-13 : 1e-6;
   Scratch sc(st);
   BasisBuffers bb;
-  SK_TRY(bb.alloc(A->n, d, k, basis_dtype, o.cgs_passes, o.breakdown, sc, B));
+  SK_TRY(bb.alloc(A->n, d, k, basis_dtype, o.cgs_passes, o.breakdown, sc, B, A, o.persistent != 0));
   bb.bp.r = r0;
   {
     double* part = nullptr;
@@ -253,7 +324,7 @@ extern "C" sk_status trunc_arnoldi_basis(const sk_op* A, const double* r0, int d
     norm2_kernel<<<g, kVecThreads, 0, st>>>(r0, A->n, part, cnt, bb.rho2_mut());
     SK_CUDA(cudaGetLastError());
   }
-  SK_TRY(enqueue_basis_build(bb.bp, A, st));
+  SK_TRY(enqueue_basis_build(bb, A, st));
   if (S) {
     Sketcher sk;
     SK_TRY(sk.create(*S, sc, st));
@@ -266,10 +337,12 @@ extern "C" sk_status trunc_arnoldi_basis(const sk_op* A, const double* r0, int d
     if (SAB) SK_TRY(enqueue_hbar_product(SBfull, bb.bp.Hbar, S->s, d, k, bb.bp.stop, SAB, st));
   }
   if (Hbar) SK_CUDA(cudaMemcpyAsync(Hbar, bb.bp.Hbar, sizeof(double) * (size_t)(d + 1) * d, cudaMemcpyDeviceToDevice, st));
-  int h[2] = {0, 0};
+  int h[3] = {0, 0, 0};
   SK_CUDA(cudaMemcpyAsync(h, bb.bp.stop, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+  if (bb.persistent) SK_CUDA(cudaMemcpyAsync(h + 2, bb.pw.err, sizeof(int), cudaMemcpyDeviceToHost, st));
   SK_CUDA(cudaStreamSynchronize(st));
   *d_used = h[0] < d ? h[0] : d;
+  if (h[2]) { set_error("persistent basis: a grid barrier timed out"); return SK_ETIMEOUT; }
   if (h[1]) { set_error("NaN/Inf in the basis recurrence"); return SK_ENAN; }
   return SK_OK;
 }
@@ -295,7 +368,8 @@ struct SolveState {
   double* vec_part;
   unsigned* vec_cnt;
   double* out;      // device: [rho2, rhat, kappa, width]
-  double* h_out;    // pinned host copy
+  double* h_out;    // pinned host copy (+ one int: the persistent kernel's error word)
+  int* h_err;
 };
 
 static sk_status enqueue_residual(const SolveState& S, const OpView<double>& Av, const double* b, const double* x,
@@ -321,21 +395,22 @@ static sk_status enqueue_cycle(SolveState& S, const sk_op* A, const OpView<doubl
   SK_TRY(mark(ev, EV_START, st, capturing));
   SK_TRY(S.sketch.apply(S.r, S.n, 1, SK_F64, S.g, S.ws_r, st));
   SK_TRY(mark(ev, EV_G, st, capturing));
-  SK_TRY(enqueue_basis_build(S.bb.bp, A, st));
+  SK_TRY(enqueue_basis_build(S.bb, A, st));
   SK_TRY(mark(ev, EV_BASIS, st, capturing));
-  SK_TRY(S.sketch.apply(S.bb.bp.B, S.n, S.d + 1, S.o.basis, S.SB, S.ws_B, st));
+  SK_TRY(S.sketch.apply(S.bb.bp.B, S.bb.bp.ldb, S.d + 1, S.o.basis, S.SB, S.ws_B, st));
   SK_TRY(mark(ev, EV_SB, st, capturing));
   SK_TRY(enqueue_hbar_product(S.SB, S.bb.bp.Hbar, S.s, S.d, S.k, S.bb.bp.stop, S.Aug, st));
   SK_CUDA(cudaMemcpyAsync(S.Aug + (size_t)S.d * S.s, S.g, sizeof(double) * S.s, cudaMemcpyDeviceToDevice, st));
   SK_TRY(enqueue_qr(S.Aug, S.s, S.d, S.d + 1, S.rdiag, S.tau, S.Tws, st));
   SK_TRY(enqueue_ls_solve(S.Aug, S.rdiag, S.s, S.d, S.o.stab_tol, S.y, S.out + 1, st));
   SK_TRY(mark(ev, EV_SMALL, st, capturing));
-  SK_TRY(enqueue_update(x, S.bb.bp.B, S.n, S.n, S.d, S.o.basis, S.y, S.out + 1, st));
+  SK_TRY(enqueue_update(x, S.bb.bp.B, S.bb.bp.ldb, S.n, S.d, S.o.basis, S.y, S.out + 1, st));
   SK_TRY(mark(ev, EV_UPDATE, st, capturing));
   SK_TRY(enqueue_residual(S, Av, b, x, st));
   SK_CUDA(cudaMemcpyAsync(S.out, S.bb.bp.rho2, sizeof(double), cudaMemcpyDeviceToDevice, st));
   SK_TRY(mark(ev, EV_RES, st, capturing));
   SK_CUDA(cudaMemcpyAsync(S.h_out, S.out, 4 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  if (S.bb.persistent) SK_CUDA(cudaMemcpyAsync(S.h_err, S.bb.pw.err, sizeof(int), cudaMemcpyDeviceToHost, st));
   return SK_OK;
 }
 
@@ -363,7 +438,7 @@ extern "C" sk_status sgmres_solve(const sk_op* A, const double* b, double* x, in
   SK_CHECK_ARG(k <= kMaxK, "k <= 16 supported");
   SK_CHECK_ARG(s >= d + 1, "need s >= d + 1");
   SK_CHECK_ARG(tol > 0, "tol > 0");
-  SK_CHECK_ARG(d <= 4096, "d <= 4096");
+  SK_CHECK_ARG(d <= 768, "d <= 768");
   cudaStream_t st = (cudaStream_t)stream;
   SolveState S;
   std::memset(&S, 0, sizeof(S));
@@ -375,7 +450,7 @@ extern "C" sk_status sgmres_solve(const sk_op* A, const double* b, double* x, in
   S.s = s;
   if (info) std::memset(info, 0, sizeof(*info));
   Scratch sc(st);
-  SK_TRY(S.bb.alloc(S.n, d, k, S.o.basis, S.o.cgs_passes, S.o.breakdown, sc, nullptr));
+  SK_TRY(S.bb.alloc(S.n, d, k, S.o.basis, S.o.cgs_passes, S.o.breakdown, sc, nullptr, A, S.o.persistent != 0));
   sk_sketch sks;
   sks.kind = S.o.sketch;
   sks.n = S.n;
@@ -399,7 +474,9 @@ extern "C" sk_status sgmres_solve(const sk_op* A, const double* b, double* x, in
   SK_CUDA(cudaMemsetAsync(S.vec_cnt, 0, 2 * sizeof(unsigned), st));
   SK_TRY(sc.alloc(&S.out, 4));
   SK_CUDA(cudaMemsetAsync(S.out, 0, 4 * sizeof(double), st));
-  SK_CUDA(cudaMallocHost((void**)&S.h_out, 4 * sizeof(double)));
+  SK_CUDA(cudaMallocHost((void**)&S.h_out, 5 * sizeof(double)));
+  S.h_err = (int*)(S.h_out + 4);
+  *S.h_err = 0;
   struct HostFree { double* p; ~HostFree() { if (p) cudaFreeHost(p); } } hf{S.h_out};
   OpView<double> Av;
   make_view(A, &Av);
@@ -492,6 +569,7 @@ extern "C" sk_status sgmres_solve(const sk_op* A, const double* b, double* x, in
     const double kap = S.h_out[2];
     width = (int)S.h_out[3];
     if (kap > kmax) kmax = kap;
+    if (*S.h_err) { set_error("persistent basis: a grid barrier timed out"); result = SK_ETIMEOUT; break; }
     if (!std::isfinite(rho2)) { set_error("NaN/Inf in the residual"); result = SK_ENAN; break; }
     relres = std::sqrt(rho2) / bnorm;
     if (relres <= tol) { result = SK_OK; break; }

@@ -118,7 +118,7 @@ static sk_status srht_launch(const SrhtPlan& p, const T* B, int64_t ldb, int nco
                              int bpg, int nblocks, cudaStream_t st) {
   using C = typename Compute<T>::type;
   const size_t smem = ((size_t)(1 << p.b) + p.s) * sizeof(C);
-  SK_CUDA(cudaFuncSetAttribute(srht_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  SK_CUDA(cudaFuncSetAttribute(srht_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, kDynSmemLimit));
   dim3 grid(ncols, ngroups);
   srht_kernel<T><<<grid, kSrhtThreads, smem, st>>>(B, ldb, p.n, p.b, nblocks, bpg, p.s, p.sign_bits, p.rows,
                                                    partial);
@@ -147,6 +147,7 @@ sk_status srht_plan_create(SrhtPlan* p, const sk_sketch* S, Scratch& scratch, cu
   p->n_p = 1ll << p->logn;
   SK_CHECK_ARG(p->logn <= 30, "SRHT needs n <= 2^30");
   SK_CHECK_ARG(p->s >= 1 && p->s <= p->n_p, "SRHT needs 1 <= s <= n_p");
+  SK_CHECK_ARG(p->s <= 16384, "SRHT needs s <= 16384");
   p->b = p->logn < 12 ? p->logn : 12;
   std::vector<int32_t> rows;
   srht_rows_host(S->seed, p->n_p, p->s, rows);

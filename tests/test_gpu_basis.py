@@ -116,3 +116,48 @@ def test_basis_low_precision_relation(skg, dtype):
     AB = A @ B[:, :d]
     assert np.linalg.norm(AB - B @ H) <= 50 * u * np.linalg.norm(AB)
     assert np.allclose(np.linalg.norm(B, axis=0), 1, atol=10 * u)
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("k", [2, 4])
+def test_persistent_matches_multikernel(skg, dtype, k):
+    # the cooperative one-launch basis and the three-launch-per-step basis run
+    # the same recurrence; their bases agree to rounding, and each satisfies
+    # the Arnoldi relation on its own
+    import torch
+    N, d = 96, 30
+    coef, A = _cd(N, 30.0)
+    r = synth.randn(7, N * N)
+    tdt = torch.float64 if dtype == "f64" else torch.float32
+    op = skg.Op.stencil5(N, N, coef)
+    rt = torch.tensor(r, device="cuda")
+    a = skg.trunc_arnoldi_basis(op, rt, d, k, dtype=tdt, persistent=True)
+    b = skg.trunc_arnoldi_basis(op, rt, d, k, dtype=tdt, persistent=False)
+    Ba = a["B"].to(torch.float64).cpu().numpy()
+    Bb = b["B"].to(torch.float64).cpu().numpy()
+    tol = 1e-11 if dtype == "f64" else 1e-4
+    assert np.linalg.norm(Ba[:, :10] - Bb[:, :10]) <= tol * 10
+    H = a["Hbar"].cpu().numpy()
+    AB = A @ Ba[:, :d]
+    u = 1e-15 if dtype == "f64" else 6e-8
+    assert np.linalg.norm(AB - Ba @ H) <= 1e3 * u * np.linalg.norm(AB)
+
+
+def test_persistent_diffusion_and_shift(skg):
+    import torch
+    N, d, k = 64, 20, 4
+    th = np.exp(synth.grf(2, N, 8.0))
+    Av = operators.diffusion_var_matrix(N, N, th)
+    r = synth.randn(3, N * N)
+    op = skg.Op.diffusion_var(N, N, torch.tensor(th, device="cuda"))
+    out = skg.trunc_arnoldi_basis(op, torch.tensor(r, device="cuda"), d, k)
+    B_ref, _, H_ref, _ = krylov.trunc_arnoldi(Av, r, d, k)
+    B = out["B"].cpu().numpy()
+    assert np.linalg.norm(B[:, :8] - B_ref[:, :8]) <= 1e-10
+    assert np.linalg.norm(Av @ B[:, :d] - B @ out["Hbar"].cpu().numpy()) <= 1e-12 * np.linalg.norm(Av @ B[:, :d])
+    shift = synth.uniform(1, N * N)
+    coef, As = _cd(N, 10.0, shift)
+    op = skg.Op.stencil5(N, N, coef, torch.tensor(shift, device="cuda"))
+    out = skg.trunc_arnoldi_basis(op, torch.tensor(r, device="cuda"), d, k)
+    B_ref, _, _, _ = krylov.trunc_arnoldi(As, r, d, k)
+    assert np.linalg.norm(out["B"].cpu().numpy()[:, :8] - B_ref[:, :8]) <= 1e-10
