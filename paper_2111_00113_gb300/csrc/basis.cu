@@ -121,16 +121,38 @@ __device__ __forceinline__ void reduce_partials(const double* part, int nblocks,
 }
 
 // ---- kernels ------------------------------------------------------------------
+// Each thread handles kIter groups of G elements.  The passes are launched
+// with programmatic dependent launch: a kernel loads every operand that its
+// immediate predecessor does not write (b_j is written by form(j), the
+// predecessor of dots1(j); the older window vectors and, for dots2 and form,
+// b_j itself are older), then waits for the predecessor's results (h1, h2,
+// nu, stop; m for FP64) and only then lets its own successor launch, so a
+// successor's early loads only ever read what completed kernels wrote.
+static constexpr int kIter = 2;
+
+__device__ __forceinline__ void pdl_trigger() {
+#if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 900
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+#endif
+}
+__device__ __forceinline__ void pdl_wait() {
+#if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 900
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+#endif
+}
+
 template <typename T, int KM, int G, bool STORE_M>
 __global__ void __launch_bounds__(kBasisThreads)
 form_kernel(BasisParams p, OpView<typename Compute<T>::type> A, int c) {
   using C = typename Compute<T>::type;
-  if (c >= *p.stop) return;
   T* out = bcol<T>(p.B, p.ldb, c);
   const int64_t n = p.n;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x * G;
   const int64_t i_begin = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * G;
   if (c == 0) {
+    pdl_wait();
+    pdl_trigger();
+    if (c >= *p.stop) return;
     const double inv = 1.0 / sqrt(*p.rho2);
     for (int64_t i = i_begin; i < n; i += stride) {
       C v[G];
@@ -142,27 +164,55 @@ form_kernel(BasisParams p, OpView<typename Compute<T>::type> A, int c) {
   }
   const int j = c - 1;
   const int kw = min(p.k, j + 1);
+  const T* bj = bcol<T>(p.B, p.ldb, j);
+  // prologue: b_j and the window are older than the predecessor (dots2(j));
+  // with one Gram-Schmidt pass the predecessor is dots1(j), which writes m
+  const bool m_late = STORE_M && p.passes == 1;
+  C m[kIter][G];
+  C bw[kIter][KM][G];
+#pragma unroll
+  for (int it = 0; it < kIter; ++it) {
+    const int64_t i = i_begin + it * stride;
+    if (i < n) {
+      if constexpr (STORE_M) {
+        if (!m_late) gload<G>(p.M, i, m[it]);
+      } else {
+        op_apply<G>(A, bj, i, m[it]);
+      }
+#pragma unroll
+      for (int q = 0; q < KM; ++q)
+        if (q < kw) gload<G>(bcol<T>(p.B, p.ldb, j - q), i, bw[it][q]);
+    }
+  }
+  pdl_wait();
+  pdl_trigger();
+  if (c >= *p.stop) return;
+  if (m_late) {
+#pragma unroll
+    for (int it = 0; it < kIter; ++it) {
+      const int64_t i = i_begin + it * stride;
+      if (i < n) gload<G>(p.M, i, m[it]);
+    }
+  }
   C h[KM];
 #pragma unroll
   for (int q = 0; q < KM; ++q) h[q] = (q < kw) ? (C)(p.h1[j * p.k + q] + p.h2[j * p.k + q]) : (C)0;
   const C inv = (C)(1.0 / p.nu[j]);
-  const T* bj = bcol<T>(p.B, p.ldb, j);
-  for (int64_t i = i_begin; i < n; i += stride) {
-    C m[G];
-    if constexpr (STORE_M) gload<G>(p.M, i, m);
-    else op_apply<G>(A, bj, i, m);
 #pragma unroll
-    for (int q = 0; q < KM; ++q) {
-      if (q < kw) {
-        C bw[G];
-        gload<G>(bcol<T>(p.B, p.ldb, j - q), i, bw);
+  for (int it = 0; it < kIter; ++it) {
+    const int64_t i = i_begin + it * stride;
+    if (i < n) {
 #pragma unroll
-        for (int e = 0; e < G; ++e) m[e] -= h[q] * bw[e];
+      for (int q = 0; q < KM; ++q) {
+        if (q < kw) {
+#pragma unroll
+          for (int e = 0; e < G; ++e) m[it][e] -= h[q] * bw[it][q][e];
+        }
       }
-    }
 #pragma unroll
-    for (int e = 0; e < G; ++e) m[e] *= inv;
-    gstore<G>(out, i, m);
+      for (int e = 0; e < G; ++e) m[it][e] *= inv;
+      gstore<G>(out, i, m[it]);
+    }
   }
 }
 
@@ -174,10 +224,32 @@ dots_kernel(BasisParams p, OpView<typename Compute<T>::type> A, int j) {
   using C = typename Compute<T>::type;
   __shared__ C red[(KM + 1) * (kBasisThreads / 32)];
   __shared__ double redd[(KM + 1) * (kBasisThreads / 32)];
-  if (j >= *p.stop) return;
   const int kw = min(p.k, j + 1);
   const int64_t n = p.n;
   const T* bj = bcol<T>(p.B, p.ldb, j);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x * G;
+  const int64_t i_begin = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * G;
+  C m[kIter][G];
+  C bw[kIter][KM][G];
+  // prologue: the window b_{j-1..} is old; b_j is old for pass 2 only
+#pragma unroll
+  for (int it = 0; it < kIter; ++it) {
+    const int64_t i = i_begin + it * stride;
+#pragma unroll
+    for (int q = 0; q < KM; ++q) {
+#pragma unroll
+      for (int e = 0; e < G; ++e) bw[it][q][e] = 0;
+    }
+    if (i < n) {
+#pragma unroll
+      for (int q = (PASS == 1 ? 1 : 0); q < KM; ++q)
+        if (q < kw) gload<G>(bcol<T>(p.B, p.ldb, j - q), i, bw[it][q]);
+      if (PASS == 2 && !STORE_M) op_apply<G>(A, bj, i, m[it]);
+    }
+  }
+  pdl_wait();
+  pdl_trigger();
+  if (j >= *p.stop) return;
   C h[KM];
   if (PASS == 2) {
 #pragma unroll
@@ -186,40 +258,37 @@ dots_kernel(BasisParams p, OpView<typename Compute<T>::type> A, int j) {
   C acc[KM + 1];
 #pragma unroll
   for (int q = 0; q <= KM; ++q) acc[q] = 0;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x * G;
-  for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * G; i < n; i += stride) {
-    C m[G];
-    if (STORE_M && PASS == 2) gload<G>(p.M, i, m);
-    else op_apply<G>(A, bj, i, m);
-    if (STORE_M && PASS == 1) {
-      double md[G];
 #pragma unroll
-      for (int e = 0; e < G; ++e) md[e] = (double)m[e];
-      gstore<G>(p.M, i, md);
-    }
-    C bw[KM][G];
+  for (int it = 0; it < kIter; ++it) {
+    const int64_t i = i_begin + it * stride;
+    if (i < n) {
+      if (PASS == 1) {
+        gload<G>(bj, i, bw[it][0]);
+        op_apply<G>(A, bj, i, m[it]);
+        if (STORE_M) {
+          double md[G];
 #pragma unroll
-    for (int q = 0; q < KM; ++q) {
-      if (q < kw) gload<G>(bcol<T>(p.B, p.ldb, j - q), i, bw[q]);
-      else {
-#pragma unroll
-        for (int e = 0; e < G; ++e) bw[q][e] = 0;
+          for (int e = 0; e < G; ++e) md[e] = (double)m[it][e];
+          gstore<G>(p.M, i, md);
+        }
+      } else if (STORE_M) {
+        gload<G>(p.M, i, m[it]);
       }
-    }
-    if (PASS == 2) {
+      if (PASS == 2) {
+#pragma unroll
+        for (int q = 0; q < KM; ++q) {
+#pragma unroll
+          for (int e = 0; e < G; ++e) m[it][e] -= h[q] * bw[it][q][e];
+        }
+      }
 #pragma unroll
       for (int q = 0; q < KM; ++q) {
 #pragma unroll
-        for (int e = 0; e < G; ++e) m[e] -= h[q] * bw[q][e];
+        for (int e = 0; e < G; ++e) acc[q] += bw[it][q][e] * m[it][e];
       }
+#pragma unroll
+      for (int e = 0; e < G; ++e) acc[KM] += m[it][e] * m[it][e];
     }
-#pragma unroll
-    for (int q = 0; q < KM; ++q) {
-#pragma unroll
-      for (int e = 0; e < G; ++e) acc[q] += bw[q][e] * m[e];
-    }
-#pragma unroll
-    for (int e = 0; e < G; ++e) acc[KM] += m[e] * m[e];
   }
   block_sum_k<KM + 1>(acc, red);
   double* part = p.partial;
@@ -262,16 +331,31 @@ dots_kernel(BasisParams p, OpView<typename Compute<T>::type> A, int j) {
   if (brk) *p.stop = j + 1;
 }
 
+template <typename K, typename... Args>
+static cudaError_t launch_pdl(K kernel, int grid, cudaStream_t st, bool pdl, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(kBasisThreads);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 template <typename T, int KM, int G, bool SM>
 static sk_status enqueue_basis_t(const BasisParams& p, const OpView<typename Compute<T>::type>& A, cudaStream_t st) {
   const int g = p.nblk;
-  form_kernel<T, KM, G, SM><<<g, kBasisThreads, 0, st>>>(p, A, 0);
+  // the first pass follows memset/plain nodes: no programmatic edge
+  SK_CUDA(launch_pdl(form_kernel<T, KM, G, SM>, g, st, false, p, A, 0));
   for (int j = 0; j < p.d; ++j) {
-    dots_kernel<T, KM, G, SM, 1><<<g, kBasisThreads, 0, st>>>(p, A, j);
-    if (p.passes == 2) dots_kernel<T, KM, G, SM, 2><<<g, kBasisThreads, 0, st>>>(p, A, j);
-    form_kernel<T, KM, G, SM><<<g, kBasisThreads, 0, st>>>(p, A, j + 1);
+    SK_CUDA(launch_pdl(dots_kernel<T, KM, G, SM, 1>, g, st, true, p, A, j));
+    if (p.passes == 2) SK_CUDA(launch_pdl(dots_kernel<T, KM, G, SM, 2>, g, st, true, p, A, j));
+    SK_CUDA(launch_pdl(form_kernel<T, KM, G, SM>, g, st, true, p, A, j + 1));
   }
-  SK_CUDA(cudaGetLastError());
   return SK_OK;
 }
 
@@ -288,11 +372,11 @@ bool basis_vector_path(const sk_op* op, int64_t ldb, const void* B) {
          ((uintptr_t)B % 16) == 0;
 }
 
-int basis_grid(int64_t n) {
-  // about 2 groups of 4 elements per thread; at most 8 CTAs per SM
-  int64_t g = (n + kBasisThreads * 8 - 1) / (kBasisThreads * 8);
-  const int64_t gmax = 8 * num_sms();
-  if (g > gmax) g = gmax;
+int basis_grid(int64_t n, int G) {
+  // every thread handles exactly kIter groups of G elements (registers hold
+  // the prefetched operands); the grid grows with n
+  const int64_t per = (int64_t)kBasisThreads * G * kIter;
+  int64_t g = (n + per - 1) / per;
   if (g < 1) g = 1;
   return (int)g;
 }
@@ -300,17 +384,22 @@ int basis_grid(int64_t n) {
 sk_status enqueue_basis(const BasisParams& p, const sk_op* op, cudaStream_t st) {
   if (p.k > kMaxK) { set_error("k <= %d supported", kMaxK); return SK_EINVAL; }
   const bool vec = basis_vector_path(op, p.ldb, p.B) && (p.r == nullptr || ((uintptr_t)p.r % 16) == 0);
+  BasisParams q = p;
+  q.nblk = basis_grid(p.n, vec ? 4 : 1);
+  if (q.nblk > p.nblk_cap) { set_error("basis: partial buffer too small"); return SK_EINVAL; }
+  const BasisParams& pp = q;
   if (p.dtype == SK_F64) {
     OpView<double> A;
     make_view(op, &A);
     if (!p.M) { set_error("FP64 basis needs the m workspace"); return SK_EINVAL; }
-    return vec ? enqueue_basis_k<double, 4, true>(p, A, st) : enqueue_basis_k<double, 1, true>(p, A, st);
+    return vec ? enqueue_basis_k<double, 4, true>(pp, A, st) : enqueue_basis_k<double, 1, true>(pp, A, st);
   }
   OpView<float> A;
   SK_TRY(make_view(op, &A, st));
   if (p.dtype == SK_F32)
-    return vec ? enqueue_basis_k<float, 4, false>(p, A, st) : enqueue_basis_k<float, 1, false>(p, A, st);
-  return vec ? enqueue_basis_k<__nv_bfloat16, 4, false>(p, A, st) : enqueue_basis_k<__nv_bfloat16, 1, false>(p, A, st);
+    return vec ? enqueue_basis_k<float, 4, false>(pp, A, st) : enqueue_basis_k<float, 1, false>(pp, A, st);
+  return vec ? enqueue_basis_k<__nv_bfloat16, 4, false>(pp, A, st)
+             : enqueue_basis_k<__nv_bfloat16, 1, false>(pp, A, st);
 }
 
 }  // namespace sk

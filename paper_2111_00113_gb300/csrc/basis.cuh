@@ -26,7 +26,8 @@ struct BasisParams {
   const double* r;    // starting vector (FP64)
   const double* rho2; // ||r||^2 (device)
   double bd;          // breakdown threshold
-  int nblk;           // CTAs per pass
+  int nblk;           // CTAs per pass (set by enqueue_basis)
+  int nblk_cap;       // partial-sum rows allocated
 };
 
 // Workspace of the persistent (cooperative) basis kernel.
@@ -40,7 +41,7 @@ struct PersistWork {
 bool persist_shape(const sk_op* op, sk_dtype dt, int* grid, int* ept, size_t* smem);
 sk_status enqueue_basis_persistent(const BasisParams& bp, const sk_op* op, PersistWork& w, cudaStream_t st);
 
-int basis_grid(int64_t n);
+int basis_grid(int64_t n, int G);
 bool basis_vector_path(const sk_op* op, int64_t ldb, const void* B);
 sk_status enqueue_basis(const BasisParams& p, const sk_op* op, cudaStream_t st);
 

@@ -166,6 +166,46 @@ struct KahanAcc {
   }
 };
 
+// One tile row (W values of the compute type) in shared memory.  Rows of 32
+// bytes are stored as two 16-byte halves whose order is swapped on every
+// other group of 4 rows, so that 8 random rows read by one quarter warp spread
+// over all 8 16-byte bank groups; rows of 16 bytes or less need no swizzle.
+template <typename C, int W>
+struct TileRow {
+  static constexpr int BYTES = W * (int)sizeof(C);
+  __device__ static __forceinline__ void store(unsigned char* tile, int il, const C (&v)[W]) {
+    if constexpr (BYTES == 32) {
+      const int swz = (il >> 2) & 1;
+      uint4 h[2];
+      memcpy(&h[0], &v[0], 16);
+      memcpy(&h[1], (const char*)&v[0] + 16, 16);
+      *reinterpret_cast<uint4*>(tile + il * 32 + swz * 16) = h[0];
+      *reinterpret_cast<uint4*>(tile + il * 32 + (swz ^ 1) * 16) = h[1];
+    } else {
+#pragma unroll
+      for (int q = 0; q < W; ++q) reinterpret_cast<C*>(tile)[il * W + q] = v[q];
+    }
+  }
+  __device__ static __forceinline__ void load(const unsigned char* tile, int il, C (&v)[W]) {
+    if constexpr (BYTES == 32) {
+      const int swz = (il >> 2) & 1;
+      const uint4 a = *reinterpret_cast<const uint4*>(tile + il * 32 + swz * 16);
+      const uint4 b = *reinterpret_cast<const uint4*>(tile + il * 32 + (swz ^ 1) * 16);
+      memcpy(&v[0], &a, 16);
+      memcpy((char*)&v[0] + 16, &b, 16);
+    } else if constexpr (BYTES == 16) {
+      const uint4 a = *reinterpret_cast<const uint4*>(tile + il * 16);
+      memcpy(&v[0], &a, 16);
+    } else if constexpr (BYTES == 8) {
+      const uint2 a = *reinterpret_cast<const uint2*>(tile + il * 8);
+      memcpy(&v[0], &a, 8);
+    } else {
+#pragma unroll
+      for (int q = 0; q < W; ++q) v[q] = reinterpret_cast<const C*>(tile)[il * W + q];
+    }
+  }
+};
+
 __host__ __device__ static inline size_t entries_bytes(int zeta) { return (((size_t)kChunk * zeta * sizeof(uint16_t)) + 15) & ~(size_t)15; }
 __host__ __device__ static inline size_t rowptr_bytes(int s) { return (((size_t)(s + 1) * sizeof(uint32_t)) + 15) & ~(size_t)15; }
 
@@ -196,11 +236,13 @@ gather_apply_kernel(const T* __restrict__ B, int64_t ldb, int ncols, int64_t n, 
     const int ne = Lc * zeta;
     __syncthreads();
     for (int il = threadIdx.x; il < Lc; il += blockDim.x) {
+      C v[W];
 #pragma unroll
       for (int q = 0; q < W; ++q) {
         const int col = col0 + q;
-        tile[il * W + q] = (col < ncols) ? to_c(B[i0 + il + (int64_t)col * ldb]) : (C)0;
+        v[q] = (col < ncols) ? to_c(B[i0 + il + (int64_t)col * ldb]) : (C)0;
       }
+      TileRow<C, W>::store((unsigned char*)tile, il, v);
     }
     {
       const uint4* src = reinterpret_cast<const uint4*>(entries + (int64_t)c * kChunk * zeta);
@@ -219,7 +261,8 @@ gather_apply_kernel(const T* __restrict__ B, int64_t ldb, int ncols, int64_t n, 
         const int e0 = (int)rp_s[r], e1 = (int)rp_s[r + 1];
         for (int e = e0 + gl; e < e1; e += kGroup) {
           const uint16_t v = ent_s[e];
-          const C* src = tile + (v & 0x7FFF) * W;
+          C src[W];
+          TileRow<C, W>::load((const unsigned char*)tile, v & 0x7FFF, src);
           if (v & 0x8000) {
 #pragma unroll
             for (int q = 0; q < W; ++q) a[q] -= src[q];

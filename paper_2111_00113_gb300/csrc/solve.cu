@@ -240,7 +240,8 @@ struct BasisBuffers {
     // aligned columns for every storage type); a caller's basis has ld = n
     bp.ldb = Bext ? n : ((n + 7) / 8) * 8;
     bp.bd = bd;
-    bp.nblk = basis_grid(n);
+    bp.nblk = basis_grid(n, 1);  // the scalar path needs the most CTAs
+    bp.nblk_cap = bp.nblk;
     if (Bext) bp.B = Bext;
     else {
       unsigned char* Bp = nullptr;

@@ -144,5 +144,18 @@ def test_scale_workload_full_size(skg, dtype):
     x, info = skg.sgmres_solve(skg.Op.stencil5(N, N, coef), torch.tensor(f, device="cuda"), W["d"], W["k"], W["s"],
                                W["tol"], zeta=W["zeta"], seed=7, basis=tdt)
     assert info["status"] == 0, info
-    assert _relres(A, f, x.cpu().numpy()) <= W["tol"]
-    assert info["cycles"] <= 30
+    rel = _relres(A, f, x.cpu().numpy())
+    assert rel <= W["tol"]
+    # the FP64 oracle's run of this workload (tests/golden/scale_oracle.json,
+    # written by make_scale_reference.py from the oracle only)
+    import json, os
+    ref = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "scale_oracle.json")))
+    assert ref["relres"][-1] <= W["tol"]
+    if dtype == "f64":
+        # same algorithm, same sketch: same number of restarts (+-1) and a
+        # final residual within 1.5x of the oracle's after as many cycles
+        assert abs(info["cycles"] - ref["cycles"]) <= 1
+        c = min(info["cycles"], len(ref["relres"])) - 1
+        assert rel <= 1.5 * ref["relres"][c]
+    else:
+        assert info["cycles"] <= ref["cycles"] + 2
