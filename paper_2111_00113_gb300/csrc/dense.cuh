@@ -16,4 +16,11 @@ sk_status enqueue_qr(double* Aug, int s, int nq, int ncols, double* rdiag, doubl
 sk_status enqueue_ls_solve(const double* Aug, const double* rdiag, int s, int d, double stab_tol, double* y,
                            double* diag, cudaStream_t st);
 
+// Eigenpairs of a d x d FP64 matrix (eig.cu).  M is overwritten by its
+// Hessenberg form and reflectors; tau needs 2d entries.  Yre/Yim (d x nev)
+// receive the eigenvectors of the nev selected eigenvalues (largest real
+// part first) in the order of sel.
+sk_status enqueue_eig(double* M, int n, int nev, double* tau, double* wr, double* wi, int* sel, double* Wre,
+                      double* Wim, double* Yre, double* Yim, int* status, cudaStream_t st);
+
 }  // namespace sk

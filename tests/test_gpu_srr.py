@@ -1,0 +1,118 @@
+"""GPU parity of sketched Rayleigh-Ritz (Algorithm 2) against the CPU oracle."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import eigs, hashing, operators, sketch
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def skg():
+    import torch
+    assert torch.cuda.is_available(), "GPU test needs CUDA"
+    import paper_2111_00113_gb300 as m
+    return m
+
+
+def _true_residuals(A, lam, X):
+    out = []
+    for i in range(len(lam)):
+        x = X[:, i]
+        Ax = A @ x.real + 1j * (A @ x.imag)
+        out.append(np.linalg.norm(Ax - lam[i] * x) / np.linalg.norm(x))
+    return np.array(out)
+
+
+def test_diagonal_spectrum_exact(skg):
+    # diag(lambda) as a stencil with a diagonal shift only; d = n: sRR returns
+    # the exact extremal eigenvalues (spectrum shape of §8.3.4)
+    import torch
+    n = 64
+    lam = np.concatenate([np.linspace(-1, -0.1, 10), np.linspace(0, 1, n - 10)])
+    op = skg.Op.stencil5(n, 1, (0, 0, 0, 0, 0), torch.tensor(lam, device="cuda"))
+    w1 = torch.tensor(synth.randn(1, n), device="cuda")
+    out = skg.srr_eigs(op, w1, 10, n, 8, 2 * n, zeta=hashing.default_zeta(n), symmetric=True)
+    got = out["lam"].real.numpy()
+    assert np.allclose(got, np.sort(lam)[::-1][:10], atol=1e-8)
+
+
+def test_laplacian_1d_closed_form(skg):
+    import torch
+    n = 64
+    op = skg.Op.stencil5(n, 1, (2, -1, -1, 0, 0))
+    exact = np.sort(2 - 2 * np.cos(np.arange(1, n + 1) * np.pi / (n + 1)))[::-1]
+    out = skg.srr_eigs(op, torch.tensor(synth.randn(2, n), device="cuda"), 8, n, 4, 2 * n,
+                       zeta=hashing.default_zeta(n), symmetric=True)
+    assert np.allclose(out["lam"].real.numpy(), exact[:8], atol=1e-8)
+
+
+@pytest.mark.parametrize("kind", ["sparse", "srht"])
+def test_matches_oracle_small_nonsymmetric(skg, kind):
+    # same basis recurrence, same sketch: the extremal Ritz values and their
+    # residual estimates agree with the oracle's Algorithm 2
+    import torch
+    N, d, k, nev = 20, 40, 4, 6
+    shift = synth.uniform(1, N * N)
+    coef = synth.conv_diff_coef(N, 10.0)
+    A = operators.stencil5_matrix(N, N, coef, shift)
+    w1 = synth.randn(synth.SRR_START_SEED, N * N)
+    s = 2 * d
+    zeta = hashing.default_zeta(d)
+    op = skg.Op.stencil5(N, N, coef, torch.tensor(shift, device="cuda"))
+    out = skg.srr_eigs(op, torch.tensor(w1, device="cuda"), nev, d, k, s, zeta=zeta, seed=7, sketch=kind)
+    ref = eigs.srr(A, w1, d, k, lambda M: sketch.apply(kind, 7, s, zeta, M), nev)
+    lam = out["lam"].numpy()
+    assert np.allclose(lam, ref["lam"], rtol=1e-7, atol=1e-9)
+    assert np.allclose(out["rhat"].numpy(), ref["rhat"], rtol=1e-3, atol=1e-12)
+    X = out["X"].cpu().numpy()
+    assert np.allclose(np.linalg.norm(X, axis=0), 1, atol=1e-12)
+    # the Ritz vectors span the oracle's (complex scalar freedom): compare residuals
+    tr = _true_residuals(A, lam, X)
+    tr_ref = _true_residuals(A, ref["lam"], ref["X"])
+    assert np.allclose(tr, tr_ref, rtol=1e-4, atol=1e-10)
+
+
+def test_residual_estimate_brackets_true_residual(skg):
+    # eq. (rescompare) with the distortion measured on range([B, AB])
+    import torch
+    N, d, k, nev = 24, 30, 4, 5
+    shift = synth.uniform(3, N * N)
+    coef = synth.conv_diff_coef(N, 15.0)
+    A = operators.stencil5_matrix(N, N, coef, shift)
+    w1 = synth.randn(4, N * N)
+    op = skg.Op.stencil5(N, N, coef, torch.tensor(shift, device="cuda"))
+    out = skg.srr_eigs(op, torch.tensor(w1, device="cuda"), nev, d, k, 2 * d, seed=3)
+    lam = out["lam"].numpy()
+    tr = _true_residuals(A, lam, out["X"].cpu().numpy())
+    est = out["rhat"].numpy()
+    # generous band: s = 2d gives distortion ~1/sqrt(2) (§3.3), ratio <= ~6
+    assert np.all(tr <= 8 * est + 1e-12) and np.all(est <= 8 * tr + 1e-12)
+
+
+def test_eig_workload_full_size(skg):
+    # 512 x 512 convection-diffusion (Pe = 10) + diag(U(0,1) seed 1); the 10
+    # eigenvalues of largest real part, d = 200, k = 4, s = 400, FP32 basis,
+    # FP64 Ritz step.  Properties that hold at any size: unit Ritz vectors,
+    # sorted eigenvalues, residual estimates within the embedding factor of
+    # the true residuals recomputed on the CPU.
+    import torch
+    W = synth.WORKLOADS["eig"]
+    N = W["N"]
+    shift = synth.uniform(W["shift_seed"], N * N)
+    coef = synth.conv_diff_coef(N, W["Pe"])
+    A = operators.stencil5_matrix(N, N, coef, shift)
+    w1 = synth.randn(synth.SRR_START_SEED, N * N)
+    op = skg.Op.stencil5(N, N, coef, torch.tensor(shift, device="cuda"))
+    out = skg.srr_eigs(op, torch.tensor(w1, device="cuda"), W["nev"], W["d"], W["k"], W["s"], zeta=W["zeta"],
+                       seed=7, basis=torch.float32)
+    lam = out["lam"].numpy()
+    assert np.all(np.diff(lam.real) <= 1e-12)
+    X = out["X"].cpu().numpy()
+    assert np.allclose(np.linalg.norm(X, axis=0), 1, atol=1e-10)
+    tr = _true_residuals(A, lam, X)
+    est = out["rhat"].numpy()
+    assert np.all(tr <= 8 * est + 1e-7)
+    # the top of the spectrum lies inside the Gershgorin bound 8 + max(shift)
+    assert lam.real.max() <= 8 + shift.max() + 1e-9
