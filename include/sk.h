@@ -74,6 +74,18 @@ sk_status sk_op_transpose(const sk_op* op, sk_op** opT);
 /* y = A x in FP64 (x, y: device, n doubles; must not alias). */
 sk_status sk_op_apply(const sk_op* op, const double* x, double* y, void* stream);
 
+/* Gradient of the bilinear form lam^T A x with respect to the operator's
+ * parameters (not in the paper: the building block of the adjoint of a
+ * solve, dL/dparams = -grad(lam^T A x) with A^T lam = dL/dx).
+ * lam, x: device n doubles.  grad: device doubles, layout by op kind:
+ *   diffusion: n entries, d/dtheta_P (interior faces pass half of
+ *              (lam_P - lam_Q)(x_P - x_Q) to each cell, boundary faces lam_P x_P);
+ *   stencil5:  5 entries d/dc[0..4], then n entries d/dshift_P = lam_P x_P if
+ *              the op has a shift;
+ *   CSR:       nnz entries d/dval_e = lam_row(e) x_col(e).
+ * Asynchronous; no allocation beyond a small reduction buffer. */
+sk_status sk_op_param_grad(const sk_op* op, const double* lam, const double* x, double* grad, void* stream);
+
 int64_t sk_op_n(const sk_op* op);
 void sk_op_destroy(sk_op* op);
 

@@ -105,6 +105,24 @@ class Op:
     def __matmul__(self, x):
         return self.apply(x)
 
+    def param_grad(self, lam, x):
+        """Gradient of lam^T A x with respect to the operator's parameters.
+
+        diffusion: (n,) d/dtheta; stencil5: 5 coefficient entries (+ n shift
+        entries if the op has a shift); CSR: (nnz,) d/dval.
+        """
+        lam = _dev_f64(lam, self.n)
+        x = _dev_f64(x, self.n)
+        if self.kind == "diffusion":
+            m = self.n
+        elif self.kind == "stencil5":
+            m = 5 + (self.n if self._keep[0] is not None else 0)
+        else:
+            m = self._keep[2].numel()
+        g = torch.empty(m, dtype=torch.float64, device=lam.device)
+        N.check(N.lib.sk_op_param_grad(self._h, _ptr(lam), _ptr(x), _ptr(g), _stream()))
+        return g
+
     def __del__(self):
         h = getattr(self, "_h", None)
         if h is not None and h.value:
@@ -225,3 +243,47 @@ def srr_eigs(A, w1, nev, d, k, s, **opts):
     lam = torch.tensor([complex(a, b) for a, b in zip(lre, lim)], dtype=torch.complex128)
     return dict(lam=lam, X=torch.complex(Xr, Xi), rhat=torch.tensor(list(rh)), nconv=nconv.value,
                 info=info.as_dict())
+
+
+class DiffusionSolve(torch.autograd.Function):
+    """x = A(theta)^{-1} b by sGMRES, differentiable in theta and b.
+
+    A(theta) is the variable-coefficient diffusion operator on an nx x ny grid
+    (Op.diffusion_var).  The backward pass is the adjoint: one sGMRES solve
+    with A^T for lam = A^{-T} dL/dx (the same library kernels), then
+    dL/db = lam and dL/dtheta = -d(lam^T A x)/dtheta (Op.param_grad).
+    The paper has no differentiable solve; this is the adjoint method built on
+    Algorithm 1.
+    """
+
+    @staticmethod
+    def forward(ctx, theta, b, nx, ny, d, k, s, tol, opts):
+        op = Op.diffusion_var(nx, ny, theta.detach())
+        x, info = sgmres_solve(op, b.detach(), d, k, s, tol, **opts)
+        if info["status"] != N.SK_OK:
+            raise SkError(info["status"], "forward solve did not reach tol (relres %g)" % info["relres"])
+        ctx.save_for_backward(theta.detach(), x)
+        ctx.cfg = (nx, ny, d, k, s, tol, opts)
+        ctx.info = info
+        return x
+
+    @staticmethod
+    def backward(ctx, gx):
+        theta, x = ctx.saved_tensors
+        nx, ny, d, k, s, tol, opts = ctx.cfg
+        op = Op.diffusion_var(nx, ny, theta)
+        opT = op.T
+        gx = gx.detach().to(torch.float64).contiguous()
+        if float(gx.abs().max()) == 0.0:
+            lam = torch.zeros_like(gx)
+        else:
+            lam, info = sgmres_solve(opT, gx, d, k, s, tol, **opts)
+            if info["status"] != N.SK_OK:
+                raise SkError(info["status"], "adjoint solve did not reach tol (relres %g)" % info["relres"])
+        gtheta = -op.param_grad(lam, x)
+        return gtheta, lam, None, None, None, None, None, None, None
+
+
+def diffusion_solve(theta, b, nx, ny, d=100, k=2, s=200, tol=1e-10, **opts):
+    """Differentiable x = A(theta)^{-1} b (see DiffusionSolve)."""
+    return DiffusionSolve.apply(theta, b, nx, ny, d, k, s, tol, opts)

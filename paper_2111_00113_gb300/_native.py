@@ -17,7 +17,7 @@ SK_SPARSE_SIGN, SK_SRHT = 0, 1
 EXPORTED = [
     "sk_op_stencil5", "sk_op_diffusion_var", "sk_op_csr", "sk_op_transpose", "sk_op_apply", "sk_op_n",
     "sk_op_destroy", "sketch_apply", "sketch_apply_noalloc", "sk_opts_default", "trunc_arnoldi_basis", "sgmres_solve", "srr_eigs",
-    "sk_last_error", "sk_status_string",
+    "sk_last_error", "sk_status_string", "sk_op_param_grad",
 ]
 
 
@@ -61,6 +61,7 @@ def _load():
         "sk_op_transpose": (st, [P, C.POINTER(P)]),
         "sk_op_apply": (st, [P, P, P, P]),
         "sk_op_n": (I64, [P]),
+        "sk_op_param_grad": (st, [P, P, P, P, P]),
         "sk_op_destroy": (None, [P]),
         "sketch_apply": (st, [C.POINTER(SkSketch), P, I64, I, I, P, P]),
         "sketch_apply_noalloc": (st, [C.POINTER(SkSketch), P, I64, I, I, P, P]),

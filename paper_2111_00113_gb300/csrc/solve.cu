@@ -483,6 +483,11 @@ extern "C" sk_status sgmres_solve(const sk_op* A, const double* b, double* x, in
   struct HostFree { double* p; ~HostFree() { if (p) cudaFreeHost(p); } } hf{S.h_out};
   OpView<double> Av;
   make_view(A, &Av);
+  if (S.o.basis != SK_F64) {
+    // the op's FP32 parameter copies are allocated here, before any capture
+    OpView<float> Af;
+    SK_TRY(make_view(A, &Af, st));
+  }
   // kernels launched before the cycle loop: sketch plan (1, or 1 for SRHT
   // signs), FP32 operator copies, ||b||^2, the initial residual
   long long pre_launches = 1 + 2;
