@@ -178,6 +178,84 @@ def run_reference(args):
     return 0
 
 
+def _bench_sketch(skg, dev, peak):
+    """Standalone sketch_apply on the basis shape (2^20 x 301, s = 600)."""
+    import torch
+    n, c, s = 1 << 20, 301, 600
+    g = torch.Generator(device=dev).manual_seed(0)
+    out = {}
+    for name, dt, kind in (("sparse_f32", torch.float32, "sparse"), ("sparse_f64", torch.float64, "sparse"),
+                           ("srht_f32", torch.float32, "srht")):
+        B = torch.randn((c, n), generator=g, device=dev, dtype=dt).t()
+        skg.sketch_apply(B, s, 12, 7, kind=kind)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        reps = 3
+        for _ in range(reps):
+            skg.sketch_apply(B, s, 12, 7, kind=kind)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        gbs = B.element_size() * n * c / (ms / 1000) / 1e9
+        out[name] = {"ms": round(ms, 3), "GB/s": round(gbs, 1), "frac_hbm": round(gbs / peak, 4)}
+        del B
+    return out
+
+
+def _bench_srr(skg, dev):
+    """sRR on the 512^2 eigen workload (10 eigenpairs, d=200, k=4, s=400)."""
+    import numpy as np
+    import torch
+    import synth
+    W = synth.WORKLOADS["eig"]
+    N = W["N"]
+    shift = torch.tensor(synth.uniform(W["shift_seed"], N * N), device=dev)
+    op = skg.Op.stencil5(N, N, synth.conv_diff_coef(N, W["Pe"]), shift)
+    w1 = torch.tensor(synth.randn(synth.SRR_START_SEED, N * N), device=dev)
+    res = {}
+    for name, dt in (("f32_basis", torch.float32), ("f64_basis", torch.float64)):
+        skg.srr_eigs(op, w1, W["nev"], W["d"], W["k"], W["s"], zeta=W["zeta"], basis=dt)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        reps = 3
+        for _ in range(reps):
+            r = skg.srr_eigs(op, w1, W["nev"], W["d"], W["k"], W["s"], zeta=W["zeta"], basis=dt)
+        torch.cuda.synchronize()
+        ms = (time.perf_counter() - t) * 1000 / reps
+        res[name] = {"ms": round(ms, 2), "nconv_1e-8": r["nconv"], "max_rhat": float(r["rhat"].max()),
+                     "lam_top": float(r["lam"].real[0])}
+    return res
+
+
+def _bench_batched(skg, dev):
+    """256 convection-diffusion systems (side U{128..512}, Pe U(1,100)), 4 RHS each."""
+    import torch
+    import synth
+    W = synth.WORKLOADS["batched"]
+    sides, pes = synth.batch_systems(W["seed"], W["nsys"])
+    ops, bs = [], []
+    for i in range(W["nsys"]):
+        N = int(sides[i])
+        ops.append(skg.Op.stencil5(N, N, synth.conv_diff_coef(N, pes[i])))
+        g = torch.Generator(device=dev).manual_seed(synth.batch_rhs_seed(i, 0))
+        bs.append([torch.randn(N * N, generator=g, dtype=torch.float64, device=dev) for _ in range(W["nrhs"])])
+    kw = dict(zeta=W["zeta"], basis=torch.float32, maxit=500)
+    best, tun = skg.autotune_batch_workers(ops, bs, W["d"], W["k"], W["s"], W["tol"], candidates=(8, 16, 32),
+                                           sample=32, **kw)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    xs, stat, info = skg.sgmres_solve_batched(ops, bs, W["d"], W["k"], W["s"], W["tol"], batch_workers=best, **kw)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t
+    conv = sum(1 for st in stat if st == 0)
+    return {"jobs": len(stat), "converged_1e-6": conv, "wall_s": round(wall, 3),
+            "solves_per_s": round(conv / wall, 2), "workers": best,
+            "autotune_s": {str(k): round(v, 3) for k, v in tun.items()}, "form": "FP32 basis, FP64 refinement",
+            "maxit": 500}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -311,6 +389,10 @@ def run_ours(args):
         "clocks": clk,
         "gpu_launches": int(sum(i["launches"] for i in infos)),
     }
+    if not args.no_extras:
+        out["sketch_apply"] = _bench_sketch(skg, dev, peak)
+        out["srr"] = _bench_srr(skg, dev)
+        out["batched"] = _bench_batched(skg, dev)
     if rank == 0 and ws == 1 and not args.no_baseline:
         try:
             r = _oracle_cycle_seconds(None)
@@ -340,6 +422,7 @@ def main():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-baseline", action="store_true")
     ap.add_argument("--persistent", action="store_true", help="one cooperative kernel per basis build")
+    ap.add_argument("--no-extras", action="store_true", help="skip the sketch, sRR and batched measurements")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

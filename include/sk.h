@@ -151,6 +151,7 @@ typedef struct {
   int use_graph;           /* capture each restart cycle in a CUDA graph (default 1) */
   int persistent;          /* grid operators: build the basis in one cooperative kernel
                               with bounded grid barriers (1), or 3 launches per step (0, default) */
+  int batch_workers;       /* sgmres_solve_batched: concurrent jobs (threads x streams); 0 = 16 */
 } sk_opts;
 
 void sk_opts_default(sk_opts* o);
@@ -196,6 +197,22 @@ sk_status trunc_arnoldi_basis(const sk_op* A, const double* r0, int d, int k, sk
  * ------------------------------------------------------------------------ */
 sk_status sgmres_solve(const sk_op* A, const double* b, double* x, int d, int k, int s, double tol,
                        const sk_opts* opts, sk_info* info, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Batched restarted sGMRES: nsys independent systems A[i] with nrhs
+ * right-hand sides each (not in the paper: many small problems at once).
+ *   A: host array of nsys ops; b, x: host arrays of nsys*nrhs device
+ *   pointers (job i*nrhs + r = system i, right-hand side r); each x is the
+ *   initial guess in, the solution out.  per_job: host array of nsys*nrhs
+ *   statuses (or NULL).  info: aggregate (cycles and matvecs summed, relres
+ *   the worst job, ms summed over jobs except ms[5] = wall time).
+ * Jobs run on opts->batch_workers host threads with one stream each, largest
+ * systems first; `stream` is joined before and after.  Blocks until done.
+ * Returns SK_OK if every job converged, else the first failing job's status.
+ * ------------------------------------------------------------------------ */
+sk_status sgmres_solve_batched(int nsys, const sk_op* const* A, int nrhs, const double* const* b,
+                               double* const* x, int d, int k, int s, double tol, const sk_opts* opts,
+                               sk_status* per_job, sk_info* info, void* stream);
 
 /* ------------------------------------------------------------------------
  * Sketched Rayleigh-Ritz (Algorithm 2, §6.3-§6.4): nev eigenpairs of A with

@@ -171,7 +171,7 @@ def sketch_apply_noalloc(B, s, zeta=0, seed=7):
 
 
 def make_opts(basis=torch.float64, sketch="sparse", zeta=0, seed=7, stab_tol=0.0, maxit=10000, cgs_passes=2,
-              tau=1e-8, symmetric=False, breakdown=0.0, use_graph=True, persistent=False):
+              tau=1e-8, symmetric=False, breakdown=0.0, use_graph=True, persistent=False, batch_workers=0):
     o = N.SkOpts()
     N.lib.sk_opts_default(C.byref(o))
     o.sketch = _KIND[sketch]
@@ -186,6 +186,7 @@ def make_opts(basis=torch.float64, sketch="sparse", zeta=0, seed=7, stab_tol=0.0
     o.breakdown = float(breakdown)
     o.use_graph = int(bool(use_graph))
     o.persistent = int(bool(persistent))
+    o.batch_workers = int(batch_workers)
     return o
 
 
@@ -225,6 +226,54 @@ def sgmres_solve(A, b, d, k, s, tol, x0=None, raise_on_noconv=False, **opts):
     out = info.as_dict()
     out["status"] = st
     return x, out
+
+
+def sgmres_solve_batched(ops, bs, d, k, s, tol, x0s=None, **opts):
+    """Batched restarted sGMRES over independent jobs.
+
+    ops: list of nsys Op; bs: list of nsys lists of nrhs CUDA tensors.
+    Returns (xs like bs, per-job status list, aggregate info dict).
+    """
+    nsys = len(ops)
+    nrhs = len(bs[0])
+    flat_b = [_dev_f64(bs[i][r], ops[i].n) for i in range(nsys) for r in range(nrhs)]
+    if x0s is None:
+        flat_x = [torch.zeros_like(t) for t in flat_b]
+    else:
+        flat_x = [_dev_f64(x0s[i][r], ops[i].n).clone() for i in range(nsys) for r in range(nrhs)]
+    PA = (C.c_void_p * nsys)(*[op._h.value for op in ops])
+    PB = (C.c_void_p * (nsys * nrhs))(*[t.data_ptr() for t in flat_b])
+    PX = (C.c_void_p * (nsys * nrhs))(*[t.data_ptr() for t in flat_x])
+    stat = (C.c_int * (nsys * nrhs))()
+    o = make_opts(**opts)
+    info = N.SkInfo()
+    N.check(N.lib.sgmres_solve_batched(nsys, PA, nrhs, PB, PX, d, k, s, float(tol), C.byref(o), stat,
+                                       C.byref(info), _stream()), allow=(N.SK_OK, N.SK_ENOCONV))
+    xs = [[flat_x[i * nrhs + r] for r in range(nrhs)] for i in range(nsys)]
+    return xs, list(stat), info.as_dict()
+
+
+def autotune_batch_workers(ops, bs, d, k, s, tol, candidates=(4, 8, 16, 32, 48), sample=48, **opts):
+    """Pick the number of concurrent batched jobs by timing a sample.
+
+    The sample takes jobs spread evenly over the size range (largest first
+    ordering is what the library uses).  Returns (best, {workers: seconds}).
+    """
+    import time
+    nsys = len(ops)
+    order = sorted(range(nsys), key=lambda i: -ops[i].n)
+    pick = sorted(set(order[int(q * (nsys - 1) / max(1, min(sample, nsys) - 1))] for q in range(min(sample, nsys))))
+    sops = [ops[i] for i in pick]
+    sbs = [bs[i][:1] for i in pick]
+    timings = {}
+    for w in candidates:
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        sgmres_solve_batched(sops, sbs, d, k, s, tol, batch_workers=w, **opts)
+        torch.cuda.synchronize()
+        timings[w] = time.perf_counter() - t
+    best = min(timings, key=timings.get)
+    return best, timings
 
 
 def srr_eigs(A, w1, nev, d, k, s, **opts):

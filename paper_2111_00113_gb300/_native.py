@@ -17,7 +17,7 @@ SK_SPARSE_SIGN, SK_SRHT = 0, 1
 EXPORTED = [
     "sk_op_stencil5", "sk_op_diffusion_var", "sk_op_csr", "sk_op_transpose", "sk_op_apply", "sk_op_n",
     "sk_op_destroy", "sketch_apply", "sketch_apply_noalloc", "sk_opts_default", "trunc_arnoldi_basis", "sgmres_solve", "srr_eigs",
-    "sk_last_error", "sk_status_string", "sk_op_param_grad",
+    "sk_last_error", "sk_status_string", "sk_op_param_grad", "sgmres_solve_batched",
 ]
 
 
@@ -30,6 +30,7 @@ class SkOpts(C.Structure):
         ("sketch", C.c_int), ("zeta", C.c_int), ("seed", C.c_uint64), ("stab_tol", C.c_double),
         ("maxit", C.c_int), ("basis", C.c_int), ("cgs_passes", C.c_int), ("tau", C.c_double),
         ("symmetric", C.c_int), ("breakdown", C.c_double), ("use_graph", C.c_int), ("persistent", C.c_int),
+        ("batch_workers", C.c_int),
     ]
 
 
@@ -69,6 +70,8 @@ def _load():
         "trunc_arnoldi_basis": (st, [P, P, I, I, I, P, P, C.POINTER(SkSketch), P, P, C.POINTER(SkOpts),
                                      C.POINTER(I), P]),
         "sgmres_solve": (st, [P, P, P, I, I, I, D, C.POINTER(SkOpts), C.POINTER(SkInfo), P]),
+        "sgmres_solve_batched": (st, [I, C.POINTER(P), I, C.POINTER(P), C.POINTER(P), I, I, I, D,
+                                      C.POINTER(SkOpts), C.POINTER(C.c_int), C.POINTER(SkInfo), P]),
         "srr_eigs": (st, [P, P, I, I, I, I, C.POINTER(SkOpts), C.POINTER(D), C.POINTER(D), P, P,
                           C.POINTER(D), C.POINTER(I), C.POINTER(SkInfo), P]),
         "sk_last_error": (C.c_char_p, []),

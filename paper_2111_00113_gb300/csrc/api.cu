@@ -172,6 +172,7 @@ void sk_opts_default(sk_opts* o) {
   o->breakdown = 0;
   o->use_graph = 1;
   o->persistent = 0;
+  o->batch_workers = 0;
 }
 
 static sk_op* new_op() {

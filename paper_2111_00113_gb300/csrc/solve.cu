@@ -9,9 +9,16 @@
 //   x += B y                                  (FP64 solution update)
 //   r = b - A x, ||r||^2                      (FP64 outer residual)
 // The host reads ||r|| once per cycle to decide whether to restart.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
 #include <cmath>
 #include <cstring>
+#include <mutex>
+#include <string>
+#include <thread>
 #include <type_traits>
+#include <vector>
 
 #include "basis.cuh"
 #include "common.cuh"
@@ -434,15 +441,10 @@ static long long count_kernel_nodes(cudaGraph_t g) {
 
 }  // namespace sk
 
-extern "C" sk_status sgmres_solve(const sk_op* A, const double* b, double* x, int d, int k, int s, double tol,
-                                  const sk_opts* opts, sk_info* info, void* stream) {
-  SK_CHECK_ARG(A != nullptr && b != nullptr && x != nullptr, "NULL argument");
-  SK_CHECK_ARG(d >= 1 && k >= 1 && k <= d, "need d >= 1 and 1 <= k <= d");
-  SK_CHECK_ARG(k <= kMaxK, "k <= 16 supported");
-  SK_CHECK_ARG(s >= d + 1, "need s >= d + 1");
-  SK_CHECK_ARG(tol > 0, "tol > 0");
-  SK_CHECK_ARG(d <= 768, "d <= 768");
-  cudaStream_t st = (cudaStream_t)stream;
+// Restarted sGMRES after argument validation (also the per-job body of the
+// batched driver).
+static sk_status sgmres_impl(const sk_op* A, const double* b, double* x, int d, int k, int s, double tol,
+                             const sk_opts* opts, sk_info* info, cudaStream_t st, double* h_pinned = nullptr) {
   SolveState S;
   std::memset(&S, 0, sizeof(S));
   resolve_opts(opts, &S.o, d);
@@ -477,10 +479,12 @@ extern "C" sk_status sgmres_solve(const sk_op* A, const double* b, double* x, in
   SK_CUDA(cudaMemsetAsync(S.vec_cnt, 0, 2 * sizeof(unsigned), st));
   SK_TRY(sc.alloc(&S.out, 4));
   SK_CUDA(cudaMemsetAsync(S.out, 0, 4 * sizeof(double), st));
-  SK_CUDA(cudaMallocHost((void**)&S.h_out, 5 * sizeof(double)));
+  // pinned landing buffer for the per-cycle scalars (the caller's, or our own)
+  if (h_pinned) S.h_out = h_pinned;
+  else SK_CUDA(cudaMallocHost((void**)&S.h_out, 5 * sizeof(double)));
   S.h_err = (int*)(S.h_out + 4);
   *S.h_err = 0;
-  struct HostFree { double* p; ~HostFree() { if (p) cudaFreeHost(p); } } hf{S.h_out};
+  struct HostFree { double* p; ~HostFree() { if (p) cudaFreeHost(p); } } hf{h_pinned ? nullptr : S.h_out};
   OpView<double> Av;
   make_view(A, &Av);
   if (S.o.basis != SK_F64) {
@@ -531,17 +535,19 @@ extern "C" sk_status sgmres_solve(const sk_op* A, const double* b, double* x, in
   struct EvsFree { cudaEvent_t* e; ~EvsFree() { for (int q = 0; q < EV_COUNT; ++q) cudaEventDestroy(e[q]); } } evf{ev};
   long long kernels_per_cycle = 0;
   if (S.o.use_graph) {
-    // capture on a private stream (legacy default stream cannot capture)
-    SK_CUDA(cudaStreamCreateWithFlags(&own, cudaStreamNonBlocking));
-    cap = own;
-    SK_CUDA(cudaStreamSynchronize(st));
+    // the legacy default stream cannot be captured: use a private stream then
+    if (st == nullptr || st == cudaStreamLegacy) {
+      SK_CUDA(cudaStreamCreateWithFlags(&own, cudaStreamNonBlocking));
+      cap = own;
+      SK_CUDA(cudaStreamSynchronize(st));
+    }
     SK_CUDA(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
     sk_status cs = enqueue_cycle(S, A, Av, b, x, cap, ev, true);
     cudaError_t ce = cudaStreamEndCapture(cap, &graph);
-    if (cs != SK_OK) { cudaStreamDestroy(own); return cs; }
-    if (ce != cudaSuccess) { cudaStreamDestroy(own); return cuda_fail(ce, "cudaStreamEndCapture"); }
+    if (cs != SK_OK) { if (own) cudaStreamDestroy(own); return cs; }
+    if (ce != cudaSuccess) { if (own) cudaStreamDestroy(own); return cuda_fail(ce, "cudaStreamEndCapture"); }
     ce = cudaGraphInstantiate(&gexec, graph, 0);
-    if (ce != cudaSuccess) { cudaStreamDestroy(own); return cuda_fail(ce, "cudaGraphInstantiate"); }
+    if (ce != cudaSuccess) { if (own) cudaStreamDestroy(own); return cuda_fail(ce, "cudaGraphInstantiate"); }
     kernels_per_cycle = count_kernel_nodes(graph);
   } else {
     kernels_per_cycle = 5 + 3 + (long long)d * (S.o.cgs_passes + 1) + 2 + 1 + 2 * ((d + kQrNb - 1) / kQrNb) + 1 + 1 + 1;
@@ -603,6 +609,126 @@ extern "C" sk_status sgmres_solve(const sk_op* A, const double* b, double* x, in
   }
   if (result == SK_ENOCONV) set_error("no convergence to tol=%g in %d cycles (relres %g)", tol, cycles, relres);
   return result;
+}
+
+extern "C" sk_status sgmres_solve(const sk_op* A, const double* b, double* x, int d, int k, int s, double tol,
+                                  const sk_opts* opts, sk_info* info, void* stream) {
+  SK_CHECK_ARG(A != nullptr && b != nullptr && x != nullptr, "NULL argument");
+  SK_CHECK_ARG(d >= 1 && k >= 1 && k <= d, "need d >= 1 and 1 <= k <= d");
+  SK_CHECK_ARG(k <= kMaxK, "k <= 16 supported");
+  SK_CHECK_ARG(s >= d + 1, "need s >= d + 1");
+  SK_CHECK_ARG(tol > 0, "tol > 0");
+  SK_CHECK_ARG(d <= 768, "d <= 768");
+  return sgmres_impl(A, b, x, d, k, s, tol, opts, info, (cudaStream_t)stream);
+}
+
+// ----------------------------------------------------------------------------
+// Batched sGMRES: many independent (system, right-hand side) jobs of uneven
+// size.  A pool of worker threads, each with its own stream, takes jobs from
+// a queue ordered by decreasing size (longest-processing-time first); every
+// job runs the single-system path above (one captured graph per restart
+// cycle), so small systems from several workers fill the GPU together.
+// ----------------------------------------------------------------------------
+extern "C" sk_status sgmres_solve_batched(int nsys, const sk_op* const* A, int nrhs, const double* const* b,
+                                          double* const* x, int d, int k, int s, double tol, const sk_opts* opts,
+                                          sk_status* per_job, sk_info* info, void* stream) {
+  SK_CHECK_ARG(nsys >= 1 && nrhs >= 1, "need nsys >= 1 and nrhs >= 1");
+  SK_CHECK_ARG(A != nullptr && b != nullptr && x != nullptr, "NULL argument");
+  SK_CHECK_ARG(d >= 1 && k >= 1 && k <= d && k <= kMaxK && s >= d + 1 && tol > 0 && d <= 768,
+               "need 1 <= k <= min(d, 16), s >= d + 1, tol > 0, d <= 768");
+  const int njobs = nsys * nrhs;
+  for (int i = 0; i < nsys; ++i) SK_CHECK_ARG(A[i] != nullptr, "NULL operator");
+  for (int j = 0; j < njobs; ++j) SK_CHECK_ARG(b[j] != nullptr && x[j] != nullptr, "NULL right-hand side or solution");
+  sk_opts o;
+  if (opts) o = *opts;
+  else sk_opts_default(&o);
+  cudaStream_t st = (cudaStream_t)stream;
+  int dev = 0;
+  SK_CUDA(cudaGetDevice(&dev));
+  // FP32 parameter copies of every operator, before the workers share them
+  if (o.basis != SK_F64) {
+    for (int i = 0; i < nsys; ++i) {
+      OpView<float> Af;
+      SK_TRY(make_view(A[i], &Af, st));
+    }
+  }
+  int workers = o.batch_workers > 0 ? o.batch_workers : 16;
+  if (workers > njobs) workers = njobs;
+  if (workers > 128) workers = 128;
+  std::vector<int> order(njobs);
+  for (int j = 0; j < njobs; ++j) order[j] = j;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return A[a / nrhs]->n > A[c / nrhs]->n; });
+  cudaEvent_t start_ev;
+  SK_CUDA(cudaEventCreateWithFlags(&start_ev, cudaEventDisableTiming));
+  SK_CUDA(cudaEventRecord(start_ev, st));
+  auto t0 = std::chrono::steady_clock::now();
+  std::atomic<int> next(0);
+  std::mutex mu;
+  sk_status first_err = SK_OK;
+  std::string first_msg;
+  long long cycles = 0, matvecs = 0, launches = 0;
+  double relmax = 0, kmax = 0;
+  float msum[5] = {0, 0, 0, 0, 0};
+  std::vector<cudaEvent_t> done(workers, nullptr);
+  std::vector<std::thread> pool;
+  for (int w = 0; w < workers; ++w) {
+    pool.emplace_back([&, w]() {
+      cudaSetDevice(dev);
+      cudaStream_t ws = nullptr;
+      if (cudaStreamCreateWithFlags(&ws, cudaStreamNonBlocking) != cudaSuccess) {
+        std::lock_guard<std::mutex> lk(mu);
+        if (first_err == SK_OK) { first_err = SK_ECUDA; first_msg = "batched: stream creation failed"; }
+        return;
+      }
+      cudaStreamWaitEvent(ws, start_ev, 0);
+      double* pinned = nullptr;
+      if (cudaMallocHost((void**)&pinned, 8 * sizeof(double)) != cudaSuccess) pinned = nullptr;
+      for (;;) {
+        const int q = next.fetch_add(1);
+        if (q >= njobs) break;
+        const int job = order[q];
+        sk_info ji;
+        const sk_status r = sgmres_impl(A[job / nrhs], b[job], x[job], d, k, s, tol, &o, &ji, ws, pinned);
+        std::lock_guard<std::mutex> lk(mu);
+        if (per_job) per_job[job] = r;
+        if (r != SK_OK && first_err == SK_OK) { first_err = r; first_msg = sk_last_error(); }
+        cycles += ji.cycles;
+        matvecs += ji.matvecs;
+        launches += ji.launches;
+        if (ji.relres > relmax) relmax = ji.relres;
+        if (ji.kappa_T_max > kmax) kmax = ji.kappa_T_max;
+        for (int p = 0; p < 5; ++p) msum[p] += ji.ms[p];
+      }
+      cudaEvent_t ev;
+      if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess) {
+        cudaEventRecord(ev, ws);
+        done[w] = ev;
+      }
+      cudaStreamSynchronize(ws);
+      cudaStreamDestroy(ws);
+      if (pinned) cudaFreeHost(pinned);
+    });
+  }
+  for (auto& t : pool) t.join();
+  for (int w = 0; w < workers; ++w)
+    if (done[w]) {
+      cudaStreamWaitEvent(st, done[w], 0);
+      cudaEventDestroy(done[w]);
+    }
+  cudaEventDestroy(start_ev);
+  const double wall_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  if (info) {
+    std::memset(info, 0, sizeof(*info));
+    info->cycles = (int)(cycles > 2147483647 ? 2147483647 : cycles);
+    info->matvecs = (int)(matvecs > 2147483647 ? 2147483647 : matvecs);
+    info->relres = relmax;
+    info->kappa_T_max = kmax;
+    for (int p = 0; p < 5; ++p) info->ms[p] = msum[p];
+    info->ms[5] = (float)wall_ms;
+    info->launches = launches;
+  }
+  if (first_err != SK_OK) set_error("%s", first_msg.c_str());
+  return first_err;
 }
 
 // ----------------------------------------------------------------------------
