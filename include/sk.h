@@ -208,6 +208,8 @@ sk_status sgmres_solve(const sk_op* A, const double* b, double* x, int d, int k,
  *   the worst job, ms summed over jobs except ms[5] = wall time).
  * Jobs run on opts->batch_workers host threads with one stream each, largest
  * systems first; `stream` is joined before and after.  Blocks until done.
+ * Jobs launch their kernels directly on their streams (opts->use_graph is
+ * ignored: capturing a graph per small job costs more than it saves).
  * Returns SK_OK if every job converged, else the first failing job's status.
  * ------------------------------------------------------------------------ */
 sk_status sgmres_solve_batched(int nsys, const sk_op* const* A, int nrhs, const double* const* b,

@@ -108,9 +108,11 @@ __device__ __forceinline__ void op_apply(const OpView<C>& A, const T* __restrict
 }
 
 // Final reduction in the last block: thread t sums blocks t, t+T, ... (fixed
-// assignment), then a fixed-order block reduction.  Result in thread 0.
-template <int K>
-__device__ __forceinline__ void reduce_partials(const double* part, int nblocks, double (&tot)[K], double* sh) {
+// assignment), then a fixed-order block reduction, all in the compute type C
+// (the per-block partials already carry C's precision; on this GPU FP64
+// shuffles and adds cost 64+ cycles each).  Result in thread 0.
+template <int K, typename C>
+__device__ __forceinline__ void reduce_partials(const C* part, int nblocks, C (&tot)[K], C* sh) {
 #pragma unroll
   for (int q = 0; q < K; ++q) tot[q] = 0;
   for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
@@ -118,6 +120,12 @@ __device__ __forceinline__ void reduce_partials(const double* part, int nblocks,
     for (int q = 0; q < K; ++q) tot[q] += __ldcg(part + b * K + q);
   }
   block_sum_k<K>(tot, sh);
+}
+
+// Step j's coefficients in the compute type (see BasisParams::coef).
+template <typename C>
+__device__ __forceinline__ C* coef_row(const BasisParams& p, int j) {
+  return static_cast<C*>(p.coef) + (int64_t)j * (kMaxK + 1);
 }
 
 // ---- kernels ------------------------------------------------------------------
@@ -153,7 +161,10 @@ form_kernel(BasisParams p, OpView<typename Compute<T>::type> A, int c) {
     pdl_wait();
     pdl_trigger();
     if (c >= *p.stop) return;
-    const double inv = 1.0 / sqrt(*p.rho2);
+    __shared__ double s_inv;
+    if (threadIdx.x == 0) s_inv = 1.0 / sqrt(*p.rho2);  // once per CTA: FP64 sqrt and divide are slow here
+    __syncthreads();
+    const double inv = s_inv;
     for (int64_t i = i_begin; i < n; i += stride) {
       C v[G];
 #pragma unroll
@@ -194,10 +205,11 @@ form_kernel(BasisParams p, OpView<typename Compute<T>::type> A, int c) {
       if (i < n) gload<G>(p.M, i, m[it]);
     }
   }
+  const C* cf = coef_row<C>(p, j);
   C h[KM];
 #pragma unroll
-  for (int q = 0; q < KM; ++q) h[q] = (q < kw) ? (C)(p.h1[j * p.k + q] + p.h2[j * p.k + q]) : (C)0;
-  const C inv = (C)(1.0 / p.nu[j]);
+  for (int q = 0; q < KM; ++q) h[q] = (q < kw) ? cf[q] : (C)0;
+  const C inv = cf[kMaxK];
 #pragma unroll
   for (int it = 0; it < kIter; ++it) {
     const int64_t i = i_begin + it * stride;
@@ -223,7 +235,6 @@ __global__ void __launch_bounds__(kBasisThreads)
 dots_kernel(BasisParams p, OpView<typename Compute<T>::type> A, int j) {
   using C = typename Compute<T>::type;
   __shared__ C red[(KM + 1) * (kBasisThreads / 32)];
-  __shared__ double redd[(KM + 1) * (kBasisThreads / 32)];
   const int kw = min(p.k, j + 1);
   const int64_t n = p.n;
   const T* bj = bcol<T>(p.B, p.ldb, j);
@@ -252,8 +263,9 @@ dots_kernel(BasisParams p, OpView<typename Compute<T>::type> A, int j) {
   if (j >= *p.stop) return;
   C h[KM];
   if (PASS == 2) {
+    const C* cf = coef_row<C>(p, j);  // h1 in the compute type, written by pass 1
 #pragma unroll
-    for (int q = 0; q < KM; ++q) h[q] = (q < kw) ? (C)p.h1[j * p.k + q] : (C)0;
+    for (int q = 0; q < KM; ++q) h[q] = (q < kw) ? cf[q] : (C)0;
   }
   C acc[KM + 1];
 #pragma unroll
@@ -291,17 +303,24 @@ dots_kernel(BasisParams p, OpView<typename Compute<T>::type> A, int j) {
     }
   }
   block_sum_k<KM + 1>(acc, red);
-  double* part = p.partial;
+  C* part = reinterpret_cast<C*>(p.partial);
   if (threadIdx.x == 0) {
 #pragma unroll
-    for (int q = 0; q <= KM; ++q) part[blockIdx.x * (KM + 1) + q] = (double)acc[q];
+    for (int q = 0; q <= KM; ++q) part[blockIdx.x * (KM + 1) + q] = acc[q];
   }
   if (!last_block_arrived(p.counters + (PASS - 1))) return;
-  double tot[KM + 1];
-  reduce_partials<KM + 1>(part, (int)gridDim.x, tot, redd);
+  C tc[KM + 1];
+  reduce_partials<KM + 1>(part, (int)gridDim.x, tc, red);
   if (threadIdx.x != 0) return;
+  C* cf = coef_row<C>(p, j);
+  double tot[KM + 1];
+#pragma unroll
+  for (int q = 0; q <= KM; ++q) tot[q] = (double)tc[q];
   if (PASS == 1) {
-    for (int q = 0; q < kw; ++q) p.h1[j * p.k + q] = tot[q];
+    for (int q = 0; q < kw; ++q) {
+      p.h1[j * p.k + q] = tot[q];
+      cf[q] = tc[q];
+    }
     p.mn2[j] = tot[KM];
     if (!isfinite(tot[KM])) *p.nanflag = 1;
     if (p.passes == 2) return;
@@ -314,20 +333,23 @@ dots_kernel(BasisParams p, OpView<typename Compute<T>::type> A, int j) {
   } else {
     for (int q = 0; q < kw; ++q) p.h2[j * p.k + q] = tot[q];
   }
-  // finalise step j: nu_j and the Hessenberg column
+  // finalise step j: nu_j, the Hessenberg column and the form pass's coefficients
   double h2sq = 0;
   for (int q = 0; q < kw; ++q) h2sq += tot[q] * tot[q];
   const double nu2 = tot[KM] - h2sq;
   const double mn2 = p.mn2[j];
   bool brk = !(nu2 > p.bd * p.bd * mn2) || !(mn2 > 0);
   if (!isfinite(nu2)) { *p.nanflag = 1; brk = true; }
-  const double nu = brk ? 0.0 : sqrt(nu2);
+  const C nuc = brk ? (C)0 : sqrt((C)nu2);
+  const double nu = (double)nuc;
   p.nu[j] = nu;
-  if (p.Hbar) {
-    double* col = p.Hbar + (int64_t)j * (p.d + 1);
-    for (int q = 0; q < kw; ++q) col[j - q] = p.h1[j * p.k + q] + p.h2[j * p.k + q];
-    col[j + 1] = nu;
+  for (int q = 0; q < kw; ++q) {
+    const double hs = p.h1[j * p.k + q] + p.h2[j * p.k + q];
+    cf[q] = (C)hs;
+    if (p.Hbar) p.Hbar[(int64_t)j * (p.d + 1) + j - q] = hs;
   }
+  cf[kMaxK] = brk ? (C)0 : (C)1 / nuc;
+  if (p.Hbar) p.Hbar[(int64_t)j * (p.d + 1) + j + 1] = nu;
   if (brk) *p.stop = j + 1;
 }
 

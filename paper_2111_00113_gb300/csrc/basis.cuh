@@ -19,7 +19,10 @@ struct BasisParams {
   double* mn2;        // d: ||A b_j||^2
   double* Hbar;       // (d+1) x d or NULL (zeroed by the caller)
   double* M;          // n: A b_j in FP64 (FP64 basis only; NULL otherwise)
-  double* partial;    // nblk x (kMaxK+1) per-CTA partial sums
+  double* partial;    // nblk x (kMaxK+1) per-CTA partial sums (held in the compute type)
+  void* coef;         // d x (kMaxK+1) in the compute type: step j's combined
+                      // coefficients h1+h2 (first k) and 1/nu_j (entry kMaxK),
+                      // written once by the step's finalising thread
   unsigned* counters; // 2 last-block counters (zero)
   int* stop;          // valid basis columns (init d+1; lowered on breakdown)
   int* nanflag;       // set on NaN/Inf

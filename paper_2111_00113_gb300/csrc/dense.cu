@@ -11,9 +11,12 @@
 // its compact-WY factor T_p (Q_p = I - V T_p V^T); the trailing update
 // A <- A - V T_p^T (V^T A) runs one CTA per column.
 #include <cmath>
+#include <cooperative_groups.h>
 
 #include "common.cuh"
 #include "dense.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace sk {
 
@@ -208,11 +211,174 @@ qr_panel_kernel(double* __restrict__ Aug, int s, int p0, int nbc, double* __rest
   }
 }
 
+// Reduce-scatter of 16 per-lane values over a warp: on return lanes 2c and
+// 2c+1 hold the warp-wide sum of value c.  16 FP64 adds per lane instead of
+// the 80 of sixteen independent butterflies.
+__device__ __forceinline__ double warp_reduce_scatter16(double (&v)[16]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int h = 8, off = 16; h >= 1; h >>= 1, off >>= 1) {
+    const bool hi = (lane & off) != 0;
+#pragma unroll
+    for (int i = 0; i < h; ++i) {
+      const double send = hi ? v[i] : v[i + h];
+      const double keep = hi ? v[i + h] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+    }
+  }
+  return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
+}
+
+// Panel factorization spread over a cluster of kQrCluster CTAs.  CTA q holds
+// a contiguous block of the panel's rows in shared memory, one row per
+// thread of the row warps.  Step j needs, over the panel rows >= j and with x
+// the current column j,
+//   tot_c = sum_r P[r, c] x_r   for every panel column c,   row_c = P[j, c];
+// then with alpha = -sign(x_0) ||x|| (||x||^2 = tot_j, x_0 = row_j) and the
+// reflector v = x - alpha e_j:
+//   v^T y_c  = tot_c - alpha row_c   (c > j, applied to the later columns)
+//   v_c^T v  = tot_c - alpha row_c   (c < j, the compact-WY coupling z_c).
+// A thread folds the update of step j and the partial sums of step j+1 into
+// one pass over its own row; partials go through a warp reduce-scatter, then
+// the control warp pushes them into every CTA of the cluster (remote shared
+// stores) and a single cluster barrier per column publishes them.  All CTAs
+// sum the pushed partials in rank order, so they hold identical reflectors.
+// The control warp also extends T (Q_p = I - V T V^T) by one column per step
+// while the row warps update.  Partial slots are double-buffered by column
+// parity: a slot is rewritten two barriers after it was read.
+static constexpr int kQrCluster = 8;
+static constexpr int kQrClusterThreads = 256;
+static constexpr int kQrRowWarps = kQrClusterThreads / 32 - 1;
+
+__global__ void __launch_bounds__(kQrClusterThreads)
+qr_panel_cluster_kernel(double* __restrict__ Aug, int s, int p0, int nbc, double* __restrict__ rdiag,
+                        double* __restrict__ tau, double* __restrict__ Tws) {
+  cg::cluster_group cluster = cg::this_cluster();
+  extern __shared__ double P[];                           // rows x kQrNb, column-major (ld = per)
+  __shared__ double slot[2][kQrCluster][kQrNb];            // tot partials of every rank
+  __shared__ double rowslot[2][kQrNb];                     // row j, posted by its owner
+  __shared__ double wpart[kQrRowWarps][kQrNb];
+  __shared__ double s_T[kQrNb * kQrNb];
+  __shared__ double s_dot[kQrNb];                          // tau * v^T y_c
+  __shared__ double s_z[kQrNb];
+  __shared__ double s_v0;
+  const int q = (int)cluster.block_rank();
+  const int len = s - p0;
+  const int per = (len + kQrCluster - 1) / kQrCluster;
+  const int r0 = q * per;                                  // first panel row held by this CTA
+  const int rows = max(0, min(len, r0 + per) - r0);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const bool ctrl = (wid == kQrRowWarps);
+  const int nrt = kQrRowWarps * 32;                        // row threads
+  for (int t = threadIdx.x; t < rows * kQrNb; t += blockDim.x) {
+    const int c = t / rows, r = t - c * rows;
+    P[c * per + r] = (c < nbc) ? Aug[(int64_t)(p0 + c) * s + p0 + r0 + r] : 0.0;
+  }
+  for (int e = threadIdx.x; e < kQrNb * kQrNb; e += blockDim.x) s_T[e] = 0;
+  cluster.sync();  // every CTA of the cluster has started before the first remote store
+  for (int jj = 0; jj < nbc; ++jj) {
+    const int buf = jj & 1;
+    if (!ctrl) {
+      // update by reflector jj-1 (s_dot, s_v0 from the previous step), then partials of step jj
+      double acc[kQrNb];
+#pragma unroll
+      for (int c = 0; c < kQrNb; ++c) acc[c] = 0;
+      if (wid * 32 < rows) {
+        for (int r = threadIdx.x; r < rows; r += nrt) {
+          const int g = r0 + r;
+          if (jj > 0 && g >= jj - 1) {
+            double x = P[(jj - 1) * per + r];
+            if (g == jj - 1) {
+              x = s_v0;
+              P[(jj - 1) * per + r] = x;
+            }
+#pragma unroll
+            for (int c = 0; c < kQrNb; ++c)
+              if (c >= jj) P[c * per + r] -= s_dot[c] * x;
+          }
+          if (g >= jj) {
+            const double x = P[jj * per + r];
+#pragma unroll
+            for (int c = 0; c < kQrNb; ++c) acc[c] += P[c * per + r] * x;
+          }
+        }
+        const double w = warp_reduce_scatter16(acc);
+        if ((lane & 1) == 0) wpart[wid][lane >> 1] = w;
+      } else if (lane < 2 * kQrNb && (lane & 1) == 0) {
+        wpart[wid][lane >> 1] = 0.0;
+      }
+    }
+    __syncthreads();
+    if (ctrl) {
+      // this CTA's partial, pushed to every rank; the owner of row jj posts that row
+      if (lane < kQrNb) {
+        double a = 0;
+#pragma unroll
+        for (int w = 0; w < kQrRowWarps; ++w) a += wpart[w][lane];
+        for (int k = 0; k < kQrCluster; ++k) cluster.map_shared_rank(&slot[buf][q][0], k)[lane] = a;
+      } else if (jj >= r0 && jj < r0 + rows) {
+        const double v = P[(lane - kQrNb) * per + (jj - r0)];
+        for (int k = 0; k < kQrCluster; ++k) cluster.map_shared_rank(&rowslot[buf][0], k)[lane - kQrNb] = v;
+      }
+    }
+    cluster.sync();
+    if (ctrl) {
+      const int c = lane & (kQrNb - 1);
+      double tot = 0;
+#pragma unroll
+      for (int k = 0; k < kQrCluster; ++k) tot += slot[buf][k][c];
+      const double row = rowslot[buf][c];
+      const double nrm2 = __shfl_sync(0xffffffffu, tot, jj);
+      const double x0 = __shfl_sync(0xffffffffu, row, jj);
+      const double nrm = sqrt(nrm2);
+      const double alpha = (x0 >= 0) ? -nrm : nrm;
+      const double v0 = x0 - alpha;
+      const double vtv = nrm2 - x0 * x0 + v0 * v0;
+      const double t = (vtv > 0) ? 2.0 / vtv : 0.0;
+      const double qv = tot - alpha * row;
+      if (lane < kQrNb) {
+        s_dot[c] = (c > jj) ? t * qv : 0.0;
+        s_z[c] = (c < jj) ? qv : 0.0;
+      }
+      if (lane == 0) {
+        s_v0 = v0;
+        if (q == 0) {
+          rdiag[p0 + jj] = (vtv > 0) ? alpha : x0;
+          tau[p0 + jj] = t;
+        }
+      }
+      __syncwarp();
+      // T[:jj, jj] = -t T[:jj, :jj] z, T[jj, jj] = t (runs while the row warps update)
+      if (lane < jj) {
+        double a = 0;
+        for (int l = lane; l < jj; ++l) a += s_T[lane * kQrNb + l] * s_z[l];
+        s_T[lane * kQrNb + jj] = -t * a;
+      } else if (lane == jj) {
+        s_T[jj * kQrNb + jj] = t;
+      }
+      __syncwarp();
+    }
+    __syncthreads();
+  }
+  // the last reflector's update of the panel (only its own diagonal entry changes)
+  for (int r = threadIdx.x; r < rows; r += blockDim.x)
+    if (r0 + r == nbc - 1) P[(nbc - 1) * per + r] = s_v0;
+  __syncthreads();
+  if (q == 0)
+    for (int e = threadIdx.x; e < kQrNb * kQrNb; e += blockDim.x) Tws[e] = s_T[e];
+  for (int e = threadIdx.x; e < rows * nbc; e += blockDim.x) {
+    const int c = e / rows, r = e - c * rows;
+    Aug[(int64_t)(p0 + c) * s + p0 + r0 + r] = P[c * per + r];
+  }
+}
+
 // Column c = c0 + blockIdx.x of Aug gets Q_p^T: a <- a - V T^T (V^T a).
 __global__ void __launch_bounds__(kQrTrailThreads)
 qr_trailing_kernel(double* __restrict__ Aug, int s, int p0, int nbc, int c0, const double* __restrict__ Tws) {
-  __shared__ double red[kQrNb * (kQrTrailThreads / 32)];
+  __shared__ double red[kQrTrailThreads / 32][kQrNb];
+  __shared__ double u[kQrNb];
   __shared__ double w[kQrNb];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int c = c0 + blockIdx.x;
   double* a = Aug + (int64_t)c * s;
   const double* V = Aug + (int64_t)p0 * s;
@@ -226,22 +392,31 @@ qr_trailing_kernel(double* __restrict__ Aug, int s, int p0, int nbc, int c0, con
       if (i < nbc && r >= p0 + i) acc[i] += V[(int64_t)i * s + r] * ar;
     }
   }
-  block_sum_k<kQrNb>(acc, red);
-  if (threadIdx.x == 0) {
-    for (int i = 0; i < nbc; ++i) {
+  const double part = warp_reduce_scatter16(acc);
+  if ((lane & 1) == 0) red[wid][lane >> 1] = part;
+  __syncthreads();
+  if (wid == 0) {
+    // u = V^T a, then w = T^T u (lane i: w_i = sum_{l <= i} T[l, i] u_l)
+    if (lane < kQrNb) {
       double t = 0;
-      for (int l = 0; l <= i; ++l) t += Tws[l * kQrNb + i] * acc[l];  // (T^T w)_i
-      w[i] = t;
+      for (int q = 0; q < nw; ++q) t += red[q][lane];
+      u[lane] = t;
+    }
+    __syncwarp();
+    if (lane < kQrNb) {
+      double t = 0;
+      for (int l = 0; l <= lane && l < nbc; ++l) t += Tws[l * kQrNb + lane] * u[l];
+      w[lane] = (lane < nbc) ? t : 0.0;
     }
   }
   __syncthreads();
   for (int r = p0 + threadIdx.x; r < s; r += blockDim.x) {
-    double u = 0;
+    double d = 0;
 #pragma unroll
     for (int i = 0; i < kQrNb; ++i) {
-      if (i < nbc && r >= p0 + i) u += V[(int64_t)i * s + r] * w[i];
+      if (i < nbc && r >= p0 + i) d += V[(int64_t)i * s + r] * w[i];
     }
-    a[r] -= u;
+    a[r] -= d;
   }
 }
 
@@ -250,6 +425,26 @@ sk_status enqueue_qr(double* Aug, int s, int nq, int ncols, double* rdiag, doubl
   for (int p0 = 0; p0 < nq; p0 += kQrNb) {
     const int nbc = (nq - p0) < kQrNb ? (nq - p0) : kQrNb;
     double* T = Tws + (int64_t)(p0 / kQrNb) * kQrNb * kQrNb;
+    const int per = (s - p0 + kQrCluster - 1) / kQrCluster;
+    if (s - p0 >= 4 * kQrCluster && (size_t)per * kQrNb * sizeof(double) <= (size_t)kDynSmemLimit) {
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(kQrCluster);
+      cfg.blockDim = dim3(kQrClusterThreads);
+      cfg.dynamicSmemBytes = (size_t)per * kQrNb * sizeof(double);
+      cfg.stream = st;
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = kQrCluster;
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      SK_CUDA(cudaFuncSetAttribute(qr_panel_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kDynSmemLimit));
+      SK_CUDA(cudaLaunchKernelEx(&cfg, qr_panel_cluster_kernel, Aug, s, p0, nbc, rdiag, tau, T));
+      const int c0 = p0 + nbc;
+      if (ncols > c0) qr_trailing_kernel<<<ncols - c0, kQrTrailThreads, 0, st>>>(Aug, s, p0, nbc, c0, T);
+      continue;
+    }
     const size_t smem = (size_t)(s - p0) * nbc * sizeof(double);
     if (smem <= 200 * 1024) {
       SK_CUDA(cudaFuncSetAttribute(qr_panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kDynSmemLimit));
@@ -267,43 +462,120 @@ sk_status enqueue_qr(double* Aug, int s, int nq, int ncols, double* rdiag, doubl
 // Back substitution for the sketched LS with the kappa truncation.
 // Aug: R above the diagonal of columns [0, d), rdiag its diagonal; column d
 // holds Q^T g.  Writes y (d, zero past width) and diag = {rhat, kappa, width}.
-// Blocked from the bottom: for each block of 32 unknowns, warp 0 solves the
-// 32 x 32 triangle from shared memory with shuffles, then the whole CTA
-// subtracts the block's contribution from the rows above it.
-__global__ void __launch_bounds__(1024)
+//
+// width is the longest leading block whose diagonal is finite, nonzero and
+// has max|r_jj| <= stab_tol * min|r_jj|: a block-wide prefix max/min of the
+// |r_jj| taken on their IEEE bit patterns (ordered like the values for
+// non-negative doubles), so no FP64 division or compare chain runs serially.
+// The solve is blocked from the bottom: for each block of 32 unknowns warp 0
+// forms the 32 reciprocals of the diagonal in parallel and solves the
+// triangle with shuffles; then four threads per row subtract the block's
+// contribution from the rows above it.
+static constexpr int kLsThreads = 1024;
+
+__device__ __forceinline__ long long warp_scan_max(long long v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const long long u = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v = max(v, u);
+  }
+  return v;
+}
+__device__ __forceinline__ long long warp_scan_min(long long v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const long long u = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v = min(v, u);
+  }
+  return v;
+}
+
+__global__ void __launch_bounds__(kLsThreads)
 ls_solve_kernel(const double* __restrict__ Aug, const double* __restrict__ rdiag, int s, int d, double stab_tol,
                 double* __restrict__ y, double* __restrict__ diag) {
   extern __shared__ double zz[];  // d right-hand side entries, then the 32 x d block of R
   double* Rb = zz + d;             // Rb[c * d + t] = R[t, i0 + c]
-  __shared__ double sh[32];
+  __shared__ long long wmax[kLsThreads / 32], wmin[kLsThreads / 32];
+  __shared__ long long s_cmax, s_cmin;
   __shared__ int s_width;
-  __shared__ double s_kappa;
+  __shared__ double sh[32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const double* z = Aug + (int64_t)d * s;
+  const long long kAbs = 0x7fffffffffffffffLL;
+  const long long kInf = 0x7ff0000000000000LL;
   if (threadIdx.x == 0) {
-    double mx = 0, mn = INFINITY, kap = 1.0;
-    int width = 0;
-    for (int j = 0; j < d; ++j) {
-      const double a = fabs(rdiag[j]);
-      if (!(a > 0) || !isfinite(a)) break;
-      mx = fmax(mx, a);
-      mn = fmin(mn, a);
-      kap = mx / mn;
-      if (kap > stab_tol) break;
-      width = j + 1;
+    s_cmax = 0;
+    s_cmin = kInf;
+    s_width = d;
+  }
+  __syncthreads();
+  long long amax = 0, amin = kInf;  // over all d entries (the kappa estimate reported in diag[1])
+  for (int base = 0; base < d; base += blockDim.x) {
+    const int j = base + threadIdx.x;
+    const long long bits = (j < d) ? (__double_as_longlong(rdiag[j]) & kAbs) : 0;
+    const bool valid = (j < d);
+    long long vmax = valid ? bits : 0, vmin = valid ? bits : kInf;
+    amax = max(amax, vmax);
+    amin = min(amin, vmin);
+    vmax = warp_scan_max(vmax);
+    vmin = warp_scan_min(vmin);
+    if (lane == 31) {
+      wmax[wid] = vmax;
+      wmin[wid] = vmin;
     }
-    double mxa = 0, mna = INFINITY;
-    for (int j = 0; j < d; ++j) { const double a = fabs(rdiag[j]); mxa = fmax(mxa, a); mna = fmin(mna, a); }
-    s_kappa = (mna > 0) ? mxa / mna : INFINITY;
-    s_width = width;
+    __syncthreads();
+    long long cmax = s_cmax, cmin = s_cmin;
+    for (int w = 0; w < wid; ++w) {
+      cmax = max(cmax, wmax[w]);
+      cmin = min(cmin, wmin[w]);
+    }
+    vmax = max(vmax, cmax);
+    vmin = min(vmin, cmin);
+    // entry j fails if it is zero or not finite, or if the prefix ratio exceeds stab_tol
+    const bool bad = valid && (bits == 0 || bits >= kInf ||
+                               __longlong_as_double(vmax) > stab_tol * __longlong_as_double(vmin));
+    if (bad) atomicMin(&s_width, j);
+    __syncthreads();
+    if (threadIdx.x == blockDim.x - 1) {
+      s_cmax = vmax;
+      s_cmin = vmin;
+    }
+    __syncthreads();
+  }
+  // kappa over all d entries (zero entries give infinity)
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    amax = max(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    amin = min(amin, __shfl_xor_sync(0xffffffffu, amin, o));
+  }
+  if (lane == 0) {
+    wmax[wid] = amax;
+    wmin[wid] = amin;
   }
   __syncthreads();
   const int width = s_width;
   for (int i = threadIdx.x; i < d; i += blockDim.x) zz[i] = (i < width) ? z[i] : 0.0;
-  double part = 0;
-  for (int i = width + threadIdx.x; i < s; i += blockDim.x) part += z[i] * z[i];
-  const double rh2 = block_sum1(part, sh);
+  // rhat^2 = ||(Q^T g)[width:s]||^2 over the first four warps
+  if (wid < 4) {
+    double part = 0;
+    for (int i = width + threadIdx.x; i < s; i += 128) part += z[i] * z[i];
+    part = warp_sum(part);
+    if (lane == 0) sh[wid] = part;
+  }
   __syncthreads();
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (threadIdx.x == 0) {
+    long long mx = 0, mn = kInf;
+    for (int w = 0; w < nw; ++w) {
+      mx = max(mx, wmax[w]);
+      mn = min(mn, wmin[w]);
+    }
+    const double mna = __longlong_as_double(mn);
+    diag[0] = sqrt((sh[0] + sh[1]) + (sh[2] + sh[3]));
+    diag[1] = (mna > 0) ? __longlong_as_double(mx) / mna : INFINITY;
+    diag[2] = (double)width;
+  }
   for (int i1 = width; i1 > 0; i1 -= 32) {
     const int i0 = max(0, i1 - 32);
     const int nb = i1 - i0;
@@ -315,30 +587,33 @@ ls_solve_kernel(const double* __restrict__ Aug, const double* __restrict__ rdiag
     __syncthreads();
     if (wid == 0) {
       // lane l holds unknown i0 + l; solve bottom-up within the block
+      const double rinv = (lane < nb) ? 1.0 / Rb[lane * d + i0 + lane] : 0.0;
       double zl = (lane < nb) ? zz[i0 + lane] : 0.0;
       double yl = 0.0;
       for (int c = nb - 1; c >= 0; --c) {
-        const double yc = __shfl_sync(0xffffffffu, zl, c) / Rb[c * d + i0 + c];
-        if (lane == c) yl = yc;
+        if (lane == c) yl = zl * rinv;
+        const double yc = __shfl_sync(0xffffffffu, yl, c);
         if (lane < c) zl -= yc * Rb[c * d + i0 + lane];
       }
       if (lane < nb) zz[i0 + lane] = yl;
     }
     __syncthreads();
-    // rows above the block: zz[t] -= sum_c R[t, i0+c] y[i0+c]
-    for (int t = threadIdx.x; t < i0; t += blockDim.x) {
-      double a = zz[t];
-      for (int c = 0; c < nb; ++c) a -= Rb[c * d + t] * zz[i0 + c];
-      zz[t] = a;
+    // rows above the block: zz[t] -= sum_c R[t, i0+c] y[i0+c], four threads per row
+    {
+      const int part = threadIdx.x & 3;
+      for (int t0 = 0; t0 < i0; t0 += blockDim.x / 4) {
+        const int t = t0 + (threadIdx.x >> 2);
+        double a = 0;
+        if (t < i0)
+          for (int c = part; c < nb; c += 4) a += Rb[c * d + t] * zz[i0 + c];
+        a += __shfl_xor_sync(0xffffffffu, a, 1);
+        a += __shfl_xor_sync(0xffffffffu, a, 2);
+        if (t < i0 && part == 0) zz[t] -= a;
+      }
     }
     __syncthreads();
   }
   for (int i = threadIdx.x; i < d; i += blockDim.x) y[i] = (i < width) ? zz[i] : 0.0;
-  if (threadIdx.x == 0) {
-    diag[0] = sqrt(rh2);
-    diag[1] = s_kappa;
-    diag[2] = (double)width;
-  }
 }
 
 sk_status enqueue_ls_solve(const double* Aug, const double* rdiag, int s, int d, double stab_tol, double* y,
@@ -346,7 +621,7 @@ sk_status enqueue_ls_solve(const double* Aug, const double* rdiag, int s, int d,
   const size_t smem = (size_t)d * 33 * sizeof(double);
   if (smem > (size_t)kDynSmemLimit) { set_error("ls_solve: d too large"); return SK_EINVAL; }
   SK_CUDA(cudaFuncSetAttribute(ls_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kDynSmemLimit));
-  ls_solve_kernel<<<1, 1024, smem, st>>>(Aug, rdiag, s, d, stab_tol, y, diag);
+  ls_solve_kernel<<<1, kLsThreads, smem, st>>>(Aug, rdiag, s, d, stab_tol, y, diag);
   SK_CUDA(cudaGetLastError());
   return SK_OK;
 }

@@ -270,7 +270,8 @@ struct BasisBuffers {
       pw.spin_limit = kBarrierSpinLimit;
     }
     double* dd = nullptr;
-    const size_t nd = (size_t)2 * d * k + 2 * (size_t)d + (size_t)(d + 1) * d + (size_t)bp.nblk * (kMaxK + 1) + 2;
+    const size_t nd = (size_t)2 * d * k + 2 * (size_t)d + (size_t)(d + 1) * d + (size_t)bp.nblk * (kMaxK + 1) + 2 +
+                      (size_t)d * (kMaxK + 1);
     SK_TRY(sc.alloc(&dd, nd));
     bp.h1 = dd;
     bp.h2 = bp.h1 + (size_t)d * k;
@@ -280,6 +281,7 @@ struct BasisBuffers {
     bp.partial = bp.Hbar + (size_t)(d + 1) * d;
     double* rho2 = bp.partial + (size_t)bp.nblk * (kMaxK + 1);
     bp.rho2 = rho2;
+    bp.coef = rho2 + 2;
     unsigned* cnt = nullptr;
     SK_TRY(sc.alloc(&cnt, 8));
     SK_CUDA(cudaMemsetAsync(cnt, 0, 8 * sizeof(unsigned), sc.st));
@@ -652,6 +654,9 @@ extern "C" sk_status sgmres_solve_batched(int nsys, const sk_op* const* A, int n
       SK_TRY(make_view(A[i], &Af, st));
     }
   }
+  // Per-job graph instantiation serialises the host threads (hundreds of
+  // kernel nodes per cycle for each small job), so batched jobs launch eagerly.
+  o.use_graph = 0;
   int workers = o.batch_workers > 0 ? o.batch_workers : 16;
   if (workers > njobs) workers = njobs;
   if (workers > 128) workers = 128;
