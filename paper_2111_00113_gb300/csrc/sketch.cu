@@ -14,9 +14,13 @@
 
 namespace sk {
 
-static constexpr int kChunk = 2048;      // data rows per chunk (local index fits 15 bits)
+static constexpr int kChunk = 1024;      // data rows per chunk (local index fits 15 bits)
 static constexpr int kMaxSparseS = 4096; // embedding dimension limit of the gather path
 static constexpr int kPlanThreads = 256;
+
+// Row offsets of a chunk are stored with a stride padded to 16 bytes so that
+// they can be staged with 16-byte asynchronous copies.
+__host__ __device__ static inline int64_t rp_stride(int s) { return ((int64_t)s + 1 + 3) / 4 * 4; }
 
 int default_zeta_for(int d) {
   int z = (int)std::ceil(2.0 * std::log1p((double)d));
@@ -89,7 +93,7 @@ plan_build_kernel(int64_t n, int s, int zeta, uint64_t skey, uint32_t* __restric
     if (threadIdx.x == 0) offs[s] = (uint32_t)ne;
   }
   __syncthreads();
-  for (int r = threadIdx.x; r <= s; r += blockDim.x) rowptr[(int64_t)c * (s + 1) + r] = offs[r];
+  for (int r = threadIdx.x; r <= s; r += blockDim.x) rowptr[(int64_t)c * rp_stride(s) + r] = offs[r];
   // 4. placement (order inside a row fixed in step 5)
   for (int r = threadIdx.x; r < s; r += blockDim.x) counts[r] = offs[r];
   __syncthreads();
@@ -132,7 +136,7 @@ sk_status plan_create(SketchPlan* p, const sk_sketch* S, Scratch& scratch, cudaS
   p->seed = S->seed;
   p->L = kChunk;
   p->nchunks = (int)((S->n + kChunk - 1) / kChunk);
-  SK_TRY(scratch.alloc(&p->rowptr, (size_t)p->nchunks * (p->s + 1)));
+  SK_TRY(scratch.alloc(&p->rowptr, (size_t)p->nchunks * rp_stride(p->s)));
   SK_TRY(scratch.alloc(&p->entries, (size_t)p->nchunks * kChunk * zeta));
   SK_TRY(scratch.alloc(&p->d_status, 1));
   SK_CUDA(cudaMemsetAsync(p->d_status, 0, sizeof(int), st));
@@ -145,7 +149,8 @@ sk_status plan_create(SketchPlan* p, const sk_sketch* S, Scratch& scratch, cudaS
 }
 
 // ----------------------------------------------------------------------------
-// Gather apply: grid (column tiles, chunk groups).  For each chunk the CTA
+// Gather apply (general kernel: any storage type, s <= kMaxSparseS): grid
+// (column tiles, chunk groups).  For each chunk the CTA
 // stages the data tile (kChunk rows x W columns), the chunk's row-sorted
 // entries and its row offsets in shared memory; then each group of G lanes
 // owns one sketch row at a time, sums +-tile[local] over the row's entries,
@@ -248,7 +253,7 @@ gather_apply_kernel(const T* __restrict__ B, int64_t ldb, int ncols, int64_t n, 
       const uint4* src = reinterpret_cast<const uint4*>(entries + (int64_t)c * kChunk * zeta);
       uint4* dst = reinterpret_cast<uint4*>(ent_s);
       for (int q = threadIdx.x; q < (ne + 7) / 8; q += blockDim.x) dst[q] = __ldg(src + q);
-      const uint32_t* rp = rowptr + (int64_t)c * (s + 1);
+      const uint32_t* rp = rowptr + (int64_t)c * rp_stride(s);
       for (int q = threadIdx.x; q <= s; q += blockDim.x) rp_s[q] = __ldg(rp + q);
     }
     __syncthreads();
@@ -289,6 +294,130 @@ gather_apply_kernel(const T* __restrict__ B, int64_t ldb, int ncols, int64_t n, 
     const int r = q / W, cq = q % W;
     const int col = col0 + cq;
     if (col < ncols) partial[((int64_t)g * ncols + col) * s + r] = (double)acc_hi[q] - (double)acc_lo[q];
+  }
+}
+
+// ----------------------------------------------------------------------------
+// Row-owner gather for FP32 data (s <= kRowsMaxS): thread r owns sketch row
+// r for a tile of kRowsW columns and keeps its sums in registers across all
+// chunks of its group (a plain FP32 sum per chunk, folded into a TwoSum
+// compensated pair once per chunk).  Chunks are double-buffered with
+// asynchronous copies: while chunk c is gathered, chunk c+1's data tile,
+// entries and row offsets land in the other buffer.  Tile rows are 64 bytes
+// (16 floats) whose four 16-byte segments are rotated by (row >> 1), so the
+// staging copies (8 consecutive rows x 4 columns per warp instruction) hit
+// 32 distinct banks.
+// ----------------------------------------------------------------------------
+static constexpr int kRowsW = 16;
+static constexpr int kRowsMaxS = 640;
+
+__device__ __forceinline__ void cp_async4(void* dst, const void* src, bool valid) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
+  const int n = valid ? 4 : 0;  // zero-fill when out of range
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sa), "l"(src), "r"(n) : "memory");
+}
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+__host__ __device__ static inline size_t rows_buf_bytes(int s, int zeta) {
+  return (size_t)kChunk * kRowsW * sizeof(float) + entries_bytes(zeta) + (size_t)rp_stride(s) * sizeof(uint32_t);
+}
+
+__global__ void __launch_bounds__(kRowsMaxS)
+gather_rows_kernel(const float* __restrict__ B, int64_t ldb, int ncols, int64_t n, int s, int zeta, int nchunks,
+                   int chunks_per_group, const uint32_t* __restrict__ rowptr, const uint16_t* __restrict__ entries,
+                   double* __restrict__ partial) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const size_t buf_bytes = rows_buf_bytes(s, zeta);
+  const int col0 = blockIdx.x * kRowsW;
+  const int g = blockIdx.y;
+  const int c_begin = g * chunks_per_group;
+  const int c_end = min(nchunks, c_begin + chunks_per_group);
+  const int nt = blockDim.x;
+  const int lane = threadIdx.x & 31;
+  const int ent_copies = (int)(entries_bytes(zeta) / 16);
+  const int rp_copies = (int)(rp_stride(s) / 4);
+
+  auto stage = [&](int c, int b) {
+    unsigned char* base = smem_raw + (size_t)b * buf_bytes;
+    const int64_t i0 = (int64_t)c * kChunk;
+    const int Lc = (int)((n - i0) < kChunk ? (n - i0) : kChunk);
+    // data tile: warp instruction = 8 consecutive rows x 4 consecutive columns
+    for (int q0 = threadIdx.x - lane; q0 < kChunk * kRowsW; q0 += nt) {
+      const int gq = q0 >> 5;                       // group of 32 elements
+      const int rb = gq % (kChunk / 8), cg = gq / (kChunk / 8);
+      const int il = rb * 8 + (lane & 7);
+      const int w = lane >> 3;
+      const int col = cg * 4 + w;
+      const bool ok = il < Lc && col0 + col < ncols;
+      const float* src = ok ? B + (i0 + il) + (int64_t)(col0 + col) * ldb : B;
+      unsigned char* dst = base + (size_t)il * 64 + (size_t)(((cg + (il >> 1)) & 3) * 16 + w * 4);
+      cp_async4(dst, src, ok);
+    }
+    const unsigned char* esrc = reinterpret_cast<const unsigned char*>(entries + (int64_t)c * kChunk * zeta);
+    unsigned char* edst = base + (size_t)kChunk * kRowsW * sizeof(float);
+    for (int q = threadIdx.x; q < ent_copies; q += nt) cp_async16(edst + q * 16, esrc + q * 16);
+    const unsigned char* rsrc = reinterpret_cast<const unsigned char*>(rowptr + (int64_t)c * rp_stride(s));
+    unsigned char* rdst = edst + entries_bytes(zeta);
+    for (int q = threadIdx.x; q < rp_copies; q += nt) cp_async16(rdst + q * 16, rsrc + q * 16);
+  };
+
+  float hi[kRowsW], lo[kRowsW];
+#pragma unroll
+  for (int q = 0; q < kRowsW; ++q) { hi[q] = 0.f; lo[q] = 0.f; }
+  const int r = threadIdx.x;
+  if (c_begin < c_end) stage(c_begin, 0);
+  cp_async_commit();
+  for (int c = c_begin; c < c_end; ++c) {
+    const int b = (c - c_begin) & 1;
+    if (c + 1 < c_end) stage(c + 1, b ^ 1);
+    cp_async_commit();
+    cp_async_wait1();
+    __syncthreads();
+    const unsigned char* base = smem_raw + (size_t)b * buf_bytes;
+    const uint16_t* ent = reinterpret_cast<const uint16_t*>(base + (size_t)kChunk * kRowsW * sizeof(float));
+    const uint32_t* rp = reinterpret_cast<const uint32_t*>(base + (size_t)kChunk * kRowsW * sizeof(float) +
+                                                           entries_bytes(zeta));
+    if (r < s) {
+      float acc[kRowsW];
+#pragma unroll
+      for (int q = 0; q < kRowsW; ++q) acc[q] = 0.f;
+      const int e0 = (int)rp[r], e1 = (int)rp[r + 1];
+      for (int e = e0; e < e1; ++e) {
+        const uint16_t v = ent[e];
+        const int il = v & 0x7FFF;
+        const float sg = (v & 0x8000) ? -1.f : 1.f;
+        const unsigned char* row = base + (size_t)il * 64;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const float4 x = *reinterpret_cast<const float4*>(row + ((k + (il >> 1)) & 3) * 16);
+          acc[4 * k + 0] = fmaf(sg, x.x, acc[4 * k + 0]);
+          acc[4 * k + 1] = fmaf(sg, x.y, acc[4 * k + 1]);
+          acc[4 * k + 2] = fmaf(sg, x.z, acc[4 * k + 2]);
+          acc[4 * k + 3] = fmaf(sg, x.w, acc[4 * k + 3]);
+        }
+      }
+      // TwoSum (Knuth) fold of the chunk sum into the compensated pair
+#pragma unroll
+      for (int q = 0; q < kRowsW; ++q) {
+        const float t = hi[q] + acc[q];
+        const float bp = t - hi[q];
+        lo[q] += (hi[q] - (t - bp)) + (acc[q] - bp);
+        hi[q] = t;
+      }
+    }
+    __syncthreads();  // buffer b is restaged by the next iteration's prefetch
+  }
+  if (r < s) {
+#pragma unroll
+    for (int q = 0; q < kRowsW; ++q) {
+      const int col = col0 + q;
+      if (col < ncols) partial[((int64_t)g * ncols + col) * s + r] = (double)hi[q] + (double)lo[q];
+    }
   }
 }
 
@@ -340,13 +469,16 @@ static int pick_width(int s, int zeta, int ncols, size_t csize) {
 }
 
 struct GatherShape {
+  bool rows;  // row-owner kernel (FP32 data, s <= kRowsMaxS, at least kRowsW columns)
   int W, ntiles, ngroups, cpg;
 };
 
 static GatherShape gather_shape(const SketchPlan& p, int ncols, sk_dtype dtype) {
   GatherShape g;
   const size_t csize = dtype == SK_F64 ? 8 : 4;
-  g.W = pick_width(p.s, p.zeta, ncols, csize);
+  g.rows = dtype == SK_F32 && p.s <= kRowsMaxS && ncols >= kRowsW &&
+           2 * rows_buf_bytes(p.s, p.zeta) <= (size_t)kDynSmemLimit;
+  g.W = g.rows ? kRowsW : pick_width(p.s, p.zeta, ncols, csize);
   g.ntiles = (ncols + g.W - 1) / g.W;
   const int target = num_sms();
   int ngroups = (target + g.ntiles - 1) / g.ntiles;
@@ -355,6 +487,18 @@ static GatherShape gather_shape(const SketchPlan& p, int ncols, sk_dtype dtype) 
   g.cpg = (p.nchunks + ngroups - 1) / ngroups;
   g.ngroups = (p.nchunks + g.cpg - 1) / g.cpg;
   return g;
+}
+
+static sk_status launch_rows(const SketchPlan& p, const float* B, int64_t ldb, int ncols, double* partial,
+                             const GatherShape& g, cudaStream_t st) {
+  const size_t smem = 2 * rows_buf_bytes(p.s, p.zeta);
+  SK_CUDA(cudaFuncSetAttribute(gather_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kDynSmemLimit));
+  const int threads = (p.s + 31) / 32 * 32;
+  dim3 grid(g.ntiles, g.ngroups);
+  gather_rows_kernel<<<grid, threads, smem, st>>>(B, ldb, ncols, p.n, p.s, p.zeta, p.nchunks, g.cpg, p.rowptr,
+                                                  p.entries, partial);
+  SK_CUDA(cudaGetLastError());
+  return SK_OK;
 }
 
 size_t plan_ws_doubles(const SketchPlan& p, int ncols, sk_dtype dtype) {
@@ -367,6 +511,7 @@ sk_status plan_apply_ws(const SketchPlan& p, const void* B, int64_t ldb, int nco
   const GatherShape g = gather_shape(p, ncols, dtype);
   sk_status stt;
   if (dtype == SK_F64) stt = gather_dispatch<double>(p, (const double*)B, ldb, ncols, partial, g.ngroups, g.cpg, g.W, st);
+  else if (dtype == SK_F32 && g.rows) stt = launch_rows(p, (const float*)B, ldb, ncols, partial, g, st);
   else if (dtype == SK_F32) stt = gather_dispatch<float>(p, (const float*)B, ldb, ncols, partial, g.ngroups, g.cpg, g.W, st);
   else stt = gather_dispatch<__nv_bfloat16>(p, (const __nv_bfloat16*)B, ldb, ncols, partial, g.ngroups, g.cpg, g.W, st);
   if (stt != SK_OK) return stt;
@@ -480,7 +625,7 @@ extern "C" sk_status sketch_apply_noalloc(const sk_sketch* S, const void* B, int
   p.L = kChunk;
   p.nchunks = (int)((S->n + kChunk - 1) / kChunk);
   const size_t b_status = align256(sizeof(int));
-  const size_t b_rowptr = align256((size_t)p.nchunks * (p.s + 1) * sizeof(uint32_t));
+  const size_t b_rowptr = align256((size_t)p.nchunks * rp_stride(p.s) * sizeof(uint32_t));
   const size_t b_entries = align256((size_t)p.nchunks * kChunk * zeta * sizeof(uint16_t));
   const size_t b_partial = align256(plan_ws_doubles(p, ncols, dtype) * sizeof(double));
   const size_t need = b_status + b_rowptr + b_entries + b_partial;

@@ -60,6 +60,20 @@ def test_sparse_sign_low_precision(skg, dtype):
     assert _relf(got, ref) <= 1e-5
 
 
+@pytest.mark.parametrize("n,c,s,zeta", [(1024 * 5 + 3, 37, 600, 12), (1024 * 40 + 1000, 16, 33, 5),
+                                        (1000, 20, 640, 14), (1024 * 3, 301, 200, 10)])
+def test_sparse_sign_fp32_row_owner(skg, n, c, s, zeta):
+    # FP32 data with at least 16 columns and s <= 640 (the row-owner gather):
+    # ragged last chunk, ragged last column tile, partial last warp of rows
+    import torch
+    X = np.random.default_rng(n + c).standard_normal((n, c))
+    Xt = _tensor(X, torch.float32)
+    Xr = Xt.to(torch.float64).cpu().numpy()
+    got = skg.sketch_apply(Xt, s, zeta, 3).cpu().numpy()
+    ref = sketch.sparse_sign_apply(3, s, zeta, Xr)
+    assert _relf(got, ref) <= 1e-6
+
+
 def test_sparse_sign_vector_and_strided(skg):
     import torch
     n = 3000
