@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <cmath>
 #include <mutex>
+#include <type_traits>
 #include <vector>
 
 #include "common.cuh"
@@ -103,7 +104,7 @@ plan_build_kernel(int64_t n, int s, int zeta, uint64_t skey, uint32_t* __restric
     sorted[pos] = (uint16_t)((e / zeta) | (p & 0x8000));
   }
   __syncthreads();
-  // 5. sort each row's entries by local index (deterministic order)
+  // 5. sort each row's entries by local index (a deterministic start for step 6)
   for (int r = threadIdx.x; r < s; r += blockDim.x) {
     const int b = (int)offs[r], e = (int)offs[r + 1];
     for (int q = b + 1; q < e; ++q) {
@@ -111,6 +112,45 @@ plan_build_kernel(int64_t n, int s, int zeta, uint64_t skey, uint32_t* __restric
       int p = q - 1;
       while (p >= b && (sorted[p] & 0x7FFF) > (v & 0x7FFF)) { sorted[p + 1] = sorted[p]; --p; }
       sorted[p + 1] = v;
+    }
+  }
+  __syncthreads();
+  // 6. bank-aware order: the row-owner gather reads, at each step, one entry
+  // of each of 8 consecutive rows with one quarter-warp phase of a 16-byte
+  // shared load, whose bank group is fixed by the tile row (rows of 64
+  // bytes whose segments rotate by row >> 1: group ((il & 1), (il >> 1) & 3)).
+  // Greedily give each of the 8 rows, step by step, a remaining entry whose
+  // group is least used in that step so far (first such entry: deterministic).
+  for (int Q = threadIdx.x; Q * 8 < s; Q += blockDim.x) {
+    const int ra = Q * 8, nr = min(8, s - ra);
+    int pos[8], end[8];
+    for (int l = 0; l < 8; ++l) {
+      pos[l] = (l < nr) ? (int)offs[ra + l] : 0;
+      end[l] = (l < nr) ? (int)offs[ra + l + 1] : 0;
+    }
+    for (;;) {
+      int cnt[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+      bool any = false;
+      for (int l = 0; l < nr; ++l) {
+        if (pos[l] >= end[l]) continue;
+        any = true;
+        int best = pos[l], bc = 1 << 30;
+        for (int q = pos[l]; q < end[l]; ++q) {
+          const int il = sorted[q] & 0x7FFF;
+          const int gq = ((il & 1) << 2) | ((il >> 1) & 3);
+          if (cnt[gq] < bc) {
+            bc = cnt[gq];
+            best = q;
+          }
+        }
+        const uint16_t t = sorted[best];
+        sorted[best] = sorted[pos[l]];
+        sorted[pos[l]] = t;
+        const int il = t & 0x7FFF;
+        ++cnt[((il & 1) << 2) | ((il >> 1) & 3)];
+        ++pos[l];
+      }
+      if (!any) break;
     }
   }
   __syncthreads();
@@ -298,23 +338,31 @@ gather_apply_kernel(const T* __restrict__ B, int64_t ldb, int ncols, int64_t n, 
 }
 
 // ----------------------------------------------------------------------------
-// Row-owner gather for FP32 data (s <= kRowsMaxS): thread r owns sketch row
-// r for a tile of kRowsW columns and keeps its sums in registers across all
-// chunks of its group (a plain FP32 sum per chunk, folded into a TwoSum
-// compensated pair once per chunk).  Chunks are double-buffered with
-// asynchronous copies: while chunk c is gathered, chunk c+1's data tile,
-// entries and row offsets land in the other buffer.  Tile rows are 64 bytes
-// (16 floats) whose four 16-byte segments are rotated by (row >> 1), so the
-// staging copies (8 consecutive rows x 4 columns per warp instruction) hit
-// 32 distinct banks.
+// Row-owner gather (FP32 or FP64 data, s <= kRowsMaxS): thread r owns sketch
+// row r for a tile of 64 bytes of columns (16 floats or 8 doubles) and keeps
+// its sums in registers across all chunks of its group.  FP32 data: a plain
+// FP32 sum per chunk, folded into a TwoSum-compensated pair once per chunk;
+// FP64 data: plain FP64 sums.  Chunks are double-buffered with asynchronous
+// copies: while chunk c is gathered, chunk c+1's data tile, entries and row
+// offsets land in the other buffer.  A tile row's four 16-byte segments are
+// rotated by (row >> 1), so the staging copies (8 consecutive rows x 4
+// consecutive columns per warp instruction) spread evenly over the banks.
 // ----------------------------------------------------------------------------
-static constexpr int kRowsW = 16;
+static constexpr int kRowsBytes = 64;  // bytes of one tile row
 static constexpr int kRowsMaxS = 640;
+template <typename T>
+struct RowsW {
+  static constexpr int value = kRowsBytes / (int)sizeof(T);
+};
 
-__device__ __forceinline__ void cp_async4(void* dst, const void* src, bool valid) {
+template <int E>
+__device__ __forceinline__ void cp_async_e(void* dst, const void* src, bool valid) {
   const unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
-  const int n = valid ? 4 : 0;  // zero-fill when out of range
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sa), "l"(src), "r"(n) : "memory");
+  const int n = valid ? E : 0;  // zero-fill when out of range
+  if constexpr (E == 4)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sa), "l"(src), "r"(n) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(sa), "l"(src), "r"(n) : "memory");
 }
 __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
   const unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
@@ -324,16 +372,45 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 
 __host__ __device__ static inline size_t rows_buf_bytes(int s, int zeta) {
-  return (size_t)kChunk * kRowsW * sizeof(float) + entries_bytes(zeta) + (size_t)rp_stride(s) * sizeof(uint32_t);
+  return (size_t)kChunk * kRowsBytes + entries_bytes(zeta) + (size_t)rp_stride(s) * sizeof(uint32_t);
 }
 
+// Accumulate one 16-byte segment (k-th of the row) into acc.
+__device__ __forceinline__ void seg_acc4(float (&acc)[16], int k, const float4& x, float sg) {
+  acc[4 * k + 0] = fmaf(sg, x.x, acc[4 * k + 0]);
+  acc[4 * k + 1] = fmaf(sg, x.y, acc[4 * k + 1]);
+  acc[4 * k + 2] = fmaf(sg, x.z, acc[4 * k + 2]);
+  acc[4 * k + 3] = fmaf(sg, x.w, acc[4 * k + 3]);
+}
+__device__ __forceinline__ void seg_acc4(double (&acc)[8], int k, const double2& x, float sg) {
+  const double sd = (double)sg;
+  acc[2 * k + 0] = fma(sd, x.x, acc[2 * k + 0]);
+  acc[2 * k + 1] = fma(sd, x.y, acc[2 * k + 1]);
+}
+__device__ __forceinline__ void seg_acc(float (&acc)[16], int k, const unsigned char* p, float sg) {
+  const float4 x = *reinterpret_cast<const float4*>(p);
+  acc[4 * k + 0] = fmaf(sg, x.x, acc[4 * k + 0]);
+  acc[4 * k + 1] = fmaf(sg, x.y, acc[4 * k + 1]);
+  acc[4 * k + 2] = fmaf(sg, x.z, acc[4 * k + 2]);
+  acc[4 * k + 3] = fmaf(sg, x.w, acc[4 * k + 3]);
+}
+__device__ __forceinline__ void seg_acc(double (&acc)[8], int k, const unsigned char* p, float sg) {
+  const double2 x = *reinterpret_cast<const double2*>(p);
+  const double sd = (double)sg;  // +-1: the product is exact, so this is an add or a subtract without divergence
+  acc[2 * k + 0] = fma(sd, x.x, acc[2 * k + 0]);
+  acc[2 * k + 1] = fma(sd, x.y, acc[2 * k + 1]);
+}
+
+template <typename T>
 __global__ void __launch_bounds__(kRowsMaxS)
-gather_rows_kernel(const float* __restrict__ B, int64_t ldb, int ncols, int64_t n, int s, int zeta, int nchunks,
+gather_rows_kernel(const T* __restrict__ B, int64_t ldb, int ncols, int64_t n, int s, int zeta, int nchunks,
                    int chunks_per_group, const uint32_t* __restrict__ rowptr, const uint16_t* __restrict__ entries,
                    double* __restrict__ partial) {
+  constexpr int E = (int)sizeof(T);
+  constexpr int W = RowsW<T>::value;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const size_t buf_bytes = rows_buf_bytes(s, zeta);
-  const int col0 = blockIdx.x * kRowsW;
+  const int col0 = blockIdx.x * W;
   const int g = blockIdx.y;
   const int c_begin = g * chunks_per_group;
   const int c_end = min(nchunks, c_begin + chunks_per_group);
@@ -347,28 +424,29 @@ gather_rows_kernel(const float* __restrict__ B, int64_t ldb, int ncols, int64_t 
     const int64_t i0 = (int64_t)c * kChunk;
     const int Lc = (int)((n - i0) < kChunk ? (n - i0) : kChunk);
     // data tile: warp instruction = 8 consecutive rows x 4 consecutive columns
-    for (int q0 = threadIdx.x - lane; q0 < kChunk * kRowsW; q0 += nt) {
-      const int gq = q0 >> 5;                       // group of 32 elements
+    for (int q0 = threadIdx.x - lane; q0 < kChunk * W; q0 += nt) {
+      const int gq = q0 >> 5;
       const int rb = gq % (kChunk / 8), cg = gq / (kChunk / 8);
       const int il = rb * 8 + (lane & 7);
-      const int w = lane >> 3;
-      const int col = cg * 4 + w;
+      const int col = cg * 4 + (lane >> 3);
       const bool ok = il < Lc && col0 + col < ncols;
-      const float* src = ok ? B + (i0 + il) + (int64_t)(col0 + col) * ldb : B;
-      unsigned char* dst = base + (size_t)il * 64 + (size_t)(((cg + (il >> 1)) & 3) * 16 + w * 4);
-      cp_async4(dst, src, ok);
+      const T* src = ok ? B + (i0 + il) + (int64_t)(col0 + col) * ldb : B;
+      const int byte = col * E;  // byte of the column inside the unrotated row
+      unsigned char* dst = smem_raw + (size_t)b * buf_bytes + (size_t)il * kRowsBytes +
+                           (size_t)((((byte >> 4) + (il >> 1)) & 3) * 16 + (byte & 15));
+      cp_async_e<E>(dst, src, ok);
     }
     const unsigned char* esrc = reinterpret_cast<const unsigned char*>(entries + (int64_t)c * kChunk * zeta);
-    unsigned char* edst = base + (size_t)kChunk * kRowsW * sizeof(float);
+    unsigned char* edst = base + (size_t)kChunk * kRowsBytes;
     for (int q = threadIdx.x; q < ent_copies; q += nt) cp_async16(edst + q * 16, esrc + q * 16);
     const unsigned char* rsrc = reinterpret_cast<const unsigned char*>(rowptr + (int64_t)c * rp_stride(s));
     unsigned char* rdst = edst + entries_bytes(zeta);
     for (int q = threadIdx.x; q < rp_copies; q += nt) cp_async16(rdst + q * 16, rsrc + q * 16);
   };
 
-  float hi[kRowsW], lo[kRowsW];
+  T hi[W], lo[W];
 #pragma unroll
-  for (int q = 0; q < kRowsW; ++q) { hi[q] = 0.f; lo[q] = 0.f; }
+  for (int q = 0; q < W; ++q) { hi[q] = 0; lo[q] = 0; }
   const int r = threadIdx.x;
   if (c_begin < c_end) stage(c_begin, 0);
   cp_async_commit();
@@ -379,42 +457,63 @@ gather_rows_kernel(const float* __restrict__ B, int64_t ldb, int ncols, int64_t 
     cp_async_wait1();
     __syncthreads();
     const unsigned char* base = smem_raw + (size_t)b * buf_bytes;
-    const uint16_t* ent = reinterpret_cast<const uint16_t*>(base + (size_t)kChunk * kRowsW * sizeof(float));
-    const uint32_t* rp = reinterpret_cast<const uint32_t*>(base + (size_t)kChunk * kRowsW * sizeof(float) +
-                                                           entries_bytes(zeta));
+    const uint16_t* ent = reinterpret_cast<const uint16_t*>(base + (size_t)kChunk * kRowsBytes);
+    const uint32_t* rp = reinterpret_cast<const uint32_t*>(base + (size_t)kChunk * kRowsBytes + entries_bytes(zeta));
     if (r < s) {
-      float acc[kRowsW];
+      T acc[W];
 #pragma unroll
-      for (int q = 0; q < kRowsW; ++q) acc[q] = 0.f;
+      for (int q = 0; q < W; ++q) acc[q] = 0;
       const int e0 = (int)rp[r], e1 = (int)rp[r + 1];
-      for (int e = e0; e < e1; ++e) {
-        const uint16_t v = ent[e];
-        const int il = v & 0x7FFF;
-        const float sg = (v & 0x8000) ? -1.f : 1.f;
-        const unsigned char* row = base + (size_t)il * 64;
+      // two entries per iteration (eight 16-byte loads in flight), the next
+      // two entry words fetched one iteration ahead
+      int e = e0;
+      uint32_t va = (e < e1) ? ent[e] : 0u, vb = (e + 1 < e1) ? ent[e + 1] : 0u;
+      for (; e + 1 < e1; e += 2) {
+        const uint32_t na = (e + 2 < e1) ? ent[e + 2] : 0u, nb = (e + 3 < e1) ? ent[e + 3] : 0u;
+        const int ia = va & 0x7FFF, ib = vb & 0x7FFF;
+        const unsigned char* ra_ = base + (size_t)ia * kRowsBytes;
+        const unsigned char* rb_ = base + (size_t)ib * kRowsBytes;
+        using V16 = typename std::conditional<E == 4, float4, double2>::type;  // one 16-byte segment
+        V16 xa[4], xb[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-          const float4 x = *reinterpret_cast<const float4*>(row + ((k + (il >> 1)) & 3) * 16);
-          acc[4 * k + 0] = fmaf(sg, x.x, acc[4 * k + 0]);
-          acc[4 * k + 1] = fmaf(sg, x.y, acc[4 * k + 1]);
-          acc[4 * k + 2] = fmaf(sg, x.z, acc[4 * k + 2]);
-          acc[4 * k + 3] = fmaf(sg, x.w, acc[4 * k + 3]);
+          xa[k] = *reinterpret_cast<const V16*>(ra_ + ((k + (ia >> 1)) & 3) * 16);
+          xb[k] = *reinterpret_cast<const V16*>(rb_ + ((k + (ib >> 1)) & 3) * 16);
         }
-      }
-      // TwoSum (Knuth) fold of the chunk sum into the compensated pair
+        const float sa = (va & 0x8000) ? -1.f : 1.f, sb = (vb & 0x8000) ? -1.f : 1.f;
 #pragma unroll
-      for (int q = 0; q < kRowsW; ++q) {
-        const float t = hi[q] + acc[q];
-        const float bp = t - hi[q];
-        lo[q] += (hi[q] - (t - bp)) + (acc[q] - bp);
-        hi[q] = t;
+        for (int k = 0; k < 4; ++k) {
+          seg_acc4(acc, k, xa[k], sa);
+          seg_acc4(acc, k, xb[k], sb);
+        }
+        va = na;
+        vb = nb;
+      }
+      if (e < e1) {
+        const int il = va & 0x7FFF;
+        const float sg = (va & 0x8000) ? -1.f : 1.f;
+        const unsigned char* row = base + (size_t)il * kRowsBytes;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) seg_acc(acc, k, row + ((k + (il >> 1)) & 3) * 16, sg);
+      }
+#pragma unroll
+      for (int q = 0; q < W; ++q) {
+        if constexpr (E == 4) {
+          // TwoSum (Knuth) fold of the chunk sum into the compensated pair
+          const float t = hi[q] + acc[q];
+          const float bp = t - hi[q];
+          lo[q] += (hi[q] - (t - bp)) + (acc[q] - bp);
+          hi[q] = t;
+        } else {
+          hi[q] += acc[q];
+        }
       }
     }
     __syncthreads();  // buffer b is restaged by the next iteration's prefetch
   }
   if (r < s) {
 #pragma unroll
-    for (int q = 0; q < kRowsW; ++q) {
+    for (int q = 0; q < W; ++q) {
       const int col = col0 + q;
       if (col < ncols) partial[((int64_t)g * ncols + col) * s + r] = (double)hi[q] + (double)lo[q];
     }
@@ -469,16 +568,17 @@ static int pick_width(int s, int zeta, int ncols, size_t csize) {
 }
 
 struct GatherShape {
-  bool rows;  // row-owner kernel (FP32 data, s <= kRowsMaxS, at least kRowsW columns)
+  bool rows;  // row-owner kernel (FP32/FP64 data, s <= kRowsMaxS, at least one full tile of columns)
   int W, ntiles, ngroups, cpg;
 };
 
 static GatherShape gather_shape(const SketchPlan& p, int ncols, sk_dtype dtype) {
   GatherShape g;
   const size_t csize = dtype == SK_F64 ? 8 : 4;
-  g.rows = dtype == SK_F32 && p.s <= kRowsMaxS && ncols >= kRowsW &&
+  const int rows_w = kRowsBytes / (int)csize;
+  g.rows = (dtype == SK_F32 || dtype == SK_F64) && p.s <= kRowsMaxS && ncols >= rows_w &&
            2 * rows_buf_bytes(p.s, p.zeta) <= (size_t)kDynSmemLimit;
-  g.W = g.rows ? kRowsW : pick_width(p.s, p.zeta, ncols, csize);
+  g.W = g.rows ? rows_w : pick_width(p.s, p.zeta, ncols, csize);
   g.ntiles = (ncols + g.W - 1) / g.W;
   const int target = num_sms();
   int ngroups = (target + g.ntiles - 1) / g.ntiles;
@@ -489,14 +589,15 @@ static GatherShape gather_shape(const SketchPlan& p, int ncols, sk_dtype dtype) 
   return g;
 }
 
-static sk_status launch_rows(const SketchPlan& p, const float* B, int64_t ldb, int ncols, double* partial,
+template <typename T>
+static sk_status launch_rows(const SketchPlan& p, const T* B, int64_t ldb, int ncols, double* partial,
                              const GatherShape& g, cudaStream_t st) {
   const size_t smem = 2 * rows_buf_bytes(p.s, p.zeta);
-  SK_CUDA(cudaFuncSetAttribute(gather_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kDynSmemLimit));
+  SK_CUDA(cudaFuncSetAttribute(gather_rows_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, kDynSmemLimit));
   const int threads = (p.s + 31) / 32 * 32;
   dim3 grid(g.ntiles, g.ngroups);
-  gather_rows_kernel<<<grid, threads, smem, st>>>(B, ldb, ncols, p.n, p.s, p.zeta, p.nchunks, g.cpg, p.rowptr,
-                                                  p.entries, partial);
+  gather_rows_kernel<T><<<grid, threads, smem, st>>>(B, ldb, ncols, p.n, p.s, p.zeta, p.nchunks, g.cpg, p.rowptr,
+                                                     p.entries, partial);
   SK_CUDA(cudaGetLastError());
   return SK_OK;
 }
@@ -510,7 +611,8 @@ sk_status plan_apply_ws(const SketchPlan& p, const void* B, int64_t ldb, int nco
                         double* partial, cudaStream_t st) {
   const GatherShape g = gather_shape(p, ncols, dtype);
   sk_status stt;
-  if (dtype == SK_F64) stt = gather_dispatch<double>(p, (const double*)B, ldb, ncols, partial, g.ngroups, g.cpg, g.W, st);
+  if (dtype == SK_F64 && g.rows) stt = launch_rows(p, (const double*)B, ldb, ncols, partial, g, st);
+  else if (dtype == SK_F64) stt = gather_dispatch<double>(p, (const double*)B, ldb, ncols, partial, g.ngroups, g.cpg, g.W, st);
   else if (dtype == SK_F32 && g.rows) stt = launch_rows(p, (const float*)B, ldb, ncols, partial, g, st);
   else if (dtype == SK_F32) stt = gather_dispatch<float>(p, (const float*)B, ldb, ncols, partial, g.ngroups, g.cpg, g.W, st);
   else stt = gather_dispatch<__nv_bfloat16>(p, (const __nv_bfloat16*)B, ldb, ncols, partial, g.ngroups, g.cpg, g.W, st);
