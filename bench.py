@@ -29,6 +29,11 @@ if ROOT not in sys.path:
 
 METRIC = "sGMRES solves/s to 1e-6 rel. residual (chosen vs plain form); sketch GB/s vs HBM"
 
+# DRAM bytes (read + write) of one Arnoldi step (its three launches), from
+# the ncu capture summarised in profiles/basis_dram_sgmres_scale_f32.md;
+# None for forms not captured (and to be reset whenever those kernels change).
+BASIS_TRAFFIC = {}
+
 
 def _peaks():
     try:
@@ -354,17 +359,22 @@ def run_ours(args):
     esz = {"f32": 4, "bf16": 2, "f64": 8}[args.form]
     d, k, s = W["d"], W["k"], W["s"]
     peak, peak_kind = _peaks()
-    # Roofline of the dominant kernel family, the truncated-Arnoldi passes:
-    # per Arnoldi step the form pass reads b_j and the k-1 older window
-    # vectors and writes b_{j+1}; each of the two dot passes reads the k
-    # window vectors: (3k+1) vectors of n elements per step.
+    # Roofline of the dominant kernel family, the truncated-Arnoldi passes
+    # (one unit = one Arnoldi step = form + dots1 + dots2).  Algorithmic bytes
+    # per unit: e*n*(3k+5) for a CGS2 step (the vector traffic of SpMV, two
+    # Gram-Schmidt passes and the normalisation).  These kernels recompute
+    # A b_j instead of storing it, so the bytes they must move are fewer:
+    # (3k+1)*e*n (each pass reads the k window vectors, form writes b_{j+1}).
     basis_ms = sum(i["ms"][1] for i in infos) / args.steps / cycles
-    basis_bytes = (3 * k + 1) * esz * n * d
-    achieved = basis_bytes / (basis_ms / 1000.0) / 1e9
-    roofline = {"kernel": "truncated-Arnoldi passes (form_kernel, dots_kernel x2 per step)", "bound": "hbm",
+    step_ms = basis_ms / d
+    unit_bytes = (3 * k + 5) * esz * n
+    achieved = unit_bytes / (step_ms / 1000.0) / 1e9
+    traffic = BASIS_TRAFFIC.get((args.form, args.persistent))
+    roofline = {"kernel": "truncated-Arnoldi step (form_kernel + dots_kernel pass 1 + pass 2)", "bound": "hbm",
                 "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
-                "traffic": None, "peak_source": peak_kind,
-                "algorithmic_bytes_per_cycle": basis_bytes}
+                "traffic": traffic, "peak_source": peak_kind,
+                "unit_bytes": unit_bytes, "moved_bytes_min": (3 * k + 1) * esz * n,
+                "step_us": round(step_ms * 1000.0, 2)}
     sketch_ms = sum(i["ms"][2] for i in infos) / args.steps / cycles
     sketch_bytes = esz * n * (d + 1) + 8 * n
     phases = [round(sum(i["ms"][q] for i in infos) / args.steps, 3) for q in range(6)]

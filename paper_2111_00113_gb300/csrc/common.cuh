@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <cuda/atomic>
 #include <cuda_bf16.h>
 #include <stdint.h>
 #include <string>
@@ -124,21 +125,23 @@ __device__ __forceinline__ void block_sum_k(V (&v)[K], V* sh) {
   __syncthreads();
 }
 
-// Last-block-done: every block calls this after writing its partials; the
-// function returns true in exactly one block (the last to arrive), after a
-// fence that makes all partials visible to it.  The counter is reset by the
-// last block so that the launch can be replayed (CUDA graphs).
+// Last-block-done: every block calls this after writing its partials;
+// the function returns true in exactly one block (the last to arrive).  One
+// acq_rel atomic by thread 0 replaces fences by every thread: the barrier
+// before it orders the block's partial writes before thread 0's release, and
+// in the last block the barrier after it orders every thread's reads of the
+// partials after thread 0's acquire.  The counter is reset by the last block
+// so that the launch can be replayed (CUDA graphs).
 __device__ __forceinline__ bool last_block_arrived(unsigned int* counter) {
   __shared__ bool s_last;
-  __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) {
-    unsigned prev = atomicAdd(counter, 1u);
+    cuda::atomic_ref<unsigned int, cuda::thread_scope_device> c(*counter);
+    const unsigned prev = c.fetch_add(1u, cuda::memory_order_acq_rel);
     s_last = (prev == gridDim.x * gridDim.y - 1);
-    if (s_last) *counter = 0;
+    if (s_last) c.store(0u, cuda::memory_order_relaxed);
   }
   __syncthreads();
-  if (s_last) __threadfence();
   return s_last;
 }
 
