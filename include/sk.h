@@ -144,7 +144,9 @@ typedef struct {
   double stab_tol;         /* kappa(T) threshold (§3.4, §5.3); <= 0 = 1e14 (F64), 2e6 (F32), 1e2 (BF16) */
   int maxit;               /* restart cycles, default 10000 */
   sk_dtype basis;          /* basis storage and SpMV precision, default SK_F64 */
-  int cgs_passes;          /* Gram-Schmidt passes, 1 or 2 (default 2: "double Gram-Schmidt") */
+  int cgs_passes;          /* Gram-Schmidt passes, 1 or 2 (default 2: "double Gram-Schmidt");
+                              1 needs an FP64 basis (SK_EINVAL otherwise: the one-pass norm
+                              update ||m||^2 - ||h||^2 is unstable in FP32/BF16) */
   double tau;              /* sRR convergence tolerance for nconv (default 1e-8) */
   int symmetric;           /* sRR: keep real parts of lambda and x (§6.8) */
   double breakdown;        /* ||w_j|| <= breakdown*||A b_{j-1}|| ends the basis; <=0 = 1e-13 (F64) / 1e-6 */

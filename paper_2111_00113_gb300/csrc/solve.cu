@@ -230,6 +230,17 @@ static void resolve_opts(const sk_opts* in, sk_opts* o, int d) {
   if (o->maxit <= 0) o->maxit = 10000;
 }
 
+// A single classical Gram-Schmidt pass takes nu_j from ||m||^2 - ||h||^2,
+// which needs the window orthonormal to the working precision: fine with an
+// FP64 basis, unstable with FP32/BF16 (columns blow up after ~20 steps).
+static sk_status check_passes(const sk_opts& o) {
+  if (o.cgs_passes == 1 && o.basis != SK_F64) {
+    set_error("invalid argument: cgs_passes = 1 needs an FP64 basis (use 2 passes with FP32/BF16)");
+    return SK_EINVAL;
+  }
+  return SK_OK;
+}
+
 static constexpr long long kBarrierSpinLimit = 1ll << 22;
 
 // Device workspace of one basis build.
@@ -270,7 +281,7 @@ struct BasisBuffers {
       pw.spin_limit = kBarrierSpinLimit;
     }
     double* dd = nullptr;
-    const size_t nd = (size_t)2 * d * k + 2 * (size_t)d + (size_t)(d + 1) * d + (size_t)bp.nblk * (kMaxK + 1) + 2 +
+    const size_t nd = (size_t)2 * d * k + 2 * (size_t)d + (size_t)(d + 1) * d + (size_t)bp.nblk_cap * (kMaxK + 1) + 2 +
                       (size_t)d * (kMaxK + 1);
     SK_TRY(sc.alloc(&dd, nd));
     bp.h1 = dd;
@@ -279,7 +290,7 @@ struct BasisBuffers {
     bp.mn2 = bp.nu + d;
     bp.Hbar = bp.mn2 + d;
     bp.partial = bp.Hbar + (size_t)(d + 1) * d;
-    double* rho2 = bp.partial + (size_t)bp.nblk * (kMaxK + 1);
+    double* rho2 = bp.partial + (size_t)bp.nblk_cap * (kMaxK + 1);
     bp.rho2 = rho2;
     bp.coef = rho2 + 2;
     unsigned* cnt = nullptr;
@@ -322,6 +333,7 @@ extern "C" sk_status trunc_arnoldi_basis(const sk_op* A, const double* r0, int d
   resolve_opts(opts, &o, d);
   o.basis = basis_dtype;
   if (!opts || opts->breakdown <= 0) o.breakdown = basis_dtype == SK_F64 ? 1e-13 : 1e-6;
+  SK_TRY(check_passes(o));
   Scratch sc(st);
   BasisBuffers bb;
   SK_TRY(bb.alloc(A->n, d, k, basis_dtype, o.cgs_passes, o.breakdown, sc, B, A, o.persistent != 0));
@@ -451,6 +463,7 @@ static sk_status sgmres_impl(const sk_op* A, const double* b, double* x, int d, 
   std::memset(&S, 0, sizeof(S));
   resolve_opts(opts, &S.o, d);
   SK_CHECK_ARG(S.o.basis == SK_F64 || S.o.basis == SK_F32 || S.o.basis == SK_BF16, "basis dtype");
+  SK_TRY(check_passes(S.o));
   S.n = A->n;
   S.d = d;
   S.k = k;
@@ -887,6 +900,7 @@ extern "C" sk_status srr_eigs(const sk_op* A, const double* w1, int nev, int d, 
   sk_opts o;
   resolve_opts(opts, &o, d);
   SK_CHECK_ARG(o.basis == SK_F64 || o.basis == SK_F32 || o.basis == SK_BF16, "basis dtype");
+  SK_TRY(check_passes(o));
   if (info) std::memset(info, 0, sizeof(*info));
   const int64_t n = A->n;
   Scratch sc(st);

@@ -161,3 +161,41 @@ def test_persistent_diffusion_and_shift(skg):
     out = skg.trunc_arnoldi_basis(op, torch.tensor(r, device="cuda"), d, k)
     B_ref, _, _, _ = krylov.trunc_arnoldi(As, r, d, k)
     assert np.linalg.norm(out["B"].cpu().numpy()[:, :8] - B_ref[:, :8]) <= 1e-10
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+@pytest.mark.parametrize("k", [2, 3, 4])
+def test_low_precision_stencil_rectangular(skg, dtype, k):
+    # FP32/BF16 bases on a rectangular stencil grid (vector path, nx % 4 == 0,
+    # ny = 37) with a diagonal shift: the leading columns follow the FP64
+    # oracle's recurrence and the Arnoldi relation holds to the storage
+    # precision.
+    import torch
+    passes = 2
+    nx, ny, d = 64, 37, 24
+    coef = synth.conv_diff_coef(64, 25.0)
+    shift = synth.uniform(5, nx * ny)
+    A = operators.stencil5_matrix(nx, ny, coef, shift)
+    r = synth.randn(6, nx * ny)
+    tdt = torch.float32 if dtype == "f32" else torch.bfloat16
+    op = skg.Op.stencil5(nx, ny, coef, torch.tensor(shift, device="cuda"))
+    out = skg.trunc_arnoldi_basis(op, torch.tensor(r, device="cuda"), d, k, dtype=tdt, cgs_passes=passes)
+    assert out["d_used"] == d
+    B = out["B"].to(torch.float64).cpu().numpy()
+    H = out["Hbar"].cpu().numpy()
+    B_ref, _, _, _ = krylov.trunc_arnoldi(A, r, d, k, passes=passes)
+    u = 6e-8 if dtype == "f32" else 4e-3
+    assert np.linalg.norm(B[:, :4] - B_ref[:, :4]) <= 1e3 * u
+    AB = A @ B[:, :d]
+    assert np.linalg.norm(AB - B @ H) <= 50 * u * np.linalg.norm(AB)
+    assert np.allclose(np.linalg.norm(B, axis=0), 1, atol=10 * u)
+
+
+def test_single_pass_needs_fp64_basis(skg):
+    import torch
+    N = 32
+    coef, _ = _cd(N, 10.0)
+    op = skg.Op.stencil5(N, N, coef)
+    r = torch.tensor(synth.randn(1, N * N), device="cuda")
+    with pytest.raises(skg.SkError, match="cgs_passes"):
+        skg.trunc_arnoldi_basis(op, r, 8, 2, dtype=torch.float32, cgs_passes=1)
