@@ -58,6 +58,44 @@ def trunc_arnoldi(A, r, d, k, passes=2, breakdown=1e-13):
 
 
 # ---------------------------------------------------------------------------
+# Shifted-and-scaled Chebyshev basis: §4.3, eq. (Chebrecurse).
+# ---------------------------------------------------------------------------
+def chebyshev_basis(A, r, d, c, dx, dy=0.0):
+    """Chebyshev basis of K_{d+1}(A; r) for a spectrum inside the rectangle
+    [c - dx, c + dx] x [-dy, dy] (rho = max(dx, dy)):
+
+        b_1 = r/||r||,   b_2 = (2 rho)^{-1} (A - c I) b_1,
+        b_j = rho^{-1} [ (A - c I) b_{j-1} - (dx^2 - dy^2)/(4 rho) b_{j-2} ],
+
+    every vector rescaled to unit norm after it has served in the recurrence.
+    Returns B (n x (d+1), unit columns), M = A B[:, :d] (formed directly), and
+    Hbar ((d+1) x d, tridiagonal) with A B[:, :d] = B Hbar, read off the
+    recurrence: A u_1 = c u_1 + 2 rho u_2 and
+    A u_j = c u_j + rho u_{j+1} + gamma u_{j-1} (gamma = (dx^2-dy^2)/(4 rho))
+    for the unscaled vectors u, then rescaled by the norms.
+    """
+    rho = max(dx, dy)
+    gamma = (dx * dx - dy * dy) / (4.0 * rho)
+    n = r.shape[0]
+    U = np.zeros((n, d + 1))
+    U[:, 0] = r / np.linalg.norm(r)
+    if d >= 1:
+        U[:, 1] = (A @ U[:, 0] - c * U[:, 0]) / (2.0 * rho)
+    for j in range(2, d + 1):
+        U[:, j] = ((A @ U[:, j - 1] - c * U[:, j - 1]) - gamma * U[:, j - 2]) / rho
+    sig = np.linalg.norm(U, axis=0)
+    B = U / sig
+    Hbar = np.zeros((d + 1, d))
+    for j in range(d):
+        Hbar[j, j] = c
+        Hbar[j + 1, j] = (2.0 * rho if j == 0 else rho) * sig[j + 1] / sig[j]
+        if j >= 1:
+            Hbar[j - 1, j] = gamma * sig[j - 1] / sig[j]
+    M = A @ B[:, :d]
+    return B, M, Hbar
+
+
+# ---------------------------------------------------------------------------
 # Dense Householder QR and the sketched least-squares solve: §3.3 eqs.
 # (sgmres-yhat), (sgmres-rhat); Algorithm 1 (QR, triangular substitution).
 # ---------------------------------------------------------------------------
@@ -154,18 +192,24 @@ def sketched_ls(C, g, stab_tol=np.inf):
 # sGMRES: Algorithm 1 with the solution built from B (§3.2 eq. (sgmres),
 # §3.3: x-hat = x_0 + B y-hat), restarted as in §3.5.
 # ---------------------------------------------------------------------------
-def sgmres_cycle(A, f, x, d, k, sketch, passes=2, stab_tol=1e14, breakdown=1e-13):
-    """One cycle of Algorithm 1 from the current iterate x."""
+def sgmres_cycle(A, f, x, d, k, sketch, passes=2, stab_tol=1e14, breakdown=1e-13, cheb=None):
+    """One cycle of Algorithm 1 from the current iterate x.  ``cheb`` =
+    (c, dx, dy) takes the Chebyshev basis (§4.3) instead of truncated
+    Arnoldi."""
     r = f - A @ x
     g = sketch(r)
-    B, M, _, d_used = trunc_arnoldi(A, r, d, k, passes=passes, breakdown=breakdown)
+    if cheb is not None:
+        B, M, _ = chebyshev_basis(A, r, d, *cheb)
+        B, d_used = B[:, :d], d
+    else:
+        B, M, _, d_used = trunc_arnoldi(A, r, d, k, passes=passes, breakdown=breakdown)
     C = sketch(M)
     y, rhat, kappa, width = sketched_ls(C, g, stab_tol)
     x_new = x + B @ y
     return x_new, dict(rhat=rhat, kappa=kappa, d_used=d_used, width=width, r0norm=np.linalg.norm(r))
 
 
-def sgmres(A, f, x0, d, k, sketch, tol, maxit=10000, passes=2, stab_tol=1e14, breakdown=1e-13):
+def sgmres(A, f, x0, d, k, sketch, tol, maxit=10000, passes=2, stab_tol=1e14, breakdown=1e-13, cheb=None):
     """Restarted sGMRES (§3.5) until ||f - A x||/||f|| <= tol or maxit cycles.
 
     Returns x, relres history (one entry per cycle, after the cycle), infos.
@@ -177,7 +221,7 @@ def sgmres(A, f, x0, d, k, sketch, tol, maxit=10000, passes=2, stab_tol=1e14, br
     rel = np.linalg.norm(f - A @ x) / fn
     cycles = 0
     while rel > tol and cycles < maxit:
-        x, info = sgmres_cycle(A, f, x, d, k, sketch, passes, stab_tol, breakdown)
+        x, info = sgmres_cycle(A, f, x, d, k, sketch, passes, stab_tol, breakdown, cheb)
         rel = np.linalg.norm(f - A @ x) / fn
         hist.append(rel)
         infos.append(info)

@@ -38,6 +38,21 @@ def stencil5_matrix(nx, ny, coef, shift=None):
     return sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(n, n))
 
 
+def neumann_laplacian_matrix(nx, ny):
+    """5-point Laplacian of an nx x ny grid with zero-flux (Neumann)
+    boundaries, h^2-scaled: the graph Laplacian of the grid, built as the
+    Kronecker sum of two path-graph Laplacians.  Positive semidefinite,
+    kernel = constant vectors, eigenvalues in [0, 8) (the E2 model problem,
+    §8: "Laplacian in 2-D" with spectrum in [0, 8]).
+    """
+    def path(m):
+        L = sp.diags([-np.ones(m - 1), 2.0 * np.ones(m), -np.ones(m - 1)], [-1, 0, 1], format="lil")
+        L[0, 0] = 1.0
+        L[m - 1, m - 1] = 1.0
+        return L.tocsr()
+    return (sp.kron(sp.identity(ny), path(nx)) + sp.kron(path(ny), sp.identity(nx))).tocsr()
+
+
 def diffusion_var_matrix(nx, ny, theta):
     """Variable-coefficient diffusion -div(theta grad u), h^2-scaled, as CSR.
 

@@ -17,6 +17,11 @@ spectra; the paper's SuiteSparse/Matrix Market matrices are not available):
              nev=10, d=200, k=4, s=400, zeta=11, FP32 basis / FP64 Ritz
   batched    256 systems, side ~ U{128..512}, Pe ~ U(1,100) (seed 4),
              4 right-hand sides ~ N(0,1) each, d=100, k=2, s=200, zeta=10
+  laplace    1024x1024 Neumann Laplacian (spectrum in [0, 8], kernel = the
+             constants), f = A x_true with x_true ~ N(0,1) seed 5 (so f is
+             consistent), d=300, k=2, s=600, zeta=12, tol 1e-6; Chebyshev
+             basis with c = 4, dx = 4, dy = 0 (the paper's §8 Laplacian
+             experiment: "eigenvalues in [0, 8]")
   adjoint    512x512 variable-coefficient diffusion, theta = exp(GRF,
              length scale 32 cells, seed 2), b ~ N(0,1) seed 3,
              x_target = A(theta = 1)^{-1} b, d=300, k=2, s=600, zeta=12,
@@ -67,6 +72,16 @@ def grf(seed, N, ell):
     return g.reshape(-1)
 
 
+def neumann_shift(nx, ny):
+    """Diagonal correction that turns the 5-point stencil (4, -1, -1, -1, -1)
+    with zero Dirichlet neighbours into the zero-flux (Neumann) Laplacian:
+    -1 for every missing neighbour of a boundary cell."""
+    ix = np.tile(np.arange(nx), ny)
+    iy = np.repeat(np.arange(ny), nx)
+    missing = (ix == 0).astype(float) + (ix == nx - 1) + (iy == 0) + (iy == ny - 1)
+    return -missing
+
+
 def batch_systems(seed, nsys, side_lo=128, side_hi=512, pe_lo=1.0, pe_hi=100.0):
     rng = np.random.default_rng(seed)
     sides = rng.integers(side_lo, side_hi + 1, size=nsys)
@@ -85,6 +100,7 @@ WORKLOADS = {
     "scale": dict(N=1024, Pe=50.0, b_seed=0, d=300, k=2, s=600, zeta=12, tol=1e-6),
     "eig": dict(N=512, Pe=10.0, shift_seed=1, nev=10, d=200, k=4, s=400, zeta=11),
     "batched": dict(nsys=256, seed=4, nrhs=4, d=100, k=2, s=200, zeta=10, tol=1e-6),
+    "laplace": dict(N=1024, x_seed=5, d=300, k=2, s=600, zeta=12, tol=1e-6, cheb=(4.0, 4.0, 0.0)),
     "adjoint": dict(N=512, grf_seed=2, ell=32.0, b_seed=3, target_seed=3, d=300, k=2, s=600, zeta=12, tol=1e-10,
                     tol_f32=1e-7),
 }

@@ -183,3 +183,71 @@ def test_restarted_sgmres_small_workload_converges():
     assert np.linalg.norm(f - A @ x) / np.linalg.norm(f) == pytest.approx(hist[-1])
     # each restart reduces the residual (the space always contains 0 update)
     assert all(b < a for a, b in zip(hist, hist[1:]))
+
+
+# ---- Chebyshev basis (§4.3, eq. (Chebrecurse)) --------------------------------
+@pytest.mark.parametrize("c,dx,dy", [(4.0, 4.0, 0.0), (1.0, 2.0, 0.0), (3.0, 2.5, 1.5)])
+def test_chebyshev_basis_is_chebyshev_polynomials_on_a_diagonal(c, dx, dy):
+    # For A = diag(lambda) the recurrence produces, up to positive scalars,
+    # T_j((A - c)/f) r with f = sqrt(dx^2 - dy^2) (the foci of the ellipse;
+    # f = dx for an interval): compare the unit columns with numpy's chebval.
+    from numpy.polynomial import chebyshev as npc
+    rng = np.random.default_rng(3)
+    n, d = 200, 25
+    lam = c + dx * rng.uniform(-1, 1, n)
+    A = np.diag(lam)
+    r = rng.standard_normal(n)
+    B, M, H = krylov.chebyshev_basis(A, r, d, c, dx, dy)
+    f = np.sqrt(dx * dx - dy * dy)
+    z = (lam - c) / f
+    for j in range(d + 1):
+        e = np.zeros(j + 1)
+        e[j] = 1.0
+        v = npc.chebval(z, e) * r
+        v /= np.linalg.norm(v)
+        assert np.allclose(B[:, j], v, atol=1e-10), j
+    assert np.allclose(M, A @ B[:, :d])
+
+
+def test_chebyshev_relation_and_tridiagonal_hbar():
+    # A B_d = B_{d+1} Hbar to rounding, Hbar tridiagonal with c on the
+    # diagonal, on a nonsymmetric convection-diffusion operator whose real
+    # spectrum (a = Pe h / 2 < 1) lies in [4 - 4 sqrt(1 - a^2), 4 + 4 sqrt(1 - a^2)]
+    N, Pe = 20, 12.0
+    A = _cd(N, Pe)
+    a = Pe / (N + 1) / 2
+    half = 4 * np.sqrt(1 - a * a)
+    r = synth.randn(4, N * N)
+    B, M, H = krylov.chebyshev_basis(A, r, 40, 4.0, half, 0.0)
+    assert np.allclose(np.linalg.norm(B, axis=0), 1)
+    assert np.linalg.norm(A @ B[:, :40] - B @ H) <= 1e-12 * np.linalg.norm(A @ B[:, :40])
+    assert np.allclose(np.diag(H), 4.0)
+    assert np.count_nonzero(np.triu(H, 2)) == 0 and np.count_nonzero(np.tril(H, -2)) == 0
+
+
+def test_sgmres_chebyshev_exact_when_d_equals_n():
+    # the Chebyshev basis spans K_n(A; r) = R^n: one cycle solves the system
+    N = 6
+    A = operators.neumann_laplacian_matrix(N, N) + sp_identity(N * N)
+    f = synth.randn(2, N * N)
+    sk = lambda M: sketch.sparse_sign_apply(1, 2 * N * N, hashing.default_zeta(N * N), M)
+    x, hist, infos = krylov.sgmres(A, f, np.zeros(N * N), N * N - 1, 2, sk, tol=1e-300, maxit=1,
+                                   cheb=(5.0, 4.0, 0.0))
+    assert hist[0] <= 1e-7
+    assert np.allclose(x, np.linalg.solve(A.toarray(), f), atol=1e-6)
+
+
+def test_sgmres_chebyshev_neumann_laplacian_converges():
+    # the E2 model problem, small: consistent singular system f = A x_true
+    N = 32
+    A = operators.neumann_laplacian_matrix(N, N)
+    f = A @ synth.randn(5, N * N)
+    sk = lambda M: sketch.sparse_sign_apply(3, 120, hashing.default_zeta(60), M)
+    x, hist, infos = krylov.sgmres(A, f, np.zeros(N * N), 60, 2, sk, tol=1e-8, maxit=60, cheb=(4.0, 4.0, 0.0))
+    assert hist[-1] <= 1e-8
+    assert all(i["width"] == 60 for i in infos)
+
+
+def sp_identity(n):
+    import scipy.sparse as sps
+    return sps.identity(n, format="csr")

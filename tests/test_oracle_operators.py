@@ -89,3 +89,23 @@ def test_grf_statistics():
     # smooth: neighbour correlation close to exp(-1/(2 ell^2))
     c = np.mean(G[:, :-1] * G[:, 1:])
     assert c > 0.9
+
+
+def test_neumann_laplacian_spectrum_and_kernel():
+    # eigenvalues of the Kronecker sum of path-graph Laplacians:
+    # (2 - 2 cos(pi i / nx)) + (2 - 2 cos(pi j / ny)), i < nx, j < ny
+    nx, ny = 7, 5
+    A = operators.neumann_laplacian_matrix(nx, ny).toarray()
+    assert np.allclose(A, A.T)
+    assert np.allclose(A @ np.ones(nx * ny), 0)
+    li = 2 - 2 * np.cos(np.pi * np.arange(nx) / nx)
+    lj = 2 - 2 * np.cos(np.pi * np.arange(ny) / ny)
+    exact = np.sort((li[:, None] + lj[None, :]).ravel())
+    assert np.allclose(np.sort(np.linalg.eigvalsh(A)), exact, atol=1e-12)
+    assert exact.max() < 8
+
+
+def test_neumann_shift_turns_the_stencil_into_the_neumann_laplacian():
+    nx, ny = 6, 4
+    S = operators.stencil5_matrix(nx, ny, (4.0, -1.0, -1.0, -1.0, -1.0), synth.neumann_shift(nx, ny))
+    assert np.allclose(S.toarray(), operators.neumann_laplacian_matrix(nx, ny).toarray())
