@@ -234,6 +234,33 @@ def _bench_srr(skg, dev):
     return res
 
 
+def _bench_laplace(skg, dev):
+    """The section 8 Laplacian example: Chebyshev basis vs truncated Arnoldi (FP32)."""
+    import torch
+    W = synth.WORKLOADS["laplace"]
+    N = W["N"]
+    op = skg.Op.stencil5(N, N, (4.0, -1.0, -1.0, -1.0, -1.0),
+                         torch.tensor(synth.neumann_shift(N, N), device=dev))
+    f = op.apply(torch.tensor(synth.grf(W["x_seed"], N, W["ell"]), device=dev))
+    out = {}
+    for name, kw in (("chebyshev_f32", dict(cheb=W["cheb"])), ("arnoldi_f32", {})):
+        args = dict(zeta=W["zeta"], basis=torch.float32, maxit=200, **kw)
+        skg.sgmres_solve(op, f, W["d"], W["k"], W["s"], W["tol"], **args)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        x, info = skg.sgmres_solve(op, f, W["d"], W["k"], W["s"], W["tol"], **args)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        out[name] = {"solves_per_s": round(1000.0 / ms, 3), "ms": round(ms, 2), "cycles": info["cycles"],
+                     "relres": info["relres"], "basis_us_per_step": round(1000.0 * info["ms"][1] /
+                                                                          (info["cycles"] * W["d"]), 2)}
+    out["workload"] = ("1024^2 Neumann Laplacian, f = A GRF(seed 5, 64 cells), d=300, s=600, zeta=12, tol=1e-6; "
+                       "Chebyshev c=4, dx=4")
+    return out
+
+
 def _bench_batched(skg, dev):
     """256 convection-diffusion systems (side U{128..512}, Pe U(1,100)), 4 RHS each."""
     import torch
@@ -403,6 +430,7 @@ def run_ours(args):
         out["sketch_apply"] = _bench_sketch(skg, dev, peak)
         out["srr"] = _bench_srr(skg, dev)
         out["batched"] = _bench_batched(skg, dev)
+        out["laplace"] = _bench_laplace(skg, dev)
     if rank == 0 and ws == 1 and not args.no_baseline:
         try:
             r = _oracle_cycle_seconds(None)

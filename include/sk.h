@@ -137,6 +137,11 @@ sk_status sketch_apply_noalloc(const sk_sketch* S, const void* B, int64_t ldb, i
 /* ------------------------------------------------------------------------
  * Solver options and diagnostics.
  * ------------------------------------------------------------------------ */
+typedef enum {
+  SK_BASIS_ARNOLDI = 0,   /* k-truncated Arnoldi with classical Gram-Schmidt (§1.2.2, §4.2) */
+  SK_BASIS_CHEBYSHEV = 1  /* shifted-and-scaled Chebyshev recurrence (§4.3, eq. (Chebrecurse)) */
+} sk_basis_kind;
+
 typedef struct {
   sk_sketch_kind sketch;   /* default SK_SPARSE_SIGN */
   int zeta;                /* 0 = ceil(2 ln(1+d)) (§2.3.2) */
@@ -154,6 +159,12 @@ typedef struct {
   int persistent;          /* grid operators: build the basis in one cooperative kernel
                               with bounded grid barriers (1), or 3 launches per step (0, default) */
   int batch_workers;       /* sgmres_solve_batched: concurrent jobs (threads x streams); 0 = 16 */
+  sk_basis_kind basis_kind; /* default SK_BASIS_ARNOLDI.  SK_BASIS_CHEBYSHEV: no inner products;
+                              needs the spectrum inside the rectangle [c - dx, c + dx] x [-dy, dy]
+                              (max(dx, dy) > 0); k, cgs_passes, breakdown and persistent are
+                              ignored; supported by trunc_arnoldi_basis, sgmres_solve and
+                              sgmres_solve_batched (srr_eigs: SK_EINVAL) */
+  double cheb_c, cheb_dx, cheb_dy;
 } sk_opts;
 
 void sk_opts_default(sk_opts* o);
@@ -176,6 +187,9 @@ typedef struct {
  * k-truncated Arnoldi basis (§1.2.2 eq. (partorth); Algorithm 1 loop with
  * double Gram-Schmidt).  b_1 = r0/||r0||; for j >= 2 w_j is A b_{j-1}
  * orthogonalised against b_{j-1..j-k} in `cgs_passes` classical passes.
+ * With opts->basis_kind = SK_BASIS_CHEBYSHEV the columns are instead the
+ * Chebyshev recurrence of §4.3 eq. (Chebrecurse), each rescaled to unit
+ * norm, and Hbar is tridiagonal.
  *   A: op; r0: device n doubles; d >= 1; 1 <= k <= d.
  *   B: device, n x (d+1) of `basis_dtype`, ld = n (column d+1 = b_{d+1},
  *      needed for the Arnoldi relation AB = B_{d+1} Hbar).

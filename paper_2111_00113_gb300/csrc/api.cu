@@ -173,6 +173,8 @@ void sk_opts_default(sk_opts* o) {
   o->use_graph = 1;
   o->persistent = 0;
   o->batch_workers = 0;
+  o->basis_kind = SK_BASIS_ARNOLDI;
+  o->cheb_c = o->cheb_dx = o->cheb_dy = 0;
 }
 
 static sk_op* new_op() {

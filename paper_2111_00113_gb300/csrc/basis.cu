@@ -368,6 +368,141 @@ static cudaError_t launch_pdl(K kernel, int grid, cudaStream_t st, bool pdl, Arg
   return cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 
+// ---- Chebyshev basis (§4.3, eq. (Chebrecurse)) -------------------------------
+// With rho = max(dx, dy) and gamma = (dx^2 - dy^2)/(4 rho), the paper's
+// recurrence u_2 = (A - c) u_1 / (2 rho), u_{j+1} = ((A - c) u_j - gamma
+// u_{j-1}) / rho shrinks like 2^-j; B stores v_j = 2^j u_j (0-based), the
+// same vectors scaled by exact powers of two (so FP32 storage neither
+// underflows nor differs from the paper's recurrence by more than rounding):
+//   v_1 = (A - c) v_0 / rho,   v_{j+1} = ((A - c) v_j - 2 gamma v_{j-1}) * 2 / rho.
+// Hence A v_0 = c v_0 + rho v_1 and A v_j = c v_j + (rho/2) v_{j+1} + 2 gamma
+// v_{j-1}.  No inner products: one launch per vector, which also leaves its
+// per-CTA partial sums of ||v_j||^2 for the unit rescaling (done once per
+// basis by cheb_finalize_kernel, and applied through Hbar and the update
+// coefficients instead of rewriting B).
+template <typename T, int G>
+__global__ void __launch_bounds__(kBasisThreads)
+cheb_kernel(BasisParams p, OpView<typename Compute<T>::type> A, int c) {
+  using C = typename Compute<T>::type;
+  __shared__ C red[2 * (kBasisThreads / 32)];
+  const int64_t n = p.n;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x * G;
+  const int64_t i_begin = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * G;
+  const T* v1 = bcol<T>(p.B, p.ldb, c - 1);
+  const T* v2 = bcol<T>(p.B, p.ldb, c >= 2 ? c - 2 : 0);
+  T* out = bcol<T>(p.B, p.ldb, c);
+  // prologue: v_{c-2} is older than the predecessor, which writes v_{c-1}
+  C x2[kIter][G];
+#pragma unroll
+  for (int it = 0; it < kIter; ++it) {
+    const int64_t i = i_begin + it * stride;
+#pragma unroll
+    for (int e = 0; e < G; ++e) x2[it][e] = 0;
+    if (i < n && c >= 2) gload<G>(v2, i, x2[it]);
+  }
+  pdl_wait();
+  pdl_trigger();
+  if (c >= *p.stop) return;
+  const C cc = (C)p.cheb_c;
+  const C al = (C)(c == 1 ? 1.0 / p.cheb_rho : 2.0 / p.cheb_rho);
+  const C be = (C)(c == 1 ? 0.0 : 2.0 * p.cheb_gamma);
+  C acc[2] = {0, 0};  // ||v_c||^2 and, for c = 1, ||v_0||^2
+#pragma unroll
+  for (int it = 0; it < kIter; ++it) {
+    const int64_t i = i_begin + it * stride;
+    if (i < n) {
+      C m[G], x1[G], v[G];
+      op_apply<G>(A, v1, i, m);
+      gload<G>(v1, i, x1);
+#pragma unroll
+      for (int e = 0; e < G; ++e) v[e] = ((m[e] - cc * x1[e]) - be * x2[it][e]) * al;
+      gstore<G>(out, i, v);
+#pragma unroll
+      for (int e = 0; e < G; ++e) {
+        const C vs = to_c(from_c<T>(v[e]));  // the value B holds
+        acc[0] += vs * vs;
+        acc[1] += x1[e] * x1[e];
+      }
+    }
+  }
+  block_sum_k<2>(acc, red);
+  if (threadIdx.x == 0) {
+    C* part = reinterpret_cast<C*>(p.cheb_part);
+    part[(int64_t)c * p.nblk_cap + blockIdx.x] = acc[0];
+    if (c == 1) part[blockIdx.x] = acc[1];
+  }
+}
+
+// One CTA per column j = 0..d: sigma_j = ||v_j|| from the partials (fixed
+// order), column j of Hbar = H_v[:, j] / sigma_j.  A zero or non-finite norm
+// ends the basis at j columns.
+template <typename C>
+__global__ void __launch_bounds__(kBasisThreads) cheb_finalize_kernel(BasisParams p, int nblk) {
+  __shared__ C red[kBasisThreads / 32];
+  const int j = blockIdx.x;
+  const C* part = reinterpret_cast<const C*>(p.cheb_part) + (int64_t)j * p.nblk_cap;
+  C t[1] = {0};
+  for (int b = threadIdx.x; b < nblk; b += blockDim.x) t[0] += part[b];
+  block_sum_k<1>(t, red);
+  if (threadIdx.x != 0) return;
+  const double sig = sqrt((double)t[0]);
+  p.sigma[j] = sig;
+  const bool ok = sig > 0 && isfinite(sig);
+  if (!isfinite(sig)) *p.nanflag = 1;
+  if (!ok) atomicMin(p.stop, j);
+  if (j < p.d && p.Hbar) {
+    double* col = p.Hbar + (int64_t)j * (p.d + 1);
+    const double inv = ok ? 1.0 / sig : 0.0;
+    col[j] = p.cheb_c * inv;
+    col[j + 1] = (j == 0 ? p.cheb_rho : 0.5 * p.cheb_rho) * inv;
+    if (j >= 1) col[j - 1] = 2.0 * p.cheb_gamma * inv;
+  }
+}
+
+template <typename T, int G>
+static sk_status enqueue_cheb_t(const BasisParams& p, const OpView<typename Compute<T>::type>& A, cudaStream_t st) {
+  using C = typename Compute<T>::type;
+  const int g = p.nblk;
+  SK_CUDA(launch_pdl(form_kernel<T, 2, G, false>, g, st, false, p, A, 0));  // v_0 = r/||r||
+  for (int c = 1; c <= p.d; ++c) SK_CUDA(launch_pdl(cheb_kernel<T, G>, g, st, true, p, A, c));
+  cheb_finalize_kernel<C><<<p.d + 1, kBasisThreads, 0, st>>>(p, g);
+  SK_CUDA(cudaGetLastError());
+  return SK_OK;
+}
+
+// Unit columns for callers of the basis itself: B[:, j] /= sigma_j and
+// Hbar[i, j] *= sigma_i (Hbar then relates the unit columns).
+template <typename T>
+__global__ void cheb_scale_cols_kernel(BasisParams p) {
+  using C = typename Compute<T>::type;
+  T* B = static_cast<T*>(p.B);
+  const int64_t total = p.n * (int64_t)(p.d + 1);
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const int j = (int)(q / p.n);
+    const int64_t i = q - (int64_t)j * p.n;
+    if (j >= *p.stop) continue;
+    T* e = B + (int64_t)j * p.ldb + i;
+    *e = from_c<T>((C)((double)to_c(*e) / p.sigma[j]));
+  }
+}
+__global__ void cheb_scale_hbar_kernel(BasisParams p) {
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < (p.d + 1) * p.d; q += gridDim.x * blockDim.x) {
+    const int i = q % (p.d + 1);
+    if (i < *p.stop) p.Hbar[q] *= p.sigma[i];
+  }
+}
+
+sk_status enqueue_cheb_normalize(const BasisParams& p, cudaStream_t st) {
+  const int blocks = 4 * num_sms();
+  if (p.dtype == SK_F64) cheb_scale_cols_kernel<double><<<blocks, 256, 0, st>>>(p);
+  else if (p.dtype == SK_F32) cheb_scale_cols_kernel<float><<<blocks, 256, 0, st>>>(p);
+  else cheb_scale_cols_kernel<__nv_bfloat16><<<blocks, 256, 0, st>>>(p);
+  if (p.Hbar) cheb_scale_hbar_kernel<<<(p.d + 256) / 256, 256, 0, st>>>(p);
+  SK_CUDA(cudaGetLastError());
+  return SK_OK;
+}
+
 template <typename T, int KM, int G, bool SM>
 static sk_status enqueue_basis_t(const BasisParams& p, const OpView<typename Compute<T>::type>& A, cudaStream_t st) {
   const int g = p.nblk;
@@ -410,6 +545,18 @@ sk_status enqueue_basis(const BasisParams& p, const sk_op* op, cudaStream_t st) 
   q.nblk = basis_grid(p.n, vec ? 4 : 1);
   if (q.nblk > p.nblk_cap) { set_error("basis: partial buffer too small"); return SK_EINVAL; }
   const BasisParams& pp = q;
+  if (p.kind == SK_BASIS_CHEBYSHEV) {
+    if (!p.sigma || !p.cheb_part || !(p.cheb_rho > 0)) { set_error("Chebyshev basis: workspace or rho missing"); return SK_EINVAL; }
+    if (p.dtype == SK_F64) {
+      OpView<double> A;
+      make_view(op, &A);
+      return vec ? enqueue_cheb_t<double, 4>(pp, A, st) : enqueue_cheb_t<double, 1>(pp, A, st);
+    }
+    OpView<float> A;
+    SK_TRY(make_view(op, &A, st));
+    if (p.dtype == SK_F32) return vec ? enqueue_cheb_t<float, 4>(pp, A, st) : enqueue_cheb_t<float, 1>(pp, A, st);
+    return vec ? enqueue_cheb_t<__nv_bfloat16, 4>(pp, A, st) : enqueue_cheb_t<__nv_bfloat16, 1>(pp, A, st);
+  }
   if (p.dtype == SK_F64) {
     OpView<double> A;
     make_view(op, &A);

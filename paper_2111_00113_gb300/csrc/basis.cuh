@@ -31,6 +31,13 @@ struct BasisParams {
   double bd;          // breakdown threshold
   int nblk;           // CTAs per pass (set by enqueue_basis)
   int nblk_cap;       // partial-sum rows allocated
+  // Chebyshev basis (kind == SK_BASIS_CHEBYSHEV): B holds the recurrence's
+  // vectors v_j (scaled by powers of two, not normalised); sigma[j] =
+  // ||v_j||, and Hbar = H_v diag(1/sigma) so that S B Hbar = S A B diag(1/sigma)
+  int kind;
+  double cheb_c, cheb_rho, cheb_gamma;
+  double* sigma;      // d+1
+  double* cheb_part;  // (d+1) x nblk_cap per-CTA partial sums of ||v_j||^2 (compute type)
 };
 
 // Workspace of the persistent (cooperative) basis kernel.
@@ -47,5 +54,8 @@ sk_status enqueue_basis_persistent(const BasisParams& bp, const sk_op* op, Persi
 int basis_grid(int64_t n, int G);
 bool basis_vector_path(const sk_op* op, int64_t ldb, const void* B);
 sk_status enqueue_basis(const BasisParams& p, const sk_op* op, cudaStream_t st);
+// Chebyshev: rescale B's columns to unit norm and Hbar to the unit basis
+// (diag(sigma) Hbar), for callers that want the normalised basis itself.
+sk_status enqueue_cheb_normalize(const BasisParams& p, cudaStream_t st);
 
 }  // namespace sk

@@ -234,6 +234,18 @@ static void resolve_opts(const sk_opts* in, sk_opts* o, int d) {
 // which needs the window orthonormal to the working precision: fine with an
 // FP64 basis, unstable with FP32/BF16 (columns blow up after ~20 steps).
 static sk_status check_passes(const sk_opts& o) {
+  if (o.basis_kind == SK_BASIS_CHEBYSHEV) {
+    const double rho = o.cheb_dx > o.cheb_dy ? o.cheb_dx : o.cheb_dy;
+    if (!(rho > 0) || !std::isfinite(rho) || !std::isfinite(o.cheb_c) || o.cheb_dx < 0 || o.cheb_dy < 0) {
+      set_error("invalid argument: the Chebyshev basis needs cheb_dx, cheb_dy >= 0 with max(cheb_dx, cheb_dy) > 0");
+      return SK_EINVAL;
+    }
+    return SK_OK;
+  }
+  if (o.basis_kind != SK_BASIS_ARNOLDI) {
+    set_error("invalid argument: unknown basis_kind %d", (int)o.basis_kind);
+    return SK_EINVAL;
+  }
   if (o.cgs_passes == 1 && o.basis != SK_F64) {
     set_error("invalid argument: cgs_passes = 1 needs an FP64 basis (use 2 passes with FP32/BF16)");
     return SK_EINVAL;
@@ -304,7 +316,30 @@ struct BasisBuffers {
     return SK_OK;
   }
   double* rho2_mut() const { return const_cast<double*>(bp.rho2); }
+  // Chebyshev basis: recurrence parameters and its workspace (call after alloc)
+  sk_status set_kind(const sk_opts& o, Scratch& sc) {
+    bp.kind = o.basis_kind;
+    if (o.basis_kind != SK_BASIS_CHEBYSHEV) return SK_OK;
+    persistent = false;
+    bp.cheb_c = o.cheb_c;
+    bp.cheb_rho = o.cheb_dx > o.cheb_dy ? o.cheb_dx : o.cheb_dy;
+    bp.cheb_gamma = (o.cheb_dx * o.cheb_dx - o.cheb_dy * o.cheb_dy) / (4.0 * bp.cheb_rho);
+    SK_TRY(sc.alloc(&bp.sigma, (size_t)bp.d + 1));
+    SK_TRY(sc.alloc(&bp.cheb_part, (size_t)(bp.d + 1) * bp.nblk_cap));
+    return SK_OK;
+  }
+  bool cheb() const { return bp.kind == SK_BASIS_CHEBYSHEV; }
+  int hbar_k() const { return cheb() && bp.k < 2 ? 2 : bp.k; }  // Chebyshev Hbar is tridiagonal
 };
+
+// y[j] /= sigma[j]: the sketched problem is posed in the unit columns
+// b_j = v_j / sigma_j, the update uses the stored v_j.
+__global__ void scale_y_kernel(double* __restrict__ y, const double* __restrict__ sigma, int d) {
+  for (int j = threadIdx.x; j < d; j += blockDim.x) {
+    const double sg = sigma[j];
+    y[j] = (sg > 0) ? y[j] / sg : 0.0;
+  }
+}
 
 // Enqueue one basis build: stop = d+1, Hbar = 0, then the kernels.
 static sk_status enqueue_basis_build(BasisBuffers& bb, const sk_op* A, cudaStream_t st) {
@@ -337,6 +372,7 @@ extern "C" sk_status trunc_arnoldi_basis(const sk_op* A, const double* r0, int d
   Scratch sc(st);
   BasisBuffers bb;
   SK_TRY(bb.alloc(A->n, d, k, basis_dtype, o.cgs_passes, o.breakdown, sc, B, A, o.persistent != 0));
+  SK_TRY(bb.set_kind(o, sc));
   bb.bp.r = r0;
   {
     double* part = nullptr;
@@ -349,6 +385,7 @@ extern "C" sk_status trunc_arnoldi_basis(const sk_op* A, const double* r0, int d
     SK_CUDA(cudaGetLastError());
   }
   SK_TRY(enqueue_basis_build(bb, A, st));
+  if (bb.cheb()) SK_TRY(enqueue_cheb_normalize(bb.bp, st));
   if (S) {
     Sketcher sk;
     SK_TRY(sk.create(*S, sc, st));
@@ -358,7 +395,7 @@ extern "C" sk_status trunc_arnoldi_basis(const sk_op* A, const double* r0, int d
     SK_TRY(sc.alloc(&ws, sk.ws(d + 1, basis_dtype)));
     SK_TRY(sk.apply(B, A->n, d + 1, basis_dtype, SBfull, ws, st));
     if (SB) SK_TRY(enqueue_copy_sb(SBfull, S->s, d, bb.bp.stop, SB, st));
-    if (SAB) SK_TRY(enqueue_hbar_product(SBfull, bb.bp.Hbar, S->s, d, k, bb.bp.stop, SAB, st));
+    if (SAB) SK_TRY(enqueue_hbar_product(SBfull, bb.bp.Hbar, S->s, d, bb.hbar_k(), bb.bp.stop, SAB, st));
   }
   if (Hbar) SK_CUDA(cudaMemcpyAsync(Hbar, bb.bp.Hbar, sizeof(double) * (size_t)(d + 1) * d, cudaMemcpyDeviceToDevice, st));
   int h[3] = {0, 0, 0};
@@ -423,10 +460,14 @@ static sk_status enqueue_cycle(SolveState& S, const sk_op* A, const OpView<doubl
   SK_TRY(mark(ev, EV_BASIS, st, capturing));
   SK_TRY(S.sketch.apply(S.bb.bp.B, S.bb.bp.ldb, S.d + 1, S.o.basis, S.SB, S.ws_B, st));
   SK_TRY(mark(ev, EV_SB, st, capturing));
-  SK_TRY(enqueue_hbar_product(S.SB, S.bb.bp.Hbar, S.s, S.d, S.k, S.bb.bp.stop, S.Aug, st));
+  SK_TRY(enqueue_hbar_product(S.SB, S.bb.bp.Hbar, S.s, S.d, S.bb.hbar_k(), S.bb.bp.stop, S.Aug, st));
   SK_CUDA(cudaMemcpyAsync(S.Aug + (size_t)S.d * S.s, S.g, sizeof(double) * S.s, cudaMemcpyDeviceToDevice, st));
   SK_TRY(enqueue_qr(S.Aug, S.s, S.d, S.d + 1, S.rdiag, S.tau, S.Tws, st));
   SK_TRY(enqueue_ls_solve(S.Aug, S.rdiag, S.s, S.d, S.o.stab_tol, S.y, S.out + 1, st));
+  if (S.bb.cheb()) {
+    scale_y_kernel<<<1, 256, 0, st>>>(S.y, S.bb.bp.sigma, S.d);
+    SK_CUDA(cudaGetLastError());
+  }
   SK_TRY(mark(ev, EV_SMALL, st, capturing));
   SK_TRY(enqueue_update(x, S.bb.bp.B, S.bb.bp.ldb, S.n, S.d, S.o.basis, S.y, S.out + 1, st));
   SK_TRY(mark(ev, EV_UPDATE, st, capturing));
@@ -471,6 +512,7 @@ static sk_status sgmres_impl(const sk_op* A, const double* b, double* x, int d, 
   if (info) std::memset(info, 0, sizeof(*info));
   Scratch sc(st);
   SK_TRY(S.bb.alloc(S.n, d, k, S.o.basis, S.o.cgs_passes, S.o.breakdown, sc, nullptr, A, S.o.persistent != 0));
+  SK_TRY(S.bb.set_kind(S.o, sc));
   sk_sketch sks;
   sks.kind = S.o.sketch;
   sks.n = S.n;
@@ -565,7 +607,8 @@ static sk_status sgmres_impl(const sk_op* A, const double* b, double* x, int d, 
     if (ce != cudaSuccess) { if (own) cudaStreamDestroy(own); return cuda_fail(ce, "cudaGraphInstantiate"); }
     kernels_per_cycle = count_kernel_nodes(graph);
   } else {
-    kernels_per_cycle = 5 + 3 + (long long)d * (S.o.cgs_passes + 1) + 2 + 1 + 2 * ((d + kQrNb - 1) / kQrNb) + 1 + 1 + 1;
+    const long long basis_kernels = S.bb.cheb() ? (long long)d + 2 : (long long)d * (S.o.cgs_passes + 1);
+    kernels_per_cycle = 5 + 3 + basis_kernels + 2 + 1 + 2 * ((d + kQrNb - 1) / kQrNb) + 1 + 1 + 1 + (S.bb.cheb() ? 1 : 0);
   }
   struct StreamFree { cudaStream_t s; ~StreamFree() { if (s) cudaStreamDestroy(s); } } sf{own};
 
@@ -901,6 +944,7 @@ extern "C" sk_status srr_eigs(const sk_op* A, const double* w1, int nev, int d, 
   resolve_opts(opts, &o, d);
   SK_CHECK_ARG(o.basis == SK_F64 || o.basis == SK_F32 || o.basis == SK_BF16, "basis dtype");
   SK_TRY(check_passes(o));
+  SK_CHECK_ARG(o.basis_kind == SK_BASIS_ARNOLDI, "srr_eigs uses the truncated-Arnoldi basis");
   if (info) std::memset(info, 0, sizeof(*info));
   const int64_t n = A->n;
   Scratch sc(st);

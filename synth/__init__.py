@@ -18,8 +18,9 @@ spectra; the paper's SuiteSparse/Matrix Market matrices are not available):
   batched    256 systems, side ~ U{128..512}, Pe ~ U(1,100) (seed 4),
              4 right-hand sides ~ N(0,1) each, d=100, k=2, s=200, zeta=10
   laplace    1024x1024 Neumann Laplacian (spectrum in [0, 8], kernel = the
-             constants), f = A x_true with x_true ~ N(0,1) seed 5 (so f is
-             consistent), d=300, k=2, s=600, zeta=12, tol 1e-6; Chebyshev
+             constants), f = A x_true with x_true = GRF(seed 5, length 64
+             cells) (f is consistent and smooth, so the small eigenvalues
+             matter), d=300, k=2, s=600, zeta=12, tol 1e-6; Chebyshev
              basis with c = 4, dx = 4, dy = 0 (the paper's §8 Laplacian
              experiment: "eigenvalues in [0, 8]")
   adjoint    512x512 variable-coefficient diffusion, theta = exp(GRF,
@@ -100,7 +101,7 @@ WORKLOADS = {
     "scale": dict(N=1024, Pe=50.0, b_seed=0, d=300, k=2, s=600, zeta=12, tol=1e-6),
     "eig": dict(N=512, Pe=10.0, shift_seed=1, nev=10, d=200, k=4, s=400, zeta=11),
     "batched": dict(nsys=256, seed=4, nrhs=4, d=100, k=2, s=200, zeta=10, tol=1e-6),
-    "laplace": dict(N=1024, x_seed=5, d=300, k=2, s=600, zeta=12, tol=1e-6, cheb=(4.0, 4.0, 0.0)),
+    "laplace": dict(N=1024, x_seed=5, ell=64.0, d=300, k=2, s=600, zeta=12, tol=1e-6, cheb=(4.0, 4.0, 0.0)),
     "adjoint": dict(N=512, grf_seed=2, ell=32.0, b_seed=3, target_seed=3, d=300, k=2, s=600, zeta=12, tol=1e-10,
                     tol_f32=1e-7),
 }

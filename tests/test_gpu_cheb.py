@@ -1,0 +1,134 @@
+"""GPU Chebyshev basis (§4.3, eq. (Chebrecurse)) and sGMRES with it, against
+the CPU oracle."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import hashing, krylov, operators, sketch
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def skg():
+    import torch
+    assert torch.cuda.is_available(), "GPU test needs CUDA"
+    import paper_2111_00113_gb300 as m
+    return m
+
+
+def _cd(nx, ny, Pe):
+    coef = synth.conv_diff_coef(max(nx, ny), Pe)
+    return coef, operators.stencil5_matrix(nx, ny, coef)
+
+
+def _interval(N, Pe):
+    # the convection-diffusion spectrum is real for a = Pe h / 2 < 1:
+    # inside [4 - 4 sqrt(1 - a^2), 4 + 4 sqrt(1 - a^2)]
+    a = Pe / (N + 1) / 2
+    return 4.0, 4.0 * np.sqrt(1 - a * a), 0.0
+
+
+def _neumann(nx, ny, skg):
+    import torch
+    coef = (4.0, -1.0, -1.0, -1.0, -1.0)
+    op = skg.Op.stencil5(nx, ny, coef, torch.tensor(synth.neumann_shift(nx, ny), device="cuda"))
+    return op, operators.neumann_laplacian_matrix(nx, ny)
+
+
+@pytest.mark.parametrize("nx,ny,ell", [(32, 32, False), (30, 21, False), (32, 32, True)])
+def test_basis_fp64_matches_oracle(skg, nx, ny, ell):
+    # vector path (nx % 4 == 0) and scalar path; interval and ellipse
+    import torch
+    d = 40
+    coef, A = _cd(nx, ny, 15.0)
+    cheb = _interval(max(nx, ny), 15.0)
+    if ell:
+        cheb = (4.0, 4.0, 1.5)
+    r = synth.randn(8, nx * ny)
+    out = skg.trunc_arnoldi_basis(skg.Op.stencil5(nx, ny, coef), torch.tensor(r, device="cuda"), d, 2, cheb=cheb)
+    B_ref, _, H_ref = krylov.chebyshev_basis(A, r, d, *cheb)
+    assert out["d_used"] == d
+    B = out["B"].cpu().numpy()
+    H = out["Hbar"].cpu().numpy()
+    assert np.allclose(np.linalg.norm(B, axis=0), 1, atol=1e-13)
+    assert np.linalg.norm(B - B_ref) <= 1e-11 * np.sqrt(d)
+    assert np.allclose(H, H_ref, rtol=1e-11, atol=1e-12)
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+def test_basis_low_precision_relation(skg, dtype):
+    import torch
+    nx, ny, d = 64, 48, 60
+    op, A = _neumann(nx, ny, skg)
+    r = synth.randn(9, nx * ny)
+    tdt = torch.float32 if dtype == "f32" else torch.bfloat16
+    out = skg.trunc_arnoldi_basis(op, torch.tensor(r, device="cuda"), d, 2, dtype=tdt, cheb=(4.0, 4.0, 0.0))
+    B = out["B"].to(torch.float64).cpu().numpy()
+    H = out["Hbar"].cpu().numpy()
+    u = 6e-8 if dtype == "f32" else 4e-3
+    AB = A @ B[:, :d]
+    assert np.linalg.norm(AB - B @ H) <= 50 * u * np.linalg.norm(AB)
+    assert np.allclose(np.linalg.norm(B, axis=0), 1, atol=20 * u)
+    B_ref, _, _ = krylov.chebyshev_basis(A, r, d, 4.0, 4.0, 0.0)
+    assert np.linalg.norm(B[:, :6] - B_ref[:, :6]) <= 1e3 * u
+
+
+def test_sgmres_matches_oracle_neumann(skg):
+    # the E2 model problem, small: consistent singular system f = A x_true,
+    # FP64, residual after every cycle within 1.5x of the oracle's
+    import torch
+    N, d, s = 32, 60, 120
+    op, A = _neumann(N, N, skg)
+    f = A @ synth.randn(5, N * N)
+    zeta = hashing.default_zeta(d)
+    cheb = (4.0, 4.0, 0.0)
+    sk = lambda M: sketch.sparse_sign_apply(7, s, zeta, M)
+    _, hist, _ = krylov.sgmres(A, f, np.zeros(N * N), d, 2, sk, 1e-10, maxit=40, cheb=cheb)
+    b = torch.tensor(f, device="cuda")
+    x = torch.zeros_like(b)
+    for c, h in enumerate(hist[:8]):
+        x, info = skg.sgmres_solve(op, b, d, 2, s, 1e-300, x0=x, maxit=1, zeta=zeta, seed=7, cheb=cheb)
+        rel = np.linalg.norm(f - A @ x.cpu().numpy()) / np.linalg.norm(f)
+        assert rel <= 1.5 * h and h <= 1.5 * rel, (c, rel, h)
+    x, info = skg.sgmres_solve(op, b, d, 2, s, 1e-10, zeta=zeta, seed=7, cheb=cheb)
+    assert info["status"] == 0
+    assert abs(info["cycles"] - len(hist)) <= 1
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+def test_sgmres_low_precision_converges(skg, dtype):
+    import torch
+    N, d, s = 128, 100, 200
+    op, A = _neumann(N, N, skg)
+    f = A @ synth.randn(5, N * N)
+    tdt = torch.float32 if dtype == "f32" else torch.bfloat16
+    tol = 1e-6 if dtype == "f32" else 1e-4
+    x, info = skg.sgmres_solve(op, torch.tensor(f, device="cuda"), d, 2, s, tol, basis=tdt, maxit=400,
+                               cheb=(4.0, 4.0, 0.0))
+    assert info["status"] == 0, info
+    assert np.linalg.norm(f - A @ x.cpu().numpy()) <= tol * np.linalg.norm(f)
+
+
+def test_batched_with_chebyshev(skg):
+    import torch
+    ops, bs = [], []
+    for i, N in enumerate((40, 36, 64)):
+        op, A = _neumann(N, N, skg)
+        ops.append(op)
+        bs.append([torch.tensor(A @ synth.randn(20 + i, N * N), device="cuda")])
+    xs, stat, info = skg.sgmres_solve_batched(ops, bs, 40, 2, 80, 1e-8, cheb=(4.0, 4.0, 0.0), maxit=500)
+    assert all(st == 0 for st in stat)
+    for i, N in enumerate((40, 36, 64)):
+        x, _ = skg.sgmres_solve(ops[i], bs[i][0], 40, 2, 80, 1e-8, cheb=(4.0, 4.0, 0.0), maxit=500)
+        assert torch.equal(x, xs[i][0])
+
+
+def test_chebyshev_argument_errors(skg):
+    import torch
+    op, _ = _neumann(16, 16, skg)
+    r = torch.tensor(synth.randn(1, 256), device="cuda")
+    with pytest.raises(skg.SkError, match="Chebyshev"):
+        skg.trunc_arnoldi_basis(op, r, 8, 2, cheb=(4.0, 0.0, 0.0))
+    with pytest.raises(skg.SkError, match="truncated-Arnoldi"):
+        skg.srr_eigs(op, r, 2, 8, 2, 16, cheb=(4.0, 4.0, 0.0))
