@@ -44,7 +44,7 @@ struct BasisParams {
 struct PersistWork {
   unsigned* bar;         // 2: barrier count and generation (reset before each launch)
   int* err;              // SK_ETIMEOUT if a grid barrier gave up
-  double* part;          // 2 x grid x (kMaxK+1) partial sums
+  double* part;          // 3 x grid x (kMaxK+1) partial sums
   long long spin_limit;  // barrier spin iterations before giving up
 };
 

@@ -121,15 +121,16 @@ __device__ __forceinline__ C next_vec(C m, const C (&h)[KM], const C (&bw)[KM], 
 struct PersistParams {
   BasisParams bp;
   PersistCtl ctl;
-  double* part1;  // grid x (kMaxK+1)
-  double* part2;
+  double* part1;  // 2 x grid x (kMaxK+1): pass-1 partials, alternating by step parity (the
+                  // reads of step j and the writes of step j+1 are separated by a grid sync)
+  double* part2;  // grid x (kMaxK+1): pass-2 partials (and ||r||^2 before step 0)
 };
 
 // Sum K per-CTA partials of every CTA (fixed order, same in all CTAs);
 // result broadcast to all threads.
-template <int K>
-__device__ __forceinline__ void all_partials(const double* part, int nblk, double (&tot)[K], double* sh, double* bc) {
-  double v[K];
+template <int K, typename V>
+__device__ __forceinline__ void all_partials(const V* part, int nblk, V (&tot)[K], V* sh, V* bc) {
+  V v[K];
 #pragma unroll
   for (int q = 0; q < K; ++q) v[q] = 0;
   for (int b = threadIdx.x; b < nblk; b += blockDim.x) {
@@ -157,6 +158,8 @@ arnoldi_persistent_kernel(PersistParams pp, GridOp<typename Compute<T>::type> A)
   __shared__ double shr[K1 * (kPThreads / 32)];
   __shared__ double bc[K1];
   __shared__ C s_red[K1 * (kPThreads / 32)];
+  __shared__ C s_bc[K1];
+  __shared__ C s_h[KM + 2];  // step coefficients h (KM), 1/nu, breakdown flag
   const int n = (int)p.n;
   const int nx = A.nx;
   const int chunk = (n + gridDim.x - 1) / gridDim.x;
@@ -187,12 +190,14 @@ arnoldi_persistent_kernel(PersistParams pp, GridOp<typename Compute<T>::type> A)
     block_sum_k<K1>(a, shr);
     if (threadIdx.x == 0) {
 #pragma unroll
-      for (int q = 0; q < K1; ++q) pp.part1[blockIdx.x * K1 + q] = a[q];
+      for (int q = 0; q < K1; ++q) pp.part2[blockIdx.x * K1 + q] = a[q];
     }
     if (!grid_sync(pp.ctl, gen)) return;
     double tot[K1];
-    all_partials<K1>(pp.part1, gridDim.x, tot, shr, bc);
-    const double inv = 1.0 / sqrt(tot[KM]);
+    all_partials<K1>(pp.part2, gridDim.x, tot, shr, bc);
+    if (threadIdx.x == 0) bc[0] = 1.0 / sqrt(tot[KM]);  // once per CTA: FP64 sqrt and divide are slow
+    __syncthreads();
+    const double inv = bc[0];
     T* b0 = (T*)p.B;
     for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) {
       const C v = to_c(from_c<T>((C)(p.r[i] * inv)));
@@ -230,20 +235,25 @@ arnoldi_persistent_kernel(PersistParams pp, GridOp<typename Compute<T>::type> A)
       }
     }
     block_sum_k<K1>(acc, s_red);
+    C* part1 = reinterpret_cast<C*>(pp.part1 + (j & 1) * (int64_t)gridDim.x * (kMaxK + 1));
+    C* part2 = reinterpret_cast<C*>(pp.part2);
     if (threadIdx.x == 0) {
 #pragma unroll
-      for (int q = 0; q < K1; ++q) pp.part1[blockIdx.x * K1 + q] = (double)acc[q];
+      for (int q = 0; q < K1; ++q) part1[blockIdx.x * K1 + q] = acc[q];
     }
     if (!grid_sync(pp.ctl, gen)) return;
-    double h1d[K1];
-    all_partials<K1>(pp.part1, gridDim.x, h1d, shr, bc);
-    double h2d[K1];
+    // sums in the compute type (the per-CTA partials carry its precision)
+    C h1c[K1];
+    all_partials<K1>(part1, gridDim.x, h1c, s_red, s_bc);
+    C h2c[K1];
+#pragma unroll
+    for (int q = 0; q < K1; ++q) h2c[q] = 0;
     C h[KM];
     if (p.passes == 2) {
       // ---- phase 2 --------------------------------------------------------------
       C h1[KM];
 #pragma unroll
-      for (int q = 0; q < KM; ++q) h1[q] = (q < kw) ? (C)h1d[q] : (C)0;
+      for (int q = 0; q < KM; ++q) h1[q] = (q < kw) ? h1c[q] : (C)0;
 #pragma unroll
       for (int q = 0; q < K1; ++q) acc[q] = 0;
 #pragma unroll
@@ -266,44 +276,57 @@ arnoldi_persistent_kernel(PersistParams pp, GridOp<typename Compute<T>::type> A)
       block_sum_k<K1>(acc, s_red);
       if (threadIdx.x == 0) {
 #pragma unroll
-        for (int q = 0; q < K1; ++q) pp.part2[blockIdx.x * K1 + q] = (double)acc[q];
+        for (int q = 0; q < K1; ++q) part2[blockIdx.x * K1 + q] = acc[q];
       }
       if (!grid_sync(pp.ctl, gen)) return;
-      all_partials<K1>(pp.part2, gridDim.x, h2d, shr, bc);
-    } else {
-      // one classical pass: ||w||^2 = ||m||^2 - ||h1||^2 (W_j orthonormal)
-      double hh = 0;
-      for (int q = 0; q < kw; ++q) hh += h1d[q] * h1d[q];
-#pragma unroll
-      for (int q = 0; q < KM; ++q) h2d[q] = 0;
-      h2d[KM] = h1d[KM] - hh;
+      all_partials<K1>(part2, gridDim.x, h2c, s_red, s_bc);
     }
-    // ---- finalise step j (identical arithmetic in every CTA) -------------------------
-    double h2sq = 0;
-    for (int q = 0; q < kw; ++q) h2sq += h2d[q] * h2d[q];
-    const double nu2 = h2d[KM] - h2sq;
-    const double mn2 = h1d[KM];
-    bool brk = !(nu2 > p.bd * p.bd * mn2) || !(mn2 > 0) || !isfinite(nu2);
-    const double nu = brk ? 0.0 : sqrt(nu2);
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-      for (int q = 0; q < kw; ++q) {
-        p.h1[j * p.k + q] = h1d[q];
-        p.h2[j * p.k + q] = h2d[q];
+    // ---- finalise step j: thread 0 of every CTA (identical arithmetic), broadcast ----
+    if (threadIdx.x == 0) {
+      double h1d[KM], h2d[KM];
+      double ww;
+      for (int q = 0; q < KM; ++q) {
+        h1d[q] = (q < kw) ? (double)h1c[q] : 0.0;
+        h2d[q] = (q < kw && p.passes == 2) ? (double)h2c[q] : 0.0;
       }
-      p.mn2[j] = mn2;
-      p.nu[j] = nu;
-      if (!isfinite(nu2) || !isfinite(mn2)) *p.nanflag = 1;
-      if (p.Hbar) {
-        double* col = p.Hbar + (int64_t)j * (p.d + 1);
-        for (int q = 0; q < kw; ++q) col[j - q] = h1d[q] + h2d[q];
-        col[j + 1] = nu;
+      const double mn2 = (double)h1c[KM];
+      if (p.passes == 2) {
+        ww = (double)h2c[KM];
+      } else {
+        // one classical pass: ||w||^2 = ||m||^2 - ||h1||^2 (W_j orthonormal)
+        ww = mn2;
+        for (int q = 0; q < kw; ++q) ww -= h1d[q] * h1d[q];
       }
-      if (brk) *p.stop = j + 1;
+      double h2sq = 0;
+      for (int q = 0; q < kw; ++q) h2sq += h2d[q] * h2d[q];
+      const double nu2 = ww - h2sq;
+      const bool brk = !(nu2 > p.bd * p.bd * mn2) || !(mn2 > 0) || !isfinite(nu2);
+      const C nuc = brk ? (C)0 : sqrt((C)nu2);
+      for (int q = 0; q < KM; ++q) s_h[q] = (q < kw) ? (C)(h1d[q] + h2d[q]) : (C)0;
+      s_h[KM] = brk ? (C)0 : (C)1 / nuc;
+      s_h[KM + 1] = brk ? (C)1 : (C)0;
+      if (blockIdx.x == 0) {
+        const double nu = (double)nuc;
+        for (int q = 0; q < kw; ++q) {
+          p.h1[j * p.k + q] = h1d[q];
+          p.h2[j * p.k + q] = h2d[q];
+        }
+        p.mn2[j] = mn2;
+        p.nu[j] = nu;
+        if (!isfinite(nu2) || !isfinite(mn2)) *p.nanflag = 1;
+        if (p.Hbar) {
+          double* col = p.Hbar + (int64_t)j * (p.d + 1);
+          for (int q = 0; q < kw; ++q) col[j - q] = h1d[q] + h2d[q];
+          col[j + 1] = nu;
+        }
+        if (brk) *p.stop = j + 1;
+      }
     }
-    if (brk) return;
+    __syncthreads();
+    if (s_h[KM + 1] != (C)0) return;
 #pragma unroll
-    for (int q = 0; q < KM; ++q) h[q] = (q < kw) ? (C)(h1d[q] + h2d[q]) : (C)0;
-    const C inv = (C)(1.0 / nu);
+    for (int q = 0; q < KM; ++q) h[q] = s_h[q];
+    const C inv = s_h[KM];
     // ---- phase 3: b_{j+1} on the owned range and on the halo rows ----------------------
     T* bnext = (T*)p.B + (int64_t)(j + 1) * p.ldb;
     const T* bj = (const T*)p.B + (int64_t)j * p.ldb;
@@ -432,7 +455,7 @@ sk_status enqueue_basis_persistent(const BasisParams& bp, const sk_op* op, Persi
   pp.ctl.err = w.err;
   pp.ctl.spin_limit = w.spin_limit;
   pp.part1 = w.part;
-  pp.part2 = w.part + (size_t)grid * (kMaxK + 1);
+  pp.part2 = w.part + (size_t)2 * grid * (kMaxK + 1);
   SK_CUDA(cudaMemsetAsync(w.bar, 0, 2 * sizeof(unsigned), st));
   if (bp.dtype == SK_F64) {
     OpView<double> v;

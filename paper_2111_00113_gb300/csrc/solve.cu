@@ -289,7 +289,7 @@ struct BasisBuffers {
       SK_TRY(sc.alloc(&pw.bar, 2));
       SK_TRY(sc.alloc(&pw.err, 1));
       SK_CUDA(cudaMemsetAsync(pw.err, 0, sizeof(int), sc.st));
-      SK_TRY(sc.alloc(&pw.part, (size_t)2 * pg * (kMaxK + 1)));
+      SK_TRY(sc.alloc(&pw.part, (size_t)3 * pg * (kMaxK + 1)));
       pw.spin_limit = kBarrierSpinLimit;
     }
     double* dd = nullptr;
