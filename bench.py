@@ -97,6 +97,22 @@ class ClockSampler:
         return out
 
 
+def max_over_ranks(ms, dev):
+    """Slowest rank's time (the job's time); identity on one process."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(ms)
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(ws, units_per_rank, ms):
+    """Whole-job throughput: the units all ranks processed / the job's time."""
+    return ws * units_per_rank / (ms / 1000.0)
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -333,13 +349,9 @@ def run_ours(args):
     e1.record(stream)
     barrier()
     clk = clocks.stop()
-    t_ms = e0.elapsed_time(e1)
-    if ws > 1:
-        tt = torch.tensor([t_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_ms = float(tt.item())
+    t_ms = max_over_ranks(e0.elapsed_time(e1), dev)
     ms_per_step = t_ms / args.steps
-    value = ws * args.steps / (t_ms / 1000.0)
+    value = job_rate(ws, args.steps, t_ms)
     # converged solves only count
     ok = all(i["status"] == 0 and i["relres"] <= W["tol"] for i in infos)
 
@@ -371,12 +383,8 @@ def run_ours(args):
         hx.copy_(xx, non_blocking=True)
     e1.record(stream)
     barrier()
-    e2e_ms = e0.elapsed_time(e1)
-    if ws > 1:
-        tt = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_ms = float(tt.item())
-    e2e = {"value": ws * args.steps / (e2e_ms / 1000.0), "unit": "solves/s",
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1), dev)
+    e2e = {"value": job_rate(ws, args.steps, e2e_ms), "unit": "solves/s",
            "h2d_bytes_per_step": hb.numel() * hb.element_size(),
            "d2h_bytes_per_step": hx.numel() * hx.element_size()}
 
@@ -448,7 +456,7 @@ def run_ours(args):
     return 0
 
 
-def main():
+def build_parser():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
@@ -460,8 +468,13 @@ def main():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-baseline", action="store_true")
     ap.add_argument("--persistent", action="store_true", help="one cooperative kernel per basis build")
-    ap.add_argument("--no-extras", action="store_true", help="skip the sketch, sRR and batched measurements")
-    args = ap.parse_args()
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the sketch, sRR, batched and Laplacian measurements")
+    return ap
+
+
+def main():
+    args = build_parser().parse_args()
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

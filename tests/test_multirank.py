@@ -1,0 +1,76 @@
+"""bench.py's multi-process path on CPU: two gloo ranks on 127.0.0.1.
+
+Every rank solves its own replica (no data-path collective); the job's time
+is the slowest rank's, and the job's value is all ranks' solves over it.
+"""
+import os
+import socket
+import sys
+
+import pytest
+import torch.multiprocessing as mp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, ws, port, q):
+    import torch
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    import bench
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(ws),
+                      LOCAL_RANK=str(rank))
+    dist.init_process_group("gloo", rank=rank, world_size=ws)
+    try:
+        w, r, l = bench._dist()
+        t = bench.max_over_ranks(100.0 + 50.0 * rank, torch.device("cpu"))
+        q.put((rank, w, r, l, t, bench.job_rate(w, 5, t)))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_take_the_slowest_time_and_sum_the_work():
+    ws = 2
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_rank_main, args=(r, ws, PORT[0], q)) for r in range(ws)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    got = sorted(q.get(timeout=10) for _ in range(ws))
+    for rank, w, r, l, t, v in got:
+        assert (w, r, l) == (ws, rank, rank)
+        assert t == 150.0                      # the slower rank's time on every rank
+        assert v == pytest.approx(2 * 5 / 0.150)  # 10 solves in 150 ms
+
+
+def test_single_process_is_identity():
+    import torch
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.max_over_ranks(12.5, torch.device("cpu")) == 12.5
+    assert bench.job_rate(1, 3, 1500.0) == pytest.approx(2.0)
+
+
+PORT = [_free_port()]
+
+
+def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
+    # under torchrun the oracle arm runs and prints on rank 0 only; other
+    # ranks exit 0 without work
+    sys.path.insert(0, ROOT)
+    import bench
+    monkeypatch.setenv("RANK", "1")
+    monkeypatch.setenv("WORLD_SIZE", "2")
+    monkeypatch.setenv("LOCAL_RANK", "1")
+    args = bench.build_parser().parse_args(["--impl", "reference", "--gpus", "2", "--steps", "1", "--warmup", "0"])
+    assert bench.run_reference(args) == 0
+    assert capsys.readouterr().out == ""
