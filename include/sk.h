@@ -38,7 +38,7 @@ typedef enum {
   SK_ENAN = 4,       /* NaN/Inf met in an input or a reduction */
   SK_ENOCONV = 5,    /* maxit cycles without reaching tol; best x and info are still written */
   SK_EILLCOND = 6,   /* kappa(T) > stab_tol could not be cured by truncation */
-  SK_ETIMEOUT = 7,   /* reserved: a bounded device-side wait gave up */
+  SK_ETIMEOUT = 7,   /* a bounded device-side wait gave up (persistent basis kernel's grid barrier) */
   SK_EHASH = 8       /* sketch hash found no distinct row in 16 attempts (s too small for zeta) */
 } sk_status;
 
@@ -165,6 +165,9 @@ typedef struct {
                               ignored; supported by trunc_arnoldi_basis, sgmres_solve and
                               sgmres_solve_batched (srr_eigs: SK_EINVAL) */
   double cheb_c, cheb_dx, cheb_dy;
+  int barrier_spins;       /* persistent kernel: polls of a grid barrier before it gives up and
+                              the call returns SK_ETIMEOUT; 0 = default (2^22, ~0.1 s), -1 = give
+                              up at the first poll (exercises the timeout path) */
 } sk_opts;
 
 void sk_opts_default(sk_opts* o);

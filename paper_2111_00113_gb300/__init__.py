@@ -172,7 +172,7 @@ def sketch_apply_noalloc(B, s, zeta=0, seed=7):
 
 def make_opts(basis=torch.float64, sketch="sparse", zeta=0, seed=7, stab_tol=0.0, maxit=10000, cgs_passes=2,
               tau=1e-8, symmetric=False, breakdown=0.0, use_graph=True, persistent=False, batch_workers=0,
-              cheb=None):
+              cheb=None, barrier_spins=0):
     """Solver options.  cheb=(c, dx, dy) selects the Chebyshev basis (§4.3)
     for a spectrum inside [c - dx, c + dx] x [-dy, dy]."""
     o = N.SkOpts()
@@ -190,6 +190,7 @@ def make_opts(basis=torch.float64, sketch="sparse", zeta=0, seed=7, stab_tol=0.0
     o.use_graph = int(bool(use_graph))
     o.persistent = int(bool(persistent))
     o.batch_workers = int(batch_workers)
+    o.barrier_spins = int(barrier_spins)
     if cheb is not None:
         o.basis_kind = 1
         o.cheb_c, o.cheb_dx, o.cheb_dy = (float(v) for v in cheb)
@@ -197,7 +198,7 @@ def make_opts(basis=torch.float64, sketch="sparse", zeta=0, seed=7, stab_tol=0.0
 
 
 def trunc_arnoldi_basis(A, r0, d, k, dtype=torch.float64, s=None, zeta=0, seed=7, kind="sparse", cgs_passes=2,
-                        persistent=False, cheb=None):
+                        persistent=False, cheb=None, barrier_spins=0):
     """k-truncated Arnoldi basis (§1.2.2 eq. (partorth)).
 
     Returns dict(B (n x (d+1), column-major), Hbar ((d+1) x d), SB, SAB (s x d
@@ -213,7 +214,8 @@ def trunc_arnoldi_basis(A, r0, d, k, dtype=torch.float64, s=None, zeta=0, seed=7
         SB = empty_colmajor(s, d, torch.float64, r0.device)
         SAB = empty_colmajor(s, d, torch.float64, r0.device)
     du = C.c_int(0)
-    o = make_opts(basis=dtype, cgs_passes=cgs_passes, persistent=persistent, cheb=cheb)
+    o = make_opts(basis=dtype, cgs_passes=cgs_passes, persistent=persistent, cheb=cheb,
+                  barrier_spins=barrier_spins)
     N.check(N.lib.trunc_arnoldi_basis(A._h, _ptr(r0), d, k, _DT[dtype], _ptr(B), _ptr(Hbar),
                                       C.byref(skp) if skp is not None else None, _ptr(SB), _ptr(SAB),
                                       C.byref(o), C.byref(du), _stream()))

@@ -318,6 +318,8 @@ struct BasisBuffers {
   double* rho2_mut() const { return const_cast<double*>(bp.rho2); }
   // Chebyshev basis: recurrence parameters and its workspace (call after alloc)
   sk_status set_kind(const sk_opts& o, Scratch& sc) {
+    if (o.barrier_spins > 0) pw.spin_limit = o.barrier_spins;
+    else if (o.barrier_spins < 0) pw.spin_limit = 0;
     bp.kind = o.basis_kind;
     if (o.basis_kind != SK_BASIS_CHEBYSHEV) return SK_OK;
     persistent = false;

@@ -199,3 +199,29 @@ def test_single_pass_needs_fp64_basis(skg):
     r = torch.tensor(synth.randn(1, N * N), device="cuda")
     with pytest.raises(skg.SkError, match="cgs_passes"):
         skg.trunc_arnoldi_basis(op, r, 8, 2, dtype=torch.float32, cgs_passes=1)
+
+
+def test_persistent_barrier_timeout_is_reported(skg):
+    # Failure detection without a GPU fault: the cooperative kernel's grid
+    # barriers are bounded; with barrier_spins = -1 a CTA that is not the last
+    # to arrive gives up at its first poll, sets the error word, and every CTA
+    # leaves the kernel.  The call reports SK_ETIMEOUT and the context stays
+    # usable.
+    import torch
+    from paper_2111_00113_gb300 import _native as N
+    n = 256
+    coef, _ = _cd(n, 10.0)
+    op = skg.Op.stencil5(n, n, coef)
+    r = torch.tensor(synth.randn(4, n * n), device="cuda")
+    seen = []
+    for _ in range(5):
+        try:
+            skg.trunc_arnoldi_basis(op, r, 10, 2, dtype=torch.float32, persistent=True, barrier_spins=-1)
+            seen.append(N.SK_OK)
+        except skg.SkError as e:
+            assert e.status == N.SK_ETIMEOUT, e
+            seen.append(e.status)
+    assert N.SK_ETIMEOUT in seen
+    out = skg.trunc_arnoldi_basis(op, r, 10, 2, dtype=torch.float32, persistent=True)
+    assert out["d_used"] == 10
+    torch.cuda.synchronize()
