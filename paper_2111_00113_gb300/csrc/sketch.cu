@@ -520,6 +520,73 @@ gather_rows_kernel(const T* __restrict__ B, int64_t ldb, int ncols, int64_t n, i
   }
 }
 
+// One column (the sketched residual g = S r): thread r owns sketch row r and
+// sums in a register over all chunks of its group; the chunk of the vector
+// is contiguous, so it is staged with 16-byte asynchronous copies (double
+// buffered like the row-owner gather).  FP64 data: plain FP64 sums.
+__host__ __device__ static inline size_t col_buf_bytes(int s, int zeta) {
+  return (size_t)kChunk * sizeof(double) + entries_bytes(zeta) + (size_t)rp_stride(s) * sizeof(uint32_t);
+}
+
+__global__ void __launch_bounds__(kRowsMaxS)
+gather_col_kernel(const double* __restrict__ x, int64_t n, int s, int zeta, int nchunks, int chunks_per_group,
+                  const uint32_t* __restrict__ rowptr, const uint16_t* __restrict__ entries,
+                  double* __restrict__ partial) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const size_t buf_bytes = col_buf_bytes(s, zeta);
+  const int g = blockIdx.x;
+  const int c_begin = g * chunks_per_group;
+  const int c_end = min(nchunks, c_begin + chunks_per_group);
+  const int nt = blockDim.x;
+  const int ent_copies = (int)(entries_bytes(zeta) / 16);
+  const int rp_copies = (int)(rp_stride(s) / 4);
+  auto stage = [&](int c, int b) {
+    unsigned char* base = smem_raw + (size_t)b * buf_bytes;
+    const int64_t i0 = (int64_t)c * kChunk;
+    const int Lc = (int)((n - i0) < kChunk ? (n - i0) : kChunk);
+    double* tile = reinterpret_cast<double*>(base);
+    // 16-byte copies where both ends are aligned and in range; single elements otherwise
+    const bool al = (((uintptr_t)(x + i0)) & 15) == 0;
+    if (al) {
+      for (int q = threadIdx.x; q < Lc / 2; q += nt) cp_async16(tile + 2 * q, x + i0 + 2 * q);
+      if ((Lc & 1) && threadIdx.x == 0) cp_async_e<8>(tile + Lc - 1, x + i0 + Lc - 1, true);
+    } else {
+      for (int q = threadIdx.x; q < Lc; q += nt) cp_async_e<8>(tile + q, x + i0 + q, true);
+    }
+    const unsigned char* esrc = reinterpret_cast<const unsigned char*>(entries + (int64_t)c * kChunk * zeta);
+    unsigned char* edst = base + (size_t)kChunk * sizeof(double);
+    for (int q = threadIdx.x; q < ent_copies; q += nt) cp_async16(edst + q * 16, esrc + q * 16);
+    const unsigned char* rsrc = reinterpret_cast<const unsigned char*>(rowptr + (int64_t)c * rp_stride(s));
+    unsigned char* rdst = edst + entries_bytes(zeta);
+    for (int q = threadIdx.x; q < rp_copies; q += nt) cp_async16(rdst + q * 16, rsrc + q * 16);
+  };
+  double acc = 0;
+  const int r = threadIdx.x;
+  if (c_begin < c_end) stage(c_begin, 0);
+  cp_async_commit();
+  for (int c = c_begin; c < c_end; ++c) {
+    const int b = (c - c_begin) & 1;
+    if (c + 1 < c_end) stage(c + 1, b ^ 1);
+    cp_async_commit();
+    cp_async_wait1();
+    __syncthreads();
+    const unsigned char* base = smem_raw + (size_t)b * buf_bytes;
+    const double* tile = reinterpret_cast<const double*>(base);
+    const uint16_t* ent = reinterpret_cast<const uint16_t*>(base + (size_t)kChunk * sizeof(double));
+    const uint32_t* rp = reinterpret_cast<const uint32_t*>(base + (size_t)kChunk * sizeof(double) + entries_bytes(zeta));
+    if (r < s) {
+      const int e0 = (int)rp[r], e1 = (int)rp[r + 1];
+      for (int e = e0; e < e1; ++e) {
+        const uint16_t v = ent[e];
+        const double sd = (v & 0x8000) ? -1.0 : 1.0;  // exact product: an add or a subtract
+        acc = fma(sd, tile[v & 0x7FFF], acc);
+      }
+    }
+    __syncthreads();
+  }
+  if (r < s) partial[(int64_t)g * s + r] = acc;
+}
+
 __global__ void reduce_partials_kernel(const double* __restrict__ partial, int ngroups, int ncols, int s,
                                        double scale, double* __restrict__ SB) {
   const int64_t total = (int64_t)ncols * s;
@@ -568,6 +635,7 @@ static int pick_width(int s, int zeta, int ncols, size_t csize) {
 }
 
 struct GatherShape {
+  bool col;   // one FP64 column (gather_col_kernel)
   bool rows;  // row-owner kernel (FP32/FP64 data, s <= kRowsMaxS, at least one full tile of columns)
   int W, ntiles, ngroups, cpg;
 };
@@ -576,9 +644,10 @@ static GatherShape gather_shape(const SketchPlan& p, int ncols, sk_dtype dtype) 
   GatherShape g;
   const size_t csize = dtype == SK_F64 ? 8 : 4;
   const int rows_w = kRowsBytes / (int)csize;
-  g.rows = (dtype == SK_F32 || dtype == SK_F64) && p.s <= kRowsMaxS && ncols >= rows_w &&
+  g.col = dtype == SK_F64 && ncols == 1 && p.s <= kRowsMaxS && 2 * col_buf_bytes(p.s, p.zeta) <= (size_t)kDynSmemLimit;
+  g.rows = !g.col && (dtype == SK_F32 || dtype == SK_F64) && p.s <= kRowsMaxS && ncols >= rows_w &&
            2 * rows_buf_bytes(p.s, p.zeta) <= (size_t)kDynSmemLimit;
-  g.W = g.rows ? rows_w : pick_width(p.s, p.zeta, ncols, csize);
+  g.W = g.col ? 1 : g.rows ? rows_w : pick_width(p.s, p.zeta, ncols, csize);
   g.ntiles = (ncols + g.W - 1) / g.W;
   const int target = num_sms();
   int ngroups = (target + g.ntiles - 1) / g.ntiles;
@@ -611,7 +680,14 @@ sk_status plan_apply_ws(const SketchPlan& p, const void* B, int64_t ldb, int nco
                         double* partial, cudaStream_t st) {
   const GatherShape g = gather_shape(p, ncols, dtype);
   sk_status stt;
-  if (dtype == SK_F64 && g.rows) stt = launch_rows(p, (const double*)B, ldb, ncols, partial, g, st);
+  if (g.col) {
+    const size_t smem = 2 * col_buf_bytes(p.s, p.zeta);
+    SK_CUDA(cudaFuncSetAttribute(gather_col_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kDynSmemLimit));
+    gather_col_kernel<<<g.ngroups, (p.s + 31) / 32 * 32, smem, st>>>((const double*)B, p.n, p.s, p.zeta, p.nchunks,
+                                                                     g.cpg, p.rowptr, p.entries, partial);
+    SK_CUDA(cudaGetLastError());
+    stt = SK_OK;
+  } else if (dtype == SK_F64 && g.rows) stt = launch_rows(p, (const double*)B, ldb, ncols, partial, g, st);
   else if (dtype == SK_F64) stt = gather_dispatch<double>(p, (const double*)B, ldb, ncols, partial, g.ngroups, g.cpg, g.W, st);
   else if (dtype == SK_F32 && g.rows) stt = launch_rows(p, (const float*)B, ldb, ncols, partial, g, st);
   else if (dtype == SK_F32) stt = gather_dispatch<float>(p, (const float*)B, ldb, ncols, partial, g.ngroups, g.cpg, g.W, st);

@@ -38,7 +38,7 @@ def test_sparse_sign_indices_bit_exact(skg):
 
 
 @pytest.mark.parametrize("n,c,s,zeta", [(4096, 41, 80, 8), (2048 * 3 + 17, 9, 600, 12), (77, 1, 16, 3),
-                                        (100003, 3, 200, 10)])
+                                        (100003, 3, 200, 10), (1024 * 5 + 3, 1, 600, 12), (1024 * 9, 1, 640, 14)])
 def test_sparse_sign_fp64(skg, n, c, s, zeta):
     import torch
     X = np.random.default_rng(n).standard_normal((n, c))
@@ -122,3 +122,15 @@ def test_full_size_sketch_sampled(skg):
         col = Xt[:, j].to(torch.float64).cpu().numpy()
         ref = S @ col
         assert _relf(got[:, j].cpu().numpy(), ref) <= 1e-5
+
+
+def test_sparse_sign_single_column_unaligned(skg):
+    # one FP64 column that does not start on a 16-byte boundary (a view at
+    # offset 1) and has an odd length: the staging falls back to 8-byte copies
+    import torch
+    n, s, zeta = 1024 * 3 + 5, 300, 10
+    X = np.random.default_rng(3).standard_normal(n + 1)
+    Xt = torch.tensor(X, device="cuda")[1:]
+    got = skg.sketch_apply(Xt, s, zeta, 4).cpu().numpy()
+    ref = sketch.sparse_sign_apply(4, s, zeta, X[1:, None])[:, 0]
+    assert _relf(got, ref) <= 1e-12
