@@ -253,6 +253,7 @@ def _bench_srr(skg, dev):
 def _bench_laplace(skg, dev):
     """The section 8 Laplacian example: Chebyshev basis vs truncated Arnoldi (FP32)."""
     import torch
+    import synth
     W = synth.WORKLOADS["laplace"]
     N = W["N"]
     op = skg.Op.stencil5(N, N, (4.0, -1.0, -1.0, -1.0, -1.0),
