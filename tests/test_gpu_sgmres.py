@@ -159,3 +159,27 @@ def test_scale_workload_full_size(skg, dtype):
         assert rel <= 1.5 * ref["relres"][c]
     else:
         assert info["cycles"] <= ref["cycles"] + 2
+
+
+def test_maximum_basis_size_one_cycle(skg):
+    # the largest basis sgmres_solve accepts (d = 768: the LS solve keeps
+    # 33 d doubles in shared memory) with s = 2d = 1536 rows (beyond the
+    # row-owner gather: the general gather kernel), FP64.  At this size the
+    # k = 2 basis reaches kappa ~ 1e16, so both sides truncate the triangle,
+    # each with its own kappa estimate (exact kappa_2 in the oracle, the
+    # diagonal ratio on the GPU): both must solve the system in one cycle.
+    import torch
+    N, d, k, s = 96, 768, 2, 1536
+    coef, A, f = _problem(N, 20.0, 6)
+    zeta = hashing.default_zeta(d)
+    op = skg.Op.stencil5(N, N, coef)
+    x1, info = skg.sgmres_solve(op, torch.tensor(f, device="cuda"), d, k, s, 1e-300, maxit=1, zeta=zeta, seed=7)
+    sk = lambda M: sketch.sparse_sign_apply(7, s, zeta, M)
+    xo, oinfo = krylov.sgmres_cycle(A, f, np.zeros(N * N), d, k, sk)
+    r_gpu = _relres(A, f, x1.cpu().numpy())
+    r_ora = _relres(A, f, xo)
+    assert info["d_used"] == oinfo["d_used"] == d
+    assert r_ora <= 1e-9
+    assert r_gpu <= max(1.5 * r_ora, 1e-9), (r_gpu, r_ora, info["width"], oinfo["width"])
+    with pytest.raises(skg.SkError):
+        skg.sgmres_solve(op, torch.tensor(f, device="cuda"), d + 1, k, 2 * d + 2, 1e-8, maxit=1)
