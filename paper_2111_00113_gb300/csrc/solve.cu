@@ -36,6 +36,11 @@ __device__ __forceinline__ void gload_rows(const T* __restrict__ col, int64_t i,
   if constexpr (G == 4 && std::is_same<T, float>::value) {
     const float4 t = __ldg(reinterpret_cast<const float4*>(col + i));
     v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+  } else if constexpr (G == 8 && std::is_same<T, float>::value) {
+    const float4 a = __ldg(reinterpret_cast<const float4*>(col + i));
+    const float4 b = __ldg(reinterpret_cast<const float4*>(col + i + 4));
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+    v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
   } else if constexpr (G == 4 && std::is_same<T, double>::value) {
     const double2 a = __ldg(reinterpret_cast<const double2*>(col + i));
     const double2 b = __ldg(reinterpret_cast<const double2*>(col + i + 2));
@@ -187,6 +192,9 @@ static sk_status enqueue_update(double* x, const void* B, int64_t ldb, int64_t n
   if (dt == SK_F64)
     return vec ? launch_update<double, 4>(x, (const double*)B, ldb, n, d, y, diag, st)
                : launch_update<double, 1>(x, (const double*)B, ldb, n, d, y, diag, st);
+  // FP32: 8 consecutive rows per thread (two 16-byte loads per column) keep
+  // the 2^20-row grid to one wave of resident CTAs
+  if (dt == SK_F32 && vec && n % 8 == 0) return launch_update<float, 8>(x, (const float*)B, ldb, n, d, y, diag, st);
   if (dt == SK_F32)
     return vec ? launch_update<float, 4>(x, (const float*)B, ldb, n, d, y, diag, st)
                : launch_update<float, 1>(x, (const float*)B, ldb, n, d, y, diag, st);
