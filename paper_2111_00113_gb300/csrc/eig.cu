@@ -38,23 +38,26 @@ __global__ void __launch_bounds__(kEigThreads)
 hessenberg_kernel(double* __restrict__ H, int n, double* __restrict__ tau) {
   __shared__ double sh[32];
   __shared__ double w[kEigMaxN];
+  __shared__ double s_sc[2];
   for (int k = 0; k + 2 < n; ++k) {
     // reflector for x = H[k+1:n, k]
     double part = 0;
     for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) part += H[i + (int64_t)k * n] * H[i + (int64_t)k * n];
     const double nrm2 = block_sum_d(part, sh);
-    const double x0 = H[k + 1 + (int64_t)k * n];
-    const double nrm = sqrt(nrm2);
-    const double alpha = x0 >= 0 ? -nrm : nrm;
-    const double v0 = x0 - alpha;
-    const double vtv = nrm2 - x0 * x0 + v0 * v0;
-    const double t = vtv > 0 ? 2.0 / vtv : 0.0;
-    __syncthreads();
+    // the reflector's scalars once (FP64 sqrt and divide are slow here), broadcast
     if (threadIdx.x == 0) {
+      const double x0 = H[k + 1 + (int64_t)k * n];
+      const double nrm = sqrt(nrm2);
+      const double alpha = x0 >= 0 ? -nrm : nrm;
+      const double v0 = x0 - alpha;
+      const double vtv = nrm2 - x0 * x0 + v0 * v0;
+      s_sc[0] = vtv > 0 ? 2.0 / vtv : 0.0;
+      s_sc[1] = alpha;
       H[k + 1 + (int64_t)k * n] = v0;  // v stored in H[k+1:, k]; H[k+1,k] := alpha below
-      tau[k] = t;
+      tau[k] = s_sc[0];
     }
     __syncthreads();
+    const double t = s_sc[0], alpha = s_sc[1];
     const double* v = H + (int64_t)k * n;  // v[i] for i >= k+1
     // left: H[k+1:, k+1:] -= t v (v^T H[k+1:, k+1:]); one warp per column
     {
@@ -74,9 +77,14 @@ hessenberg_kernel(double* __restrict__ H, int n, double* __restrict__ tau) {
     __syncthreads();
     // right: H[:, k+1:] -= t (H[:, k+1:] v) v^T
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
-      double a = 0;
-      for (int j = k + 1; j < n; ++j) a += H[i + (int64_t)j * n] * v[j];
-      w[i] = a * t;
+      double a[4] = {0, 0, 0, 0};  // four independent chains (FP64 FMA latency ~64 cycles)
+      int j = k + 1;
+      for (; j + 3 < n; j += 4) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) a[u] += H[i + (int64_t)(j + u) * n] * v[j + u];
+      }
+      for (; j < n; ++j) a[0] += H[i + (int64_t)j * n] * v[j];
+      w[i] = ((a[0] + a[1]) + (a[2] + a[3])) * t;
     }
     __syncthreads();
     for (int q = threadIdx.x; q < n * (n - k - 1); q += blockDim.x) {
@@ -104,6 +112,7 @@ hqr_kernel(const double* __restrict__ Hg, const double* __restrict__ tau, int n,
   __shared__ double sh[32];
   __shared__ int s_l, s_m;
   __shared__ double s_shift[3];  // x, y, w of the shift polynomial
+  __shared__ double s_ref[6];    // the current 3x3 reflector (vx, vy, vz, q2, r2) and a non-zero flag
   if (threadIdx.x == 0) {
     int o = 0;
     for (int i = 0; i < n; ++i) { off[i] = o; o += n - max(0, i - 3); }
@@ -212,39 +221,57 @@ hqr_kernel(const double* __restrict__ Hg, const double* __restrict__ tau, int n,
       const int m = s_m;
       ++its;
       const double xs = s_shift[0], ys = s_shift[1], ws = s_shift[2];
-      // double-shift QR step on rows l..nn, columns m..nn (bulge chase)
+      // double-shift QR step on rows l..nn, columns m..nn (bulge chase).  Thread
+      // 0 forms each 3x3 reflector once and broadcasts it (FP64 divide and sqrt
+      // take ~600 cycles each here; every thread computing them would also
+      // saturate the FP64 pipe).
       for (int k = m; k <= nn - 1; ++k) {
-        double p, q, r = 0.0, xk = 0.0;
-        if (k == m) {
-          const double zm = A.at(m, m);
-          const double rr0 = xs - zm, ss0 = ys - zm;
-          p = (rr0 * ss0 - ws) / A.at(m + 1, m) + A.at(m, m + 1);
-          q = A.at(m + 1, m + 1) - zm - rr0 - ss0;
-          r = A.at(m + 2, m + 1);
-          xk = fabs(p) + fabs(q) + fabs(r);
-          p /= xk; q /= xk; r /= xk;
-        } else {
-          p = A.at(k, k - 1);
-          q = A.at(k + 1, k - 1);
-          if (k != nn - 1) r = A.at(k + 2, k - 1);
-          xk = fabs(p) + fabs(q) + fabs(r);
-          if (xk != 0.0) { p /= xk; q /= xk; r /= xk; }
-        }
-        const double s = copysign(sqrt(p * p + q * q + r * r), p);
-        __syncthreads();  // everyone has read the column before it changes
-        if (s == 0.0) continue;
         if (threadIdx.x == 0) {
+          double p, q, r = 0.0, xk = 0.0;
           if (k == m) {
-            if (l != m) A.at(k, k - 1) = -A.at(k, k - 1);
+            const double zm = A.at(m, m);
+            const double rr0 = xs - zm, ss0 = ys - zm;
+            p = (rr0 * ss0 - ws) / A.at(m + 1, m) + A.at(m, m + 1);
+            q = A.at(m + 1, m + 1) - zm - rr0 - ss0;
+            r = A.at(m + 2, m + 1);
+            xk = fabs(p) + fabs(q) + fabs(r);
+            const double ix = 1.0 / xk;
+            p *= ix; q *= ix; r *= ix;
           } else {
-            A.at(k, k - 1) = -s * xk;
-            A.at(k + 1, k - 1) = 0.0;
-            if (k != nn - 1) A.at(k + 2, k - 1) = 0.0;
+            p = A.at(k, k - 1);
+            q = A.at(k + 1, k - 1);
+            if (k != nn - 1) r = A.at(k + 2, k - 1);
+            xk = fabs(p) + fabs(q) + fabs(r);
+            if (xk != 0.0) {
+              const double ix = 1.0 / xk;
+              p *= ix; q *= ix; r *= ix;
+            }
+          }
+          const double sg = copysign(sqrt(p * p + q * q + r * r), p);
+          s_ref[5] = (sg == 0.0) ? 0.0 : 1.0;
+          if (sg != 0.0) {
+            if (k == m) {
+              if (l != m) A.at(k, k - 1) = -A.at(k, k - 1);
+            } else {
+              A.at(k, k - 1) = -sg * xk;
+              A.at(k + 1, k - 1) = 0.0;
+              if (k != nn - 1) A.at(k + 2, k - 1) = 0.0;
+            }
+            const double pp = p + sg;
+            const double is = 1.0 / sg, ip = 1.0 / pp;
+            s_ref[0] = pp * is;  // vx
+            s_ref[1] = q * is;   // vy
+            s_ref[2] = r * is;   // vz
+            s_ref[3] = q * ip;   // q2
+            s_ref[4] = r * ip;   // r2
           }
         }
-        const double pp = p + s;
-        const double vx = pp / s, vy = q / s, vz = r / s;
-        const double q2 = q / pp, r2 = r / pp;
+        __syncthreads();
+        if (s_ref[5] == 0.0) {
+          __syncthreads();  // all threads have read the flag before thread 0 forms the next reflector
+          continue;
+        }
+        const double vx = s_ref[0], vy = s_ref[1], vz = s_ref[2], q2 = s_ref[3], r2 = s_ref[4];
         // rows k..k+2, columns k..nn
         for (int j = k + threadIdx.x; j <= nn; j += blockDim.x) {
           double t = A.at(k, j) + q2 * A.at(k + 1, j);
