@@ -157,7 +157,9 @@ typedef struct {
   double breakdown;        /* ||w_j|| <= breakdown*||A b_{j-1}|| ends the basis; <=0 = 1e-13 (F64) / 1e-6 */
   int use_graph;           /* capture each restart cycle in a CUDA graph (default 1) */
   int persistent;          /* grid operators: build the basis in one cooperative kernel
-                              with bounded grid barriers (1), or 3 launches per step (0, default) */
+                              with bounded grid barriers (1), or 3 launches per step (0, default);
+                              the persistent kernel covers k <= 4 with FP32/FP64 storage, other
+                              cases take the 3-launch path */
   int batch_workers;       /* sgmres_solve_batched: concurrent jobs (threads x streams); 0 = 16 */
   sk_basis_kind basis_kind; /* default SK_BASIS_ARNOLDI.  SK_BASIS_CHEBYSHEV: no inner products;
                               needs the spectrum inside the rectangle [c - dx, c + dx] x [-dy, dy]

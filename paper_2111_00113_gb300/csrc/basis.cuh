@@ -48,7 +48,7 @@ struct PersistWork {
   long long spin_limit;  // barrier spin iterations before giving up
 };
 
-bool persist_shape(const sk_op* op, sk_dtype dt, int* grid, int* ept, size_t* smem);
+bool persist_shape(const sk_op* op, sk_dtype dt, int k, int* grid, int* ept, size_t* smem);
 sk_status enqueue_basis_persistent(const BasisParams& bp, const sk_op* op, PersistWork& w, cudaStream_t st);
 
 int basis_grid(int64_t n, int G);

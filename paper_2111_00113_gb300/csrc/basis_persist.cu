@@ -401,9 +401,7 @@ template <typename T, int EPT>
 static sk_status launch_persist_k(const PersistParams& pp, const GridOp<typename Compute<T>::type>& A, int grid,
                                   size_t smem, cudaStream_t st) {
   if (pp.bp.k <= 2) return launch_persist_t<T, 2, EPT>(pp, A, grid, smem, st);
-  if (pp.bp.k <= 4) return launch_persist_t<T, 4, EPT>(pp, A, grid, smem, st);
-  if (pp.bp.k <= 8) return launch_persist_t<T, 8, EPT>(pp, A, grid, smem, st);
-  return launch_persist_t<T, 16, EPT>(pp, A, grid, smem, st);
+  return launch_persist_t<T, 4, EPT>(pp, A, grid, smem, st);  // persist_shape admits k <= 4
 }
 
 template <typename T>
@@ -418,9 +416,12 @@ static sk_status launch_persist_e(const PersistParams& pp, const GridOp<typename
   }
 }
 
-// Geometry of the persistent launch; false if the problem does not fit.
-bool persist_shape(const sk_op* op, sk_dtype dt, int* grid, int* ept, size_t* smem) {
+// Geometry of the persistent launch; false if the problem does not fit.  The
+// opt-in persistent path covers k <= 4 with FP32 or FP64 storage (other
+// cases use the three-launch path), which keeps its instantiations few.
+bool persist_shape(const sk_op* op, sk_dtype dt, int k, int* grid, int* ept, size_t* smem) {
   if (!(op->kind == OP_STENCIL5 || op->kind == OP_DIFFUSION)) return false;
+  if (k > 4 || dt == SK_BF16) return false;
   if (op->n >= (1ll << 30)) return false;
   const int64_t n = op->n;
   int g = num_sms();
@@ -447,7 +448,7 @@ bool persist_shape(const sk_op* op, sk_dtype dt, int* grid, int* ept, size_t* sm
 sk_status enqueue_basis_persistent(const BasisParams& bp, const sk_op* op, PersistWork& w, cudaStream_t st) {
   int grid = 0, ept = 0;
   size_t smem = 0;
-  if (!persist_shape(op, bp.dtype, &grid, &ept, &smem)) { set_error("persistent basis: shape"); return SK_EINVAL; }
+  if (!persist_shape(op, bp.dtype, bp.k, &grid, &ept, &smem)) { set_error("persistent basis: shape"); return SK_EINVAL; }
   PersistParams pp;
   pp.bp = bp;
   pp.ctl.bar_count = w.bar;
@@ -466,8 +467,7 @@ sk_status enqueue_basis_persistent(const BasisParams& bp, const sk_op* op, Persi
   OpView<float> v;
   SK_TRY(make_view(op, &v, st));
   GridOp<float> A{v.kind, v.nx, v.ny, v.cP, v.cE, v.cW, v.cN, v.cS, v.shift, v.theta};
-  if (bp.dtype == SK_F32) return launch_persist_e<float>(pp, A, grid, ept, smem, st);
-  return launch_persist_e<__nv_bfloat16>(pp, A, grid, ept, smem, st);
+  return launch_persist_e<float>(pp, A, grid, ept, smem, st);
 }
 
 }  // namespace sk

@@ -291,7 +291,7 @@ struct BasisBuffers {
     if (dt == SK_F64) SK_TRY(sc.alloc(&bp.M, (size_t)n));
     int pg = 0, pe = 0;
     size_t psm = 0;
-    persistent = want_persistent && op != nullptr && persist_shape(op, dt, &pg, &pe, &psm);
+    persistent = want_persistent && op != nullptr && persist_shape(op, dt, k, &pg, &pe, &psm);
     std::memset(&pw, 0, sizeof(pw));
     if (persistent) {
       SK_TRY(sc.alloc(&pw.bar, 2));
