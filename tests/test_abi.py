@@ -65,5 +65,21 @@ def test_invalid_arguments_rejected_on_host(native):
     assert lib.sgmres_solve(h, None, dummy, 10, 2, 40, 1e-6, None, C.byref(info), None) == native.SK_EINVAL
     sk = native.SkSketch(0, 25, 8, 4, 1)
     assert lib.sketch_apply(C.byref(sk), dummy, 10, 1, 0, dummy, None) == native.SK_EINVAL  # ldb < n
+    # option combinations rejected before any device work
+    o1 = native.SkOpts()
+    lib.sk_opts_default(C.byref(o1))
+    o1.basis, o1.cgs_passes = native.SK_F32, 1  # one Gram-Schmidt pass needs an FP64 basis
+    assert lib.sgmres_solve(h, dummy, dummy, 10, 2, 40, 1e-6, C.byref(o1), C.byref(info), None) == native.SK_EINVAL
+    assert b"cgs_passes" in lib.sk_last_error()
+    o2 = native.SkOpts()
+    lib.sk_opts_default(C.byref(o2))
+    o2.basis_kind, o2.cheb_c = 1, 4.0  # Chebyshev basis without an interval
+    assert lib.sgmres_solve(h, dummy, dummy, 10, 2, 40, 1e-6, C.byref(o2), C.byref(info), None) == native.SK_EINVAL
+    assert b"Chebyshev" in lib.sk_last_error()
+    o2.basis_kind = 7  # unknown basis kind
+    assert lib.sgmres_solve(h, dummy, dummy, 10, 2, 40, 1e-6, C.byref(o2), C.byref(info), None) == native.SK_EINVAL
+    o3 = native.SkOpts()
+    lib.sk_opts_default(C.byref(o3))
+    assert o3.basis_kind == 0 and o3.barrier_spins == 0 and o3.persistent == 0
     lib.sk_op_destroy(hT)
     lib.sk_op_destroy(h)
