@@ -186,11 +186,12 @@ def test_restarted_sgmres_small_workload_converges():
 
 
 # ---- Chebyshev basis (§4.3, eq. (Chebrecurse)) --------------------------------
-@pytest.mark.parametrize("c,dx,dy", [(4.0, 4.0, 0.0), (1.0, 2.0, 0.0), (3.0, 2.5, 1.5)])
+@pytest.mark.parametrize("c,dx,dy", [(4.0, 4.0, 0.0), (1.0, 2.0, 0.0), (3.0, 2.5, 1.5), (3.0, 1.0, 2.0)])
 def test_chebyshev_basis_is_chebyshev_polynomials_on_a_diagonal(c, dx, dy):
     # For A = diag(lambda) the recurrence produces, up to positive scalars,
-    # T_j((A - c)/f) r with f = sqrt(dx^2 - dy^2) (the foci of the ellipse;
-    # f = dx for an interval): compare the unit columns with numpy's chebval.
+    # i^j T_j((A - c)/f) r with f = sqrt(dx^2 - dy^2) (the foci of the
+    # ellipse; f = dx for an interval; f imaginary for a tall ellipse, where
+    # i^j T_j is real): compare the unit columns with numpy's chebval.
     from numpy.polynomial import chebyshev as npc
     rng = np.random.default_rng(3)
     n, d = 200, 25
@@ -198,13 +199,16 @@ def test_chebyshev_basis_is_chebyshev_polynomials_on_a_diagonal(c, dx, dy):
     A = np.diag(lam)
     r = rng.standard_normal(n)
     B, M, H = krylov.chebyshev_basis(A, r, d, c, dx, dy)
-    f = np.sqrt(dx * dx - dy * dy)
+    f = np.sqrt(complex(dx * dx - dy * dy))
     z = (lam - c) / f
     for j in range(d + 1):
         e = np.zeros(j + 1)
         e[j] = 1.0
         v = npc.chebval(z, e) * r
-        v /= np.linalg.norm(v)
+        if dy > dx:
+            v = v * (1j) ** j  # real: T_j has the parity of j and f is imaginary
+        assert np.abs(v.imag).max() <= 1e-9 * np.abs(v).max()
+        v = v.real / np.linalg.norm(v.real)
         assert np.allclose(B[:, j], v, atol=1e-10), j
     assert np.allclose(M, A @ B[:, :d])
 
