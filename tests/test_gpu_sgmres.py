@@ -183,3 +183,27 @@ def test_maximum_basis_size_one_cycle(skg):
     assert r_gpu <= max(1.5 * r_ora, 1e-9), (r_gpu, r_ora, info["width"], oinfo["width"])
     with pytest.raises(skg.SkError):
         skg.sgmres_solve(op, torch.tensor(f, device="cuda"), d + 1, k, 2 * d + 2, 1e-8, maxit=1)
+
+
+def test_csr_operator_fp64_cycle_and_fp32_solve(skg):
+    # a general sparse (CSR) nonsymmetric operator: the convection-diffusion
+    # matrix plus a random sparse perturbation (scalar path of every pass).
+    # FP64: one cycle within 1.5x of the oracle's; FP32 basis: converges to 1e-8.
+    import scipy.sparse as sp
+    import torch
+    N, d, k, s = 48, 40, 2, 80
+    coef, A0, f = _problem(N, 15.0, 9)
+    P = sp.random(N * N, N * N, density=2e-4, random_state=3, format="csr")
+    A = (A0 + 0.05 * P).tocsr()
+    rp, ci, va = operators.csr_from_scipy(A)
+    op = skg.Op.csr(torch.tensor(rp, device="cuda"), torch.tensor(ci, device="cuda"),
+                    torch.tensor(va, device="cuda"))
+    zeta = hashing.default_zeta(d)
+    b = torch.tensor(f, device="cuda")
+    x1, info = skg.sgmres_solve(op, b, d, k, s, 1e-300, maxit=1, zeta=zeta, seed=7)
+    xo, _ = krylov.sgmres_cycle(A, f, np.zeros(N * N), d, k, lambda M: sketch.sparse_sign_apply(7, s, zeta, M))
+    r_gpu, r_ora = _relres(A, f, x1.cpu().numpy()), _relres(A, f, xo)
+    assert r_gpu <= 1.5 * r_ora and r_ora <= 1.5 * r_gpu, (r_gpu, r_ora)
+    x, info = skg.sgmres_solve(op, b, d, k, s, 1e-8, zeta=zeta, seed=7, basis=torch.float32, maxit=500)
+    assert info["status"] == 0, info
+    assert _relres(A, f, x.cpu().numpy()) <= 1e-8
