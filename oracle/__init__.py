@@ -19,8 +19,9 @@ Modules
   operators 5-point convection-diffusion and variable-coefficient
             diffusion operators (the model problems)
   krylov    k-truncated Arnoldi with double Gram-Schmidt, Householder QR,
-            sGMRES (Algorithm 1) with restarting (§3.5), Householder-Arnoldi
-            GMRES (§4.2)
+            sGMRES (Algorithm 1) with restarting (§3.5), iterative sGMRES
+            with early stopping (§5.2, §5.3), Householder-Arnoldi GMRES
+            (§4.2), the Chebyshev basis (§4.3)
   eigs      sketched Rayleigh-Ritz (Algorithm 2), Rayleigh-Ritz (§6.1)
   adjoint   dense adjoint gradient of ||x(theta)-x_t||^2
 

@@ -1,4 +1,5 @@
-"""k-truncated Arnoldi, Householder QR, sGMRES (Algorithm 1) and GMRES.
+"""k-truncated Arnoldi, Chebyshev basis, Householder QR, sGMRES (Algorithm 1,
+restarted and iterative) and GMRES.
 
 Test infrastructure only (see oracle/__init__.py).
 
@@ -13,6 +14,19 @@ import numpy as np
 # Basis generation: §1.2.2 eq. (partorth), Algorithm 1 (truncated Arnoldi
 # loop, "double Gram-Schmidt" implementation note), §4.2.
 # ---------------------------------------------------------------------------
+def _partorth(W, m, passes):
+    """w = (I - W W^T) m by ``passes`` classical Gram-Schmidt passes against
+    the columns of W (the k previous basis vectors); returns w, the summed
+    coefficients h and ||w||."""
+    w = m.copy()
+    h = np.zeros(W.shape[1])
+    for _ in range(passes):
+        c = W.T @ w
+        w = w - W @ c
+        h += c
+    return w, h, np.linalg.norm(w)
+
+
 def trunc_arnoldi(A, r, d, k, passes=2, breakdown=1e-13):
     """Basis B = [b_1..b_d] and reduced matrix AB = [m_1..m_d].
 
@@ -39,14 +53,7 @@ def trunc_arnoldi(A, r, d, k, passes=2, breakdown=1e-13):
     d_used = d
     for j in range(1, d):
         lo = max(0, j - k)
-        W = B[:, lo:j]
-        w = M[:, j - 1].copy()
-        h = np.zeros(j - lo)
-        for _ in range(passes):
-            c = W.T @ w
-            w = w - W @ c
-            h += c
-        nu = np.linalg.norm(w)
+        w, h, nu = _partorth(B[:, lo:j], M[:, j - 1], passes)
         if nu <= breakdown * np.linalg.norm(M[:, j - 1]):
             d_used = j
             break
@@ -226,6 +233,99 @@ def sgmres(A, f, x0, d, k, sketch, tol, maxit=10000, passes=2, stab_tol=1e14, br
         hist.append(rel)
         infos.append(info)
         cycles += 1
+    return x, hist, infos
+
+
+# ---------------------------------------------------------------------------
+# Iterative sGMRES (§5.2): each reduced-matrix column is sketched as soon as
+# it exists, the QR of S(A B_j) grows by one Householder reflector, and the
+# cycle stops on the residual estimate; adaptive restart (§5.3): the cycle
+# also ends, one column early, when kappa_2(T_j) first exceeds stab_tol.
+# ---------------------------------------------------------------------------
+def sgmres_iterative_cycle(A, f, x, dmax, k, sketch, tol_rel, passes=2, stab_tol=1e14, breakdown=1e-13):
+    """One cycle from the iterate x with at most dmax basis vectors.
+
+    g = S r_0.  For j = 1, 2, ..: b_j from the truncated recurrence of eq.
+    (partorth), m_j = A b_j, c_j = S m_j; reflectors H_1..H_{j-1} are
+    applied to c_j, H_j is formed from its entries j.. (the new column of
+    T_j is the top j entries), and z = H_j ... H_1 g.  Then
+        y_j = T_j^{-1} z[:j],   rhat_j = ||z[j:]|| = ||(I - U_j U_j^T) g||.
+    The cycle stops at the first j with rhat_j <= tol_rel * ||g|| (both
+    sides are sketched norms, so the sketch's distortion cancels to first
+    order; an absolute threshold on rhat_j alone lets a restart stop at j = 1
+    without progress once ||S r|| < threshold < ||r||), at a breakdown of
+    the recurrence (the Krylov space is invariant), at j = dmax, or -- when
+    kappa_2(T_j) > stab_tol -- with the previous solution y_{j-1}.
+    Returns x + B_j y_j and a dict: ``j`` (columns used), ``rhat`` (the
+    estimate for every j formed), ``kappa`` (kappa_2(T_j) likewise),
+    ``stop`` in {"tol", "kappa", "breakdown", "dmax"}, ``r0norm``.
+    """
+    r = f - A @ x
+    g = sketch(r)
+    n, s = r.shape[0], g.shape[0]
+    if not 1 <= dmax < s:
+        raise ValueError("need 1 <= dmax < s (the paper takes s = 2(dmax + 1))")
+    B = np.zeros((n, dmax))
+    T = np.zeros((dmax, dmax))
+    z = np.array(g, dtype=np.float64, copy=True)
+    gnorm = np.linalg.norm(g)
+    V = []
+    rhats, kappas = [], []
+    y = np.zeros(0)
+    stop = "dmax"
+    B[:, 0] = r / np.linalg.norm(r)
+    m = A @ B[:, 0]
+    j = 0  # columns in the QR so far
+    while True:
+        c = np.array(sketch(m), dtype=np.float64, copy=True)
+        for i, v in enumerate(V):
+            c[i:] -= 2.0 * v * (v @ c[i:])
+        v, alpha = _reflector(c[j:])
+        T[:j, j] = c[:j]
+        T[j, j] = alpha
+        z[j:] -= 2.0 * v * (v @ z[j:])
+        V.append(v)
+        j += 1
+        kappa = cond2(T[:j, :j])
+        kappas.append(kappa)
+        if kappa > stab_tol:
+            j -= 1  # keep y_{j-1}: restart from the previous residual
+            stop = "kappa"
+            break
+        y = back_substitute(T[:j, :j], z[:j])
+        rhats.append(np.sqrt(np.sum(z[j:] ** 2)))
+        if rhats[-1] <= tol_rel * gnorm:
+            stop = "tol"
+            break
+        if j == dmax:
+            break
+        lo = max(0, j - k)
+        w, _, nu = _partorth(B[:, lo:j], m, passes)
+        if nu <= breakdown * np.linalg.norm(m):
+            stop = "breakdown"
+            break
+        B[:, j] = w / nu
+        m = A @ B[:, j]
+    if stop == "kappa":
+        y = back_substitute(T[:j, :j], z[:j])
+    x_new = x + B[:, :j] @ y
+    return x_new, dict(j=j, rhat=rhats, kappa=kappas, stop=stop, r0norm=np.linalg.norm(r))
+
+
+def sgmres_iterative(A, f, x0, dmax, k, sketch, tol, maxit=10000, passes=2, stab_tol=1e14, breakdown=1e-13):
+    """Restarted iterative sGMRES: cycles of sgmres_iterative_cycle, each
+    asked for the reduction tol ||f|| / ||r_0|| that would meet the target,
+    until ||f - A x||/||f|| <= tol or maxit cycles.  Returns x, the relres
+    history (after each cycle) and the per-cycle infos."""
+    x = np.array(x0, dtype=np.float64, copy=True)
+    fn = np.linalg.norm(f)
+    hist, infos = [], []
+    rel = np.linalg.norm(f - A @ x) / fn
+    while rel > tol and len(hist) < maxit:
+        x, info = sgmres_iterative_cycle(A, f, x, dmax, k, sketch, tol / rel, passes, stab_tol, breakdown)
+        rel = np.linalg.norm(f - A @ x) / fn
+        hist.append(rel)
+        infos.append(info)
     return x, hist, infos
 
 
