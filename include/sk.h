@@ -170,6 +170,16 @@ typedef struct {
   int barrier_spins;       /* persistent kernel: polls of a grid barrier before it gives up and
                               the call returns SK_ETIMEOUT; 0 = default (2^22, ~0.1 s), -1 = give
                               up at the first poll (exercises the timeout path) */
+  int iter_chunk;          /* sgmres_solve / sgmres_solve_batched: 0 (default) = Algorithm 1 with
+                              all d columns per cycle.  > 0 = iterative sGMRES (§5.2, §5.3): the
+                              basis grows iter_chunk columns at a time, each chunk is sketched
+                              and appended to the QR of S A B, and the cycle ends at the first
+                              prefix j with ||(I - U_j U_j^T) g|| <= (tol ||b|| / ||r_0||) ||g||
+                              (g = S r_0: the reduction that would meet tol), or when the kappa
+                              estimate exceeds stab_tol, the basis breaks down, or j = d; the
+                              solve uses exactly that prefix.  A positive multiple of 16, at most
+                              1024; truncated-Arnoldi basis only (SK_EINVAL otherwise); no CUDA
+                              graph and no persistent kernel; the host reads one flag per chunk */
 } sk_opts;
 
 void sk_opts_default(sk_opts* o);
@@ -177,14 +187,16 @@ void sk_opts_default(sk_opts* o);
 typedef struct {
   int cycles;          /* restart cycles run */
   int matvecs;         /* products with A (basis + residuals) */
-  int d_used;          /* basis columns in the last cycle */
+  int d_used;          /* basis columns in the last cycle (iter_chunk > 0: the prefix its solve used) */
   int width;           /* columns kept by the kappa truncation in the last cycle */
   double relres;       /* final ||b - A x|| / ||b|| (FP64) */
   double rhat_est;     /* last sketched residual estimate (eq. (sgmres-rhat)) */
   double kappa_T_max;  /* largest kappa(T) estimate over cycles */
   float ms[6];         /* device ms summed over cycles (CUDA events on the call's stream):
                           [0] residual r = b - A x, [1] basis, [2] sketches (g = S r, S B),
-                          [3] small dense solve, [4] solution update, [5] whole call */
+                          [3] small dense solve, [4] solution update, [5] whole call.
+                          iter_chunk > 0: [1] is the whole chunk loop (basis, S B, QR, the
+                          per-chunk test), [2] is g = S r and [3] the final solve */
   long long launches;  /* CUDA kernels launched by the call */
 } sk_info;
 

@@ -176,6 +176,7 @@ void sk_opts_default(sk_opts* o) {
   o->basis_kind = SK_BASIS_ARNOLDI;
   o->cheb_c = o->cheb_dx = o->cheb_dy = 0;
   o->barrier_spins = 0;
+  o->iter_chunk = 0;
 }
 
 static sk_op* new_op() {

@@ -506,10 +506,12 @@ sk_status enqueue_cheb_normalize(const BasisParams& p, cudaStream_t st) {
 template <typename T, int KM, int G, bool SM>
 static sk_status enqueue_basis_t(const BasisParams& p, const OpView<typename Compute<T>::type>& A, cudaStream_t st) {
   const int g = p.nblk;
-  // the first pass follows memset/plain nodes: no programmatic edge
-  SK_CUDA(launch_pdl(form_kernel<T, KM, G, SM>, g, st, false, p, A, 0));
-  for (int j = 0; j < p.d; ++j) {
-    SK_CUDA(launch_pdl(dots_kernel<T, KM, G, SM, 1>, g, st, true, p, A, j));
+  // steps [j_begin, j_end) (j_end = 0: all d); the first launch follows
+  // memset/plain nodes or other kernels: no programmatic edge
+  const int jb = p.j_begin, je = p.j_end > 0 ? p.j_end : p.d;
+  if (jb == 0) SK_CUDA(launch_pdl(form_kernel<T, KM, G, SM>, g, st, false, p, A, 0));
+  for (int j = jb; j < je; ++j) {
+    SK_CUDA(launch_pdl(dots_kernel<T, KM, G, SM, 1>, g, st, jb == 0 || j > jb, p, A, j));
     if (p.passes == 2) SK_CUDA(launch_pdl(dots_kernel<T, KM, G, SM, 2>, g, st, true, p, A, j));
     SK_CUDA(launch_pdl(form_kernel<T, KM, G, SM>, g, st, true, p, A, j + 1));
   }

@@ -31,6 +31,9 @@ struct BasisParams {
   double bd;          // breakdown threshold
   int nblk;           // CTAs per pass (set by enqueue_basis)
   int nblk_cap;       // partial-sum rows allocated
+  int j_begin, j_end; // truncated Arnoldi: steps [j_begin, j_end) of this launch
+                      // sequence (j_end = 0: all d); step j forms b_{j+1}.
+                      // j_begin > 0 resumes a build whose steps < j_begin ran
   // Chebyshev basis (kind == SK_BASIS_CHEBYSHEV): B holds the recurrence's
   // vectors v_j (scaled by powers of two, not normalised); sigma[j] =
   // ||v_j||, and Hbar = H_v diag(1/sigma) so that S B Hbar = S A B diag(1/sigma)

@@ -21,13 +21,14 @@ namespace cg = cooperative_groups;
 namespace sk {
 
 // Aug[:, j] = sum_i SB[:, i] Hbar[i, j] over the k+1 nonzeros of column j,
-// for j < du (du = min(stop, d)); zero for du <= j < d.
+// for columns c0 <= j < c1 (0 <= c0 < c1 <= d): the product for j < du
+// (du = min(stop, d)), zero for du <= j.
 __global__ void hbar_product_kernel(const double* __restrict__ SB, const double* __restrict__ Hbar, int s, int d,
-                                    int k, const int* __restrict__ stop, double* __restrict__ Aug) {
+                                    int k, const int* __restrict__ stop, int c0, int c1, double* __restrict__ Aug) {
   const int du = min(*stop, d);
-  const int64_t total = (int64_t)s * d;
+  const int64_t total = (int64_t)s * (c1 - c0);
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
-    const int r = (int)(q % s), j = (int)(q / s);
+    const int r = (int)(q % s), j = c0 + (int)(q / s);
     double a = 0;
     if (j < du) {
       const int i0 = max(0, j - k + 1);
@@ -36,7 +37,7 @@ __global__ void hbar_product_kernel(const double* __restrict__ SB, const double*
         a += SB[(int64_t)i * s + r] * Hbar[(int64_t)j * (d + 1) + i];
       }
     }
-    Aug[q] = a;
+    Aug[(int64_t)j * s + r] = a;
   }
 }
 
@@ -420,41 +421,179 @@ qr_trailing_kernel(double* __restrict__ Aug, int s, int p0, int nbc, int c0, con
   }
 }
 
+// Factor panel [p0, p0+nbc) of Aug in place: the 8-CTA cluster kernel when
+// the panel is tall enough, else one CTA (shared or global memory).
+static sk_status factor_panel(double* Aug, int s, int p0, int nbc, double* rdiag, double* tau, double* T,
+                              cudaStream_t st) {
+  const int per = (s - p0 + kQrCluster - 1) / kQrCluster;
+  if (s - p0 >= 4 * kQrCluster && (size_t)per * kQrNb * sizeof(double) <= (size_t)kDynSmemLimit) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(kQrCluster);
+    cfg.blockDim = dim3(kQrClusterThreads);
+    cfg.dynamicSmemBytes = (size_t)per * kQrNb * sizeof(double);
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = kQrCluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    SK_CUDA(cudaFuncSetAttribute(qr_panel_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kDynSmemLimit));
+    SK_CUDA(cudaLaunchKernelEx(&cfg, qr_panel_cluster_kernel, Aug, s, p0, nbc, rdiag, tau, T));
+    return SK_OK;
+  }
+  const size_t smem = (size_t)(s - p0) * nbc * sizeof(double);
+  if (smem <= 200 * 1024) {
+    SK_CUDA(cudaFuncSetAttribute(qr_panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kDynSmemLimit));
+    qr_panel_kernel<<<1, kQrPanelThreads, smem, st>>>(Aug, s, p0, nbc, rdiag, tau, T);
+  } else {
+    qr_panel_global_kernel<<<1, kQrPanelThreads, 0, st>>>(Aug, s, p0, nbc, rdiag, tau, T);
+  }
+  return SK_OK;
+}
+
 sk_status enqueue_qr(double* Aug, int s, int nq, int ncols, double* rdiag, double* tau, double* Tws,
                      cudaStream_t st) {
   for (int p0 = 0; p0 < nq; p0 += kQrNb) {
     const int nbc = (nq - p0) < kQrNb ? (nq - p0) : kQrNb;
     double* T = Tws + (int64_t)(p0 / kQrNb) * kQrNb * kQrNb;
-    const int per = (s - p0 + kQrCluster - 1) / kQrCluster;
-    if (s - p0 >= 4 * kQrCluster && (size_t)per * kQrNb * sizeof(double) <= (size_t)kDynSmemLimit) {
-      cudaLaunchConfig_t cfg = {};
-      cfg.gridDim = dim3(kQrCluster);
-      cfg.blockDim = dim3(kQrClusterThreads);
-      cfg.dynamicSmemBytes = (size_t)per * kQrNb * sizeof(double);
-      cfg.stream = st;
-      cudaLaunchAttribute attr[1];
-      attr[0].id = cudaLaunchAttributeClusterDimension;
-      attr[0].val.clusterDim.x = kQrCluster;
-      attr[0].val.clusterDim.y = 1;
-      attr[0].val.clusterDim.z = 1;
-      cfg.attrs = attr;
-      cfg.numAttrs = 1;
-      SK_CUDA(cudaFuncSetAttribute(qr_panel_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kDynSmemLimit));
-      SK_CUDA(cudaLaunchKernelEx(&cfg, qr_panel_cluster_kernel, Aug, s, p0, nbc, rdiag, tau, T));
-      const int c0 = p0 + nbc;
-      if (ncols > c0) qr_trailing_kernel<<<ncols - c0, kQrTrailThreads, 0, st>>>(Aug, s, p0, nbc, c0, T);
-      continue;
-    }
-    const size_t smem = (size_t)(s - p0) * nbc * sizeof(double);
-    if (smem <= 200 * 1024) {
-      SK_CUDA(cudaFuncSetAttribute(qr_panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kDynSmemLimit));
-      qr_panel_kernel<<<1, kQrPanelThreads, smem, st>>>(Aug, s, p0, nbc, rdiag, tau, T);
-    } else {
-      qr_panel_global_kernel<<<1, kQrPanelThreads, 0, st>>>(Aug, s, p0, nbc, rdiag, tau, T);
-    }
+    SK_TRY(factor_panel(Aug, s, p0, nbc, rdiag, tau, T, st));
     const int c0 = p0 + nbc;
     if (ncols > c0) qr_trailing_kernel<<<ncols - c0, kQrTrailThreads, 0, st>>>(Aug, s, p0, nbc, c0, T);
   }
+  SK_CUDA(cudaGetLastError());
+  return SK_OK;
+}
+
+// Columns [c0, c1) joined a QR whose columns [0, c0) are factored (c0 a
+// multiple of the panel width) and whose column zc has received those
+// panels' reflectors.  Every earlier panel is applied to the new columns in
+// order (left-looking), then the new panels are factored, each applied to
+// the new columns right of it and to column zc.  Column by column this is
+// the arithmetic of enqueue_qr: the same reflectors, in the same order,
+// through the same per-column trailing kernel.  Returns the launch count
+// through *launches.
+sk_status enqueue_qr_append(double* Aug, int s, int c0, int c1, int zc, double* rdiag, double* tau, double* Tws,
+                            long long* launches, cudaStream_t st) {
+  if (c0 < 0 || c0 % kQrNb != 0 || c1 <= c0 || zc < c1 || s <= c1) {
+    set_error("qr_append: bad column range");
+    return SK_EINVAL;
+  }
+  long long nl = 0;
+  for (int p0 = 0; p0 < c0; p0 += kQrNb) {
+    const double* T = Tws + (int64_t)(p0 / kQrNb) * kQrNb * kQrNb;
+    qr_trailing_kernel<<<c1 - c0, kQrTrailThreads, 0, st>>>(Aug, s, p0, kQrNb, c0, T);
+    ++nl;
+  }
+  for (int p0 = c0; p0 < c1; p0 += kQrNb) {
+    const int nbc = (c1 - p0) < kQrNb ? (c1 - p0) : kQrNb;
+    double* T = Tws + (int64_t)(p0 / kQrNb) * kQrNb * kQrNb;
+    SK_TRY(factor_panel(Aug, s, p0, nbc, rdiag, tau, T, st));
+    const int cn = p0 + nbc;
+    if (c1 > cn) {
+      qr_trailing_kernel<<<c1 - cn, kQrTrailThreads, 0, st>>>(Aug, s, p0, nbc, cn, T);
+      ++nl;
+    }
+    qr_trailing_kernel<<<1, kQrTrailThreads, 0, st>>>(Aug, s, p0, nbc, zc, T);
+    nl += 2;
+  }
+  SK_CUDA(cudaGetLastError());
+  if (launches) *launches += nl;
+  return SK_OK;
+}
+
+// Early stop of the iterative cycle (§5.2 eq. (sgmres-iterative-soln)), run
+// after the QR covers columns [0, c1) and z = Q^T g.  For every prefix j in
+// (c0, c1] the estimate is rhat_j^2 = sum_{i >= j} z_i^2 (the reflectors past
+// j leave that tail's norm unchanged).  out[0] = the first j with
+// rhat_j <= tau ||z|| (||z|| = ||g||), or 0; out[1] = 1 when the kappa
+// estimate of the solve (max/min |r_jj| over [0, c1)) exceeds stab_tol or a
+// diagonal entry is zero or not finite (§5.3), or when the basis broke down
+// before column c1 (stop <= c1).  One CTA of kCheckThreads threads; the chunk
+// c1 - c0 is at most kCheckThreads.
+static constexpr int kCheckThreads = 1024;
+
+__global__ void __launch_bounds__(kCheckThreads)
+prefix_check_kernel(const double* __restrict__ z, const double* __restrict__ rdiag, const int* __restrict__ stop,
+                    int s, int c0, int c1, double tau, double stab_tol, int* __restrict__ out) {
+  __shared__ double red[kCheckThreads / 32][2];
+  __shared__ double wsum[kCheckThreads / 32];
+  __shared__ long long wmx[kCheckThreads / 32], wmn[kCheckThreads / 32];
+  __shared__ int s_first;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const long long kAbs = 0x7fffffffffffffffLL;
+  const long long kInf = 0x7ff0000000000000LL;
+  if (threadIdx.x == 0) s_first = 0x7fffffff;
+  // ||z||^2 and the tail past the chunk, sum_{i >= c1} z_i^2
+  double all = 0, tail = 0;
+  for (int i = threadIdx.x; i < s; i += blockDim.x) {
+    const double q = z[i] * z[i];
+    all += q;
+    if (i >= c1) tail += q;
+  }
+  // max / min |r_jj| over [0, c1) on the IEEE bit patterns
+  long long mx = 0, mn = kInf;
+  for (int j = threadIdx.x; j < c1; j += blockDim.x) {
+    const long long b = __double_as_longlong(rdiag[j]) & kAbs;
+    mx = max(mx, b);
+    mn = min(mn, b);
+  }
+  all = warp_sum(all);
+  tail = warp_sum(tail);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+  }
+  // inclusive suffix sums of v_t = z_{c0+t}^2 within the chunk, t < m
+  const int m = c1 - c0;
+  const int t = threadIdx.x;
+  double v = (t < m) ? z[c0 + t] * z[c0 + t] : 0.0;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const double u = __shfl_down_sync(0xffffffffu, v, o);
+    if (lane + o < 32) v += u;
+  }
+  if (lane == 0) {
+    red[wid][0] = all;
+    red[wid][1] = tail;
+    wsum[wid] = v;  // lane 0 holds its warp's total
+    wmx[wid] = mx;
+    wmn[wid] = mn;
+  }
+  __syncthreads();
+  double tot = 0, tl = 0, later = 0;
+  long long gmx = 0, gmn = kInf;
+  for (int w = 0; w < nw; ++w) {
+    tot += red[w][0];
+    tl += red[w][1];
+    if (w > wid) later += wsum[w];
+    gmx = max(gmx, wmx[w]);
+    gmn = min(gmn, wmn[w]);
+  }
+  // thread t in [1, m) tests prefix j = c0 + t: rhat_j^2 = sum_{u >= t} v_u
+  // + tail; thread 0 tests j = c1 (the tail alone)
+  if (t < m) {
+    const double r2 = (t == 0 ? 0.0 : v + later) + tl;
+    if (r2 <= tau * tau * tot) atomicMin(&s_first, t == 0 ? c1 : c0 + t);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const double dmx = __longlong_as_double(gmx), dmn = __longlong_as_double(gmn);
+    const bool bad = gmn == 0 || gmx >= kInf || dmx > stab_tol * dmn || *stop <= c1;
+    out[0] = (s_first == 0x7fffffff) ? 0 : s_first;
+    out[1] = bad ? 1 : 0;
+  }
+}
+
+sk_status enqueue_prefix_check(const double* z, const double* rdiag, const int* stop, int s, int c0, int c1,
+                               double tau, double stab_tol, int* out, cudaStream_t st) {
+  if (c0 < 0 || c1 <= c0 || c1 - c0 > kCheckThreads || c1 > s) {
+    set_error("prefix_check: bad column range");
+    return SK_EINVAL;
+  }
+  prefix_check_kernel<<<1, kCheckThreads, 0, st>>>(z, rdiag, stop, s, c0, c1, tau, stab_tol, out);
   SK_CUDA(cudaGetLastError());
   return SK_OK;
 }
@@ -493,8 +632,8 @@ __device__ __forceinline__ long long warp_scan_min(long long v) {
 }
 
 __global__ void __launch_bounds__(kLsThreads)
-ls_solve_kernel(const double* __restrict__ Aug, const double* __restrict__ rdiag, int s, int d, double stab_tol,
-                double* __restrict__ y, double* __restrict__ diag) {
+ls_solve_kernel(const double* __restrict__ Aug, const double* __restrict__ rdiag, const double* __restrict__ z,
+                int s, int d, double stab_tol, double* __restrict__ y, double* __restrict__ diag) {
   extern __shared__ double zz[];  // d right-hand side entries, then the 32 x d block of R
   double* Rb = zz + d;             // Rb[c * d + t] = R[t, i0 + c]
   __shared__ long long wmax[kLsThreads / 32], wmin[kLsThreads / 32];
@@ -502,7 +641,6 @@ ls_solve_kernel(const double* __restrict__ Aug, const double* __restrict__ rdiag
   __shared__ int s_width;
   __shared__ double sh[32];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const double* z = Aug + (int64_t)d * s;
   const long long kAbs = 0x7fffffffffffffffLL;
   const long long kInf = 0x7ff0000000000000LL;
   if (threadIdx.x == 0) {
@@ -618,19 +756,30 @@ ls_solve_kernel(const double* __restrict__ Aug, const double* __restrict__ rdiag
 
 sk_status enqueue_ls_solve(const double* Aug, const double* rdiag, int s, int d, double stab_tol, double* y,
                            double* diag, cudaStream_t st) {
+  return enqueue_ls_solve_z(Aug, rdiag, Aug + (size_t)d * s, s, d, stab_tol, y, diag, st);
+}
+
+sk_status enqueue_ls_solve_z(const double* Aug, const double* rdiag, const double* z, int s, int d, double stab_tol,
+                             double* y, double* diag, cudaStream_t st) {
   const size_t smem = (size_t)d * 33 * sizeof(double);
-  if (smem > (size_t)kDynSmemLimit) { set_error("ls_solve: d too large"); return SK_EINVAL; }
+  if (d < 1 || smem > (size_t)kDynSmemLimit) { set_error("ls_solve: d out of range"); return SK_EINVAL; }
   SK_CUDA(cudaFuncSetAttribute(ls_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kDynSmemLimit));
-  ls_solve_kernel<<<1, kLsThreads, smem, st>>>(Aug, rdiag, s, d, stab_tol, y, diag);
+  ls_solve_kernel<<<1, kLsThreads, smem, st>>>(Aug, rdiag, z, s, d, stab_tol, y, diag);
   SK_CUDA(cudaGetLastError());
   return SK_OK;
 }
 
 sk_status enqueue_hbar_product(const double* SB, const double* Hbar, int s, int d, int k, const int* stop,
                                double* Aug, cudaStream_t st) {
-  int blocks = (int)(((int64_t)s * d + 255) / 256);
+  return enqueue_hbar_product_cols(SB, Hbar, s, d, k, stop, 0, d, Aug, st);
+}
+
+sk_status enqueue_hbar_product_cols(const double* SB, const double* Hbar, int s, int d, int k, const int* stop,
+                                    int c0, int c1, double* Aug, cudaStream_t st) {
+  if (c0 < 0 || c1 > d || c0 >= c1) { set_error("hbar_product: bad column range"); return SK_EINVAL; }
+  int blocks = (int)(((int64_t)s * (c1 - c0) + 255) / 256);
   if (blocks > 4 * num_sms()) blocks = 4 * num_sms();
-  hbar_product_kernel<<<blocks, 256, 0, st>>>(SB, Hbar, s, d, k, stop, Aug);
+  hbar_product_kernel<<<blocks, 256, 0, st>>>(SB, Hbar, s, d, k, stop, c0, c1, Aug);
   SK_CUDA(cudaGetLastError());
   return SK_OK;
 }

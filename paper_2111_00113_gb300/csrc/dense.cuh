@@ -15,6 +15,17 @@ sk_status enqueue_qr(double* Aug, int s, int nq, int ncols, double* rdiag, doubl
                      cudaStream_t st);
 sk_status enqueue_ls_solve(const double* Aug, const double* rdiag, int s, int d, double stab_tol, double* y,
                            double* diag, cudaStream_t st);
+// Iterative sGMRES (§5.2): the product on columns [c0, c1) only; the solve
+// with Q^T g read from z (d = the prefix solved); the QR grown by columns
+// [c0, c1) with column zc holding Q^T g; the early-stop test of a chunk.
+sk_status enqueue_hbar_product_cols(const double* SB, const double* Hbar, int s, int d, int k, const int* stop,
+                                    int c0, int c1, double* Aug, cudaStream_t st);
+sk_status enqueue_ls_solve_z(const double* Aug, const double* rdiag, const double* z, int s, int d, double stab_tol,
+                             double* y, double* diag, cudaStream_t st);
+sk_status enqueue_qr_append(double* Aug, int s, int c0, int c1, int zc, double* rdiag, double* tau, double* Tws,
+                            long long* launches, cudaStream_t st);
+sk_status enqueue_prefix_check(const double* z, const double* rdiag, const int* stop, int s, int c0, int c1,
+                               double tau, double stab_tol, int* out, cudaStream_t st);
 
 // Eigenpairs of a d x d FP64 matrix (eig.cu).  M is overwritten by its
 // Hessenberg form and reflectors; tau needs 2d entries.  Yre/Yim (d x nev)

@@ -489,6 +489,80 @@ static sk_status enqueue_cycle(SolveState& S, const sk_op* A, const OpView<doubl
   return SK_OK;
 }
 
+// One cycle of iterative sGMRES (§5.2; restart on kappa, §5.3).  The basis
+// grows o.iter_chunk columns at a time; after each chunk its new columns are
+// sketched, S A B's QR grows by them (enqueue_qr_append: the reflectors of
+// enqueue_qr, applied left-looking) and prefix_check finds the first prefix
+// j whose estimate ||z[j:]|| (z = Q^T g) meets tau_rel ||g||.  The host reads
+// that one answer per chunk; the cycle ends there, or on the kappa estimate,
+// a breakdown or j = d, and the solve and the update use that prefix.
+// *used = the prefix solved, *built = the steps the basis ran.
+static sk_status run_iterative_cycle(SolveState& S, const sk_op* A, const OpView<double>& Av, const double* b,
+                                     double* x, double tau_rel, int* chk, cudaStream_t st, cudaEvent_t* ev,
+                                     int* used, int* built, long long* launches) {
+  const int d = S.d, s = S.s, chunk = S.o.iter_chunk;
+  const size_t esz = dtype_size(S.o.basis);
+  BasisParams& bp = S.bb.bp;
+  long long nl = 0;
+  SK_TRY(mark(ev, EV_START, st, false));
+  SK_TRY(S.sketch.apply(S.r, S.n, 1, SK_F64, S.g, S.ws_r, st));
+  nl += 2;
+  SK_TRY(mark(ev, EV_G, st, false));
+  init_stop_kernel<<<1, 1, 0, st>>>(bp.stop, d + 1, bp.nanflag);
+  ++nl;
+  SK_CUDA(cudaMemsetAsync(bp.Hbar, 0, sizeof(double) * (size_t)(d + 1) * d, st));
+  double* z = S.Aug + (size_t)d * s;
+  SK_CUDA(cudaMemcpyAsync(z, S.g, sizeof(double) * s, cudaMemcpyDeviceToDevice, st));
+  int dp = d, c1 = 0;
+  for (int c0 = 0; c0 < d; c0 = c1) {
+    c1 = c0 + chunk < d ? c0 + chunk : d;
+    bp.j_begin = c0;
+    bp.j_end = c1;
+    const sk_status bs = enqueue_basis(bp, A, st);
+    bp.j_begin = bp.j_end = 0;
+    SK_TRY(bs);
+    nl += (long long)(c1 - c0) * (S.o.cgs_passes + 1) + (c0 == 0 ? 1 : 0);
+    // the chunk's new basis columns: b_{c0+1} .. b_{c1} (0-based), and b_0 first
+    const int s0 = c0 == 0 ? 0 : c0 + 1;
+    SK_TRY(S.sketch.apply((const unsigned char*)bp.B + (size_t)s0 * bp.ldb * esz, bp.ldb, c1 + 1 - s0, S.o.basis,
+                          S.SB + (size_t)s0 * s, S.ws_B, st));
+    nl += 2;
+    SK_TRY(enqueue_hbar_product_cols(S.SB, bp.Hbar, s, d, S.bb.hbar_k(), bp.stop, c0, c1, S.Aug, st));
+    ++nl;
+    SK_TRY(enqueue_qr_append(S.Aug, s, c0, c1, d, S.rdiag, S.tau, S.Tws, &nl, st));
+    SK_TRY(enqueue_prefix_check(z, S.rdiag, bp.stop, s, c0, c1, tau_rel, S.o.stab_tol, chk, st));
+    ++nl;
+    int h[2] = {0, 0};
+    SK_CUDA(cudaMemcpyAsync(h, chk, sizeof(h), cudaMemcpyDeviceToHost, st));
+    SK_CUDA(cudaStreamSynchronize(st));
+    if (h[0] > 0) {
+      dp = h[0];
+      break;
+    }
+    if (h[1] || c1 == d) {
+      dp = c1;
+      break;
+    }
+  }
+  SK_TRY(mark(ev, EV_BASIS, st, false));
+  SK_TRY(mark(ev, EV_SB, st, false));
+  SK_TRY(enqueue_ls_solve_z(S.Aug, S.rdiag, z, s, dp, S.o.stab_tol, S.y, S.out + 1, st));
+  ++nl;
+  SK_TRY(mark(ev, EV_SMALL, st, false));
+  SK_TRY(enqueue_update(x, bp.B, bp.ldb, S.n, dp, S.o.basis, S.y, S.out + 1, st));
+  ++nl;
+  SK_TRY(mark(ev, EV_UPDATE, st, false));
+  SK_TRY(enqueue_residual(S, Av, b, x, st));
+  ++nl;
+  SK_CUDA(cudaMemcpyAsync(S.out, bp.rho2, sizeof(double), cudaMemcpyDeviceToDevice, st));
+  SK_TRY(mark(ev, EV_RES, st, false));
+  SK_CUDA(cudaMemcpyAsync(S.h_out, S.out, 4 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  *used = dp;
+  *built = c1;
+  *launches += nl;
+  return SK_OK;
+}
+
 static long long count_kernel_nodes(cudaGraph_t g) {
   size_t nn = 0;
   if (cudaGraphGetNodes(g, nullptr, &nn) != cudaSuccess) return -1;
@@ -515,6 +589,14 @@ static sk_status sgmres_impl(const sk_op* A, const double* b, double* x, int d, 
   resolve_opts(opts, &S.o, d);
   SK_CHECK_ARG(S.o.basis == SK_F64 || S.o.basis == SK_F32 || S.o.basis == SK_BF16, "basis dtype");
   SK_TRY(check_passes(S.o));
+  const bool iter = S.o.iter_chunk != 0;
+  if (iter) {
+    SK_CHECK_ARG(S.o.iter_chunk > 0 && S.o.iter_chunk % kQrNb == 0 && S.o.iter_chunk <= 1024,
+                 "iter_chunk must be a positive multiple of 16, at most 1024");
+    SK_CHECK_ARG(S.o.basis_kind == SK_BASIS_ARNOLDI, "iter_chunk needs the truncated-Arnoldi basis");
+    S.o.use_graph = 0;
+    S.o.persistent = 0;
+  }
   S.n = A->n;
   S.d = d;
   S.k = k;
@@ -540,7 +622,18 @@ static sk_status sgmres_impl(const sk_op* A, const double* b, double* x, int d, 
   SK_TRY(sc.alloc(&S.Tws, (size_t)((d + kQrNb - 1) / kQrNb) * kQrNb * kQrNb));
   SK_TRY(sc.alloc(&S.y, d));
   SK_TRY(sc.alloc(&S.ws_r, S.sketch.ws(1, SK_F64)));
-  SK_TRY(sc.alloc(&S.ws_B, S.sketch.ws(d + 1, S.o.basis)));
+  {
+    // iterative cycles sketch 1..iter_chunk+1 columns at a time: room for
+    // the largest of those shapes too
+    size_t wsb = S.sketch.ws(d + 1, S.o.basis);
+    for (int c = 1; iter && c <= S.o.iter_chunk + 1 && c <= d + 1; ++c) {
+      const size_t w = S.sketch.ws(c, S.o.basis);
+      if (w > wsb) wsb = w;
+    }
+    SK_TRY(sc.alloc(&S.ws_B, wsb));
+  }
+  int* chk = nullptr;
+  if (iter) SK_TRY(sc.alloc(&chk, 2));
   SK_TRY(sc.alloc(&S.vec_part, vec_grid(S.n)));
   SK_TRY(sc.alloc(&S.vec_cnt, 2));
   SK_CUDA(cudaMemsetAsync(S.vec_cnt, 0, 2 * sizeof(unsigned), st));
@@ -601,7 +694,11 @@ static sk_status sgmres_impl(const sk_op* A, const double* b, double* x, int d, 
   for (int q = 0; q < EV_COUNT; ++q) SK_CUDA(cudaEventCreate(&ev[q]));
   struct EvsFree { cudaEvent_t* e; ~EvsFree() { for (int q = 0; q < EV_COUNT; ++q) cudaEventDestroy(e[q]); } } evf{ev};
   long long kernels_per_cycle = 0;
-  if (S.o.use_graph) {
+  long long iter_launches = 0;
+  long long iter_matvecs = 0;
+  if (iter) {
+    // launches are counted per cycle by run_iterative_cycle
+  } else if (S.o.use_graph) {
     // the legacy default stream cannot be captured: use a private stream then
     if (st == nullptr || st == cudaStreamLegacy) {
       SK_CUDA(cudaStreamCreateWithFlags(&own, cudaStreamNonBlocking));
@@ -632,8 +729,13 @@ static sk_status sgmres_impl(const sk_op* A, const double* b, double* x, int d, 
   double kmax = 0, rhat = 0;
   int width = 0;
   float phase[5] = {0, 0, 0, 0, 0};
+  int iter_used = 0;
   while (cycles < S.o.maxit) {
-    if (gexec) SK_CUDA(cudaGraphLaunch(gexec, cap));
+    if (iter) {
+      int built = 0;
+      SK_TRY(run_iterative_cycle(S, A, Av, b, x, tol / relres, chk, cap, ev, &iter_used, &built, &iter_launches));
+      iter_matvecs += built + 1;
+    } else if (gexec) SK_CUDA(cudaGraphLaunch(gexec, cap));
     else SK_TRY(enqueue_cycle(S, A, Av, b, x, cap, ev, false));
     SK_CUDA(cudaStreamSynchronize(cap));
     ++cycles;
@@ -665,15 +767,15 @@ static sk_status sgmres_impl(const sk_op* A, const double* b, double* x, int d, 
     int stop = 0;
     cudaMemcpy(&stop, S.bb.bp.stop, sizeof(int), cudaMemcpyDeviceToHost);
     info->cycles = cycles;
-    info->matvecs = cycles * (d + 1) + 1;
-    info->d_used = stop < d ? stop : d;
+    info->matvecs = iter ? (int)iter_matvecs + 1 : cycles * (d + 1) + 1;
+    info->d_used = iter ? iter_used : (stop < d ? stop : d);
     info->width = width;
     info->relres = relres;
     info->rhat_est = rhat;
     info->kappa_T_max = kmax;
     for (int q = 0; q < 5; ++q) info->ms[q] = phase[q];
     info->ms[5] = ms;
-    info->launches = pre_launches + kernels_per_cycle * cycles;
+    info->launches = pre_launches + (iter ? iter_launches : kernels_per_cycle * cycles);
   }
   if (result == SK_ENOCONV) set_error("no convergence to tol=%g in %d cycles (relres %g)", tol, cycles, relres);
   return result;

@@ -80,6 +80,15 @@ def test_invalid_arguments_rejected_on_host(native):
     assert lib.sgmres_solve(h, dummy, dummy, 10, 2, 40, 1e-6, C.byref(o2), C.byref(info), None) == native.SK_EINVAL
     o3 = native.SkOpts()
     lib.sk_opts_default(C.byref(o3))
-    assert o3.basis_kind == 0 and o3.barrier_spins == 0 and o3.persistent == 0
+    assert o3.basis_kind == 0 and o3.barrier_spins == 0 and o3.persistent == 0 and o3.iter_chunk == 0
+    # iterative sGMRES: the chunk is a positive multiple of the QR panel
+    # width (16), at most 1024, with the truncated-Arnoldi basis only
+    for bad_chunk in (8, -16, 2048):
+        o3.iter_chunk = bad_chunk
+        assert lib.sgmres_solve(h, dummy, dummy, 10, 2, 40, 1e-6, C.byref(o3), C.byref(info), None) == native.SK_EINVAL
+        assert b"iter_chunk" in lib.sk_last_error()
+    o3.iter_chunk, o3.basis_kind, o3.cheb_c, o3.cheb_dx = 16, 1, 4.0, 4.0
+    assert lib.sgmres_solve(h, dummy, dummy, 10, 2, 40, 1e-6, C.byref(o3), C.byref(info), None) == native.SK_EINVAL
+    assert b"truncated-Arnoldi" in lib.sk_last_error()
     lib.sk_op_destroy(hT)
     lib.sk_op_destroy(h)
