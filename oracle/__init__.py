@@ -22,7 +22,8 @@ Modules
             sGMRES (Algorithm 1) with restarting (§3.5), iterative sGMRES
             with early stopping (§5.2, §5.3), Householder-Arnoldi GMRES
             (§4.2), the Chebyshev basis (§4.3)
-  eigs      sketched Rayleigh-Ritz (Algorithm 2), Rayleigh-Ritz (§6.1)
+  eigs      sketched Rayleigh-Ritz (Algorithm 2), stabilized sRR (§6.5),
+            Rayleigh-Ritz (§6.1)
   adjoint   dense adjoint gradient of ||x(theta)-x_t||^2
 
 Every function is pinned by a ``-m "not gpu"`` test against something other

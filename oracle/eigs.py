@@ -1,8 +1,10 @@
-"""Sketched Rayleigh-Ritz (Algorithm 2) and Rayleigh-Ritz (§6.1).
+"""Sketched Rayleigh-Ritz (Algorithm 2), its stabilized form (§6.5) and
+Rayleigh-Ritz (§6.1).
 
 Test infrastructure only (see oracle/__init__.py).
 """
 import numpy as np
+import scipy.linalg
 
 from . import krylov
 
@@ -47,6 +49,47 @@ def srr(A, w1, d, k, sketch, nev, tau=1e-8, symmetric=False, passes=2, breakdown
     X /= np.linalg.norm(X, axis=0)
     return dict(lam=lam[order], X=X, rhat=rhat[order], nconv=int(np.sum(rhat[order] <= tau)),
                 kappa=kappa, Mhat=Mhat, B=B, M=M, C=C, D=D, d_used=d_used, all_lam=lam)
+
+
+def srr_stabilized_from_basis(B, M, sketch, nev, trunc_tol=1e14, tau=1e-8, symmetric=False):
+    """Stabilized sRR (§6.5, eq. (qz)) on a given basis B and M = A B.
+
+    C = S B, D = S A B; thin SVD C = U Sigma V^T (LAPACK gesdd as one
+    step), truncated to the r singular values with sigma_1 / sigma_i <=
+    trunc_tol (the kept part has condition number at most trunc_tol); the
+    generalized eigenproblem (U_r^T D V_r) z = theta Sigma_r z by QZ (LAPACK
+    ggev through scipy.linalg.eig with two matrices, as one step); Ritz
+    vectors y = V_r z in the coordinates of B; residual estimates
+    ||D y - theta C y|| / ||C y|| (eq. (srr-resid-est)); the nev values of
+    largest real part; x = B y / ||B y||.  For real symmetric A (§6.8) the
+    real parts are kept.
+    """
+    C = sketch(B)
+    D = sketch(M)
+    U, sg, Vt = np.linalg.svd(C, full_matrices=False)
+    r = int(np.sum(sg >= sg[0] / trunc_tol)) if sg[0] > 0 else 0
+    if r == 0:
+        raise ValueError("the sketched basis is zero")
+    G = U[:, :r].T @ D @ Vt[:r].T
+    theta, Z = scipy.linalg.eig(G, np.diag(sg[:r]))
+    Y = Vt[:r].T @ Z
+    if symmetric:
+        theta = theta.real.astype(np.complex128)
+        Y = Y.real.astype(np.complex128)
+    rhat = np.array([np.linalg.norm(D @ Y[:, i] - theta[i] * (C @ Y[:, i])) / np.linalg.norm(C @ Y[:, i])
+                     for i in range(r)])
+    order = select_order(theta, nev)
+    X = B @ Y[:, order]
+    X /= np.linalg.norm(X, axis=0)
+    return dict(lam=theta[order], X=X, rhat=rhat[order], nconv=int(np.sum(rhat[order] <= tau)), rank=r,
+                sigma=sg, all_lam=theta)
+
+
+def srr_stabilized(A, w1, d, k, sketch, nev, trunc_tol=1e14, tau=1e-8, symmetric=False, passes=2,
+                   breakdown=1e-13):
+    """Stabilized sRR on the truncated Arnoldi basis of Algorithm 2."""
+    B, M, _, _ = krylov.trunc_arnoldi(A, w1, d, k, passes=passes, breakdown=breakdown)
+    return srr_stabilized_from_basis(B, M, sketch, nev, trunc_tol, tau, symmetric)
 
 
 def rr_matrix(B, M):

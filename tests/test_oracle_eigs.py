@@ -89,3 +89,94 @@ def test_selection_order_and_normalisation():
     for i in range(4):
         r = eigs.eig_residual(A, out["lam"][i], out["X"][:, i])
         assert r < 1e-2
+
+
+# ---------------------------------------------------------------------------
+# Stabilized sRR (§6.5, eq. (qz))
+# ---------------------------------------------------------------------------
+def _monomial_basis(A, w, d):
+    # b_j = A^{j-1} w, each column scaled to unit norm: the badly conditioned
+    # basis that §6.5 is about (kappa grows geometrically with d)
+    B = np.zeros((w.shape[0], d))
+    v = w / np.linalg.norm(w)
+    for j in range(d):
+        B[:, j] = v
+        v = A @ v
+        v = v / np.linalg.norm(v)
+    return B
+
+
+def _plain_srr_from_basis(B, M, sk, nev):
+    # Algorithm 2's reduction M-hat = T^{-1} U^T (S A B) on the same basis
+    C, D = sk(B), sk(M)
+    V, T = krylov.householder_qr(C)
+    d = B.shape[1]
+    UtD = np.stack([krylov.apply_qt(V, D[:, j])[:d] for j in range(d)], axis=1)
+    lam = np.linalg.eigvals(np.linalg.solve(T, UtD))
+    return lam[eigs.select_order(lam, nev)], krylov.cond2(T)
+
+
+@pytest.mark.parametrize("seed", [1, 3])
+def test_stabilized_recovers_spectrum_past_unit_roundoff(seed):
+    # diagonal A with six separated top eigenvalues above a bulk in [0, 1];
+    # monomial bases of depth 40..80 with kappa_2(T) ~ 1e17 (beyond 1/u).
+    # The stabilized form finds the top six to 5e-4 or better (measured:
+    # 8e-5 at worst over three start vectors and two sketches), where
+    # Algorithm 2's reduction on the same basis is off by 0.1 or more in the
+    # real parts (measured 0.3 to 2.2).  At d = 20 (kappa ~ 1e16) both work.
+    n = 2000
+    top = np.array([3.0, 2.6, 2.2, 2.0, 1.7, 1.5])
+    lam = np.concatenate([top, np.linspace(1.0, 0.0, n - 6)])
+    A = np.diag(lam)
+    w = synth.randn(seed, n)
+    for d in (40, 60, 80):
+        B = _monomial_basis(A, w, d)
+        M = A @ B
+        sk = lambda X: sketch.sparse_sign_apply(5, 4 * d, hashing.default_zeta(d), X)
+        out = eigs.srr_stabilized_from_basis(B, M, sk, 6, trunc_tol=1e13, symmetric=True)
+        err = np.abs(out["lam"].real - top).max()
+        assert err <= 5e-4, (d, err)
+        assert out["rank"] < d and out["sigma"][0] / out["sigma"][out["rank"] - 1] <= 1e13
+        lp, kp = _plain_srr_from_basis(B, M, sk, 6)
+        assert kp > 1e16 and np.abs(lp.real - top).max() > 0.1
+
+
+def test_stabilized_equals_algorithm_2_on_a_good_basis():
+    # no truncation (rank = d): (U^T S A B) V z = theta Sigma z is M-hat's
+    # eigenproblem in other coordinates (y = V z), so the Ritz values agree.
+    # Full orthogonalisation (k = d) keeps kappa_2(S B) near 1.
+    N = 16
+    A = operators.stencil5_matrix(N, N, synth.conv_diff_coef(N, 20.0))
+    w1 = synth.randn(4, N * N)
+    d = 30
+    sk = _sk(d, seed=9)
+    a = eigs.srr(A, w1, d, d, sk, nev=8)
+    b = eigs.srr_stabilized(A, w1, d, d, sk, nev=8, trunc_tol=np.inf)
+    assert b["rank"] == d and b["sigma"][0] / b["sigma"][-1] < 10 and a["kappa"] < 10
+    la, lb = a["all_lam"], b["all_lam"]
+    assert la.shape == lb.shape
+    # every Ritz value of one has a partner in the other (both ways)
+    assert np.abs(la[:, None] - lb[None, :]).min(axis=1).max() <= 1e-9
+    assert np.abs(lb[:, None] - la[None, :]).min(axis=1).max() <= 1e-9
+    # the selected values as a set (a conjugate pair's real parts tie up to
+    # rounding, so its order within the selection is not fixed)
+    sa, sb = a["lam"], b["lam"]
+    assert np.abs(sa[:, None] - sb[None, :]).min(axis=1).max() <= 1e-9
+    ia = np.argsort(np.round(sa.real, 6) + 1e-3 * np.round(sa.imag, 6))
+    ib = np.argsort(np.round(sb.real, 6) + 1e-3 * np.round(sb.imag, 6))
+    assert np.allclose(a["rhat"][ia], b["rhat"][ib], rtol=1e-6, atol=1e-12)
+
+
+def test_stabilized_diagonal_and_laplacian_closed_forms():
+    # exact spectra at d = n (diagonal, §8.3.4 shape) and the 1-D Laplacian's
+    # 2 - 2 cos(j pi / (n+1))
+    n = 64
+    lam = np.concatenate([np.linspace(-1, -0.1, 10), np.linspace(0, 1, n - 10)])
+    out = eigs.srr_stabilized(np.diag(lam), synth.randn(1, n), n, n, _sk(n), nev=n, symmetric=True)
+    assert np.allclose(np.sort(out["lam"].real), np.sort(lam), atol=1e-8)
+    L = np.diag(2 * np.ones(n)) - np.diag(np.ones(n - 1), 1) - np.diag(np.ones(n - 1), -1)
+    exact = np.sort(2 - 2 * np.cos(np.arange(1, n + 1) * np.pi / (n + 1)))[::-1]
+    out = eigs.srr_stabilized(L, synth.randn(2, n), n, n, _sk(n), nev=10, symmetric=True)
+    assert np.allclose(out["lam"].real, exact[:10], atol=1e-8)
+    # the residual estimate is small for converged pairs and the vectors are unit
+    assert np.all(out["rhat"] <= 1e-8) and np.allclose(np.linalg.norm(out["X"], axis=0), 1)
