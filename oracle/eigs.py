@@ -19,36 +19,45 @@ def select_order(lam, nev):
     return idx[:nev]
 
 
-def srr(A, w1, d, k, sketch, nev, tau=1e-8, symmetric=False, passes=2, breakdown=1e-13):
-    """Algorithm 2 with the basis of §1.2.2 eq. (partorth).
+def srr_from_basis(B, M, sketch, nev, tau=1e-8, symmetric=False):
+    """Algorithm 2's reduction on a given basis B (n x d) and M = A B.
 
-    b_1 = w_1/||w_1||; truncated Arnoldi basis B and AB; C = S B, D = S AB
-    (§6.4); C = U T; M-hat = T^{-1}(U^T D) (eq. (Mhat-form)); eig(M-hat)
-    (numpy's LAPACK dgeev as one step); residual estimates
-    ||D y_i - lam_i C y_i|| / ||C y_i|| (eq. (srr-resid-est)); the nev
-    eigenvalues of largest real part; x_i = B y_i / ||B y_i||.
-    For real symmetric A (§6.8) the real parts of lam and x are kept.
+    C = S B, D = S A B (§6.4); C = U T (Householder); M-hat = T^{-1}(U^T D)
+    (eq. (Mhat-form)); eig(M-hat) (numpy's LAPACK dgeev as one step);
+    residual estimates ||D y_i - lam_i C y_i|| / ||C y_i|| (eq.
+    (srr-resid-est)); the nev eigenvalues of largest real part;
+    x_i = B y_i / ||B y_i||.  For real symmetric A (§6.8) the real parts of
+    lam and x are kept.
     """
-    B, M, _, d_used = krylov.trunc_arnoldi(A, w1, d, k, passes=passes, breakdown=breakdown)
+    d = B.shape[1]
     C = sketch(B)
     D = sketch(M)
     V, T = krylov.householder_qr(C)
     kappa = krylov.cond2(T)
-    UtD = np.stack([krylov.apply_qt(V, D[:, j])[:d_used] for j in range(d_used)], axis=1)
-    Mhat = np.zeros((d_used, d_used))
-    for j in range(d_used):
+    UtD = np.stack([krylov.apply_qt(V, D[:, j])[:d] for j in range(d)], axis=1)
+    Mhat = np.zeros((d, d))
+    for j in range(d):
         Mhat[:, j] = krylov.back_substitute(T, UtD[:, j])
     lam, Y = np.linalg.eig(Mhat)
     if symmetric:
         lam = lam.real.astype(np.complex128)
         Y = Y.real.astype(np.complex128)
     rhat = np.array([np.linalg.norm(D @ Y[:, i] - lam[i] * (C @ Y[:, i])) / np.linalg.norm(C @ Y[:, i])
-                     for i in range(d_used)])
+                     for i in range(d)])
     order = select_order(lam, nev)
     X = B @ Y[:, order]
     X /= np.linalg.norm(X, axis=0)
     return dict(lam=lam[order], X=X, rhat=rhat[order], nconv=int(np.sum(rhat[order] <= tau)),
-                kappa=kappa, Mhat=Mhat, B=B, M=M, C=C, D=D, d_used=d_used, all_lam=lam)
+                kappa=kappa, Mhat=Mhat, C=C, D=D, all_lam=lam)
+
+
+def srr(A, w1, d, k, sketch, nev, tau=1e-8, symmetric=False, passes=2, breakdown=1e-13):
+    """Algorithm 2 with the basis of §1.2.2 eq. (partorth): b_1 = w_1/||w_1||,
+    the truncated Arnoldi basis B and AB, then srr_from_basis."""
+    B, M, _, d_used = krylov.trunc_arnoldi(A, w1, d, k, passes=passes, breakdown=breakdown)
+    out = srr_from_basis(B, M, sketch, nev, tau, symmetric)
+    out.update(B=B, M=M, d_used=d_used)
+    return out
 
 
 def srr_stabilized_from_basis(B, M, sketch, nev, trunc_tol=1e14, tau=1e-8, symmetric=False):

@@ -1,5 +1,5 @@
-"""k-truncated Arnoldi, Chebyshev basis, Householder QR, sGMRES (Algorithm 1,
-restarted and iterative) and GMRES.
+"""k-truncated Arnoldi, Chebyshev and block Chebyshev bases, Householder QR,
+sGMRES (Algorithm 1, restarted and iterative) and GMRES.
 
 Test infrastructure only (see oracle/__init__.py).
 
@@ -100,6 +100,29 @@ def chebyshev_basis(A, r, d, c, dx, dy=0.0):
             Hbar[j - 1, j] = gamma * sig[j - 1] / sig[j]
     M = A @ B[:, :d]
     return B, M, Hbar
+
+
+# ---------------------------------------------------------------------------
+# Block Chebyshev basis: §7.5 (the recurrence of §4.3 on an n x b block).
+# ---------------------------------------------------------------------------
+def block_chebyshev_basis(A, Omega, p, c, dx, dy=0.0):
+    """Block Chebyshev basis [B_1, ..., B_p] of K_p(A; Omega) for a spectrum
+    inside [c - dx, c + dx] x [-dy, dy] (rho = max(dx, dy),
+    gamma = (dx^2 - dy^2) / (4 rho)):
+
+        B_1 = Omega,   B_2 = (2 rho)^{-1} (A - c I) Omega,
+        B_j = rho^{-1} [ (A - c I) B_{j-1} - gamma B_{j-2} ],
+
+    as printed (no rescaling).  Returns the n x (b p) matrix, block-major.
+    """
+    rho = max(dx, dy)
+    gamma = (dx * dx - dy * dy) / (4.0 * rho)
+    blocks = [np.array(Omega, dtype=np.float64, copy=True)]
+    if p >= 2:
+        blocks.append((A @ blocks[0] - c * blocks[0]) / (2.0 * rho))
+    for _ in range(2, p):
+        blocks.append(((A @ blocks[-1] - c * blocks[-1]) - gamma * blocks[-2]) / rho)
+    return np.hstack(blocks)
 
 
 # ---------------------------------------------------------------------------

@@ -213,6 +213,44 @@ def test_chebyshev_basis_is_chebyshev_polynomials_on_a_diagonal(c, dx, dy):
     assert np.allclose(M, A @ B[:, :d])
 
 
+@pytest.mark.parametrize("c,dx,dy", [(4.0, 4.0, 0.0), (0.5, 0.5, 0.0), (3.0, 2.5, 1.5), (3.0, 1.0, 2.0)])
+def test_block_chebyshev_is_scaled_chebyshev_polynomials_on_a_diagonal(c, dx, dy):
+    # §7.5 as printed (no rescaling): for A = diag(lambda), block j (1-based)
+    # is exactly (f / (2 rho))^{j-1} T_{j-1}((A - c)/f) Omega with
+    # f = sqrt(dx^2 - dy^2) (imaginary for a tall ellipse, where the product
+    # is still real): compare with numpy's chebval, scalars included
+    from numpy.polynomial import chebyshev as npc
+    rng = np.random.default_rng(5)
+    n, b, p = 150, 4, 12
+    lam = c + dx * rng.uniform(-1, 1, n)
+    Om = rng.standard_normal((n, b))
+    B = krylov.block_chebyshev_basis(np.diag(lam), Om, p, c, dx, dy)
+    assert B.shape == (n, b * p)
+    rho = max(dx, dy)
+    f = np.sqrt(complex(dx * dx - dy * dy))
+    z = (lam - c) / f
+    for j in range(1, p + 1):
+        e = np.zeros(j)
+        e[j - 1] = 1.0
+        phi = (f / (2 * rho)) ** (j - 1) * npc.chebval(z, e)
+        assert np.abs(phi.imag).max() <= 1e-12 * max(1.0, np.abs(phi).max())
+        ref = phi.real[:, None] * Om
+        blk = B[:, (j - 1) * b: j * b]
+        assert np.allclose(blk, ref, rtol=1e-10, atol=1e-13 * np.abs(ref).max()), j
+
+
+def test_block_chebyshev_columns_are_the_vector_recurrence():
+    # column i of every block is the single-vector recurrence of §4.3 started
+    # from column i of Omega (nonsymmetric operator), up to column scaling
+    A = _cd(12, 10.0)
+    Om = np.column_stack([synth.randn(40 + i, 144) for i in range(3)])
+    B = krylov.block_chebyshev_basis(A, Om, 8, 4.0, 3.5, 0.0)
+    for i in range(3):
+        Bv, _, _ = krylov.chebyshev_basis(A, Om[:, i], 7, 4.0, 3.5, 0.0)
+        cols = B[:, i::3]
+        assert np.allclose(cols / np.linalg.norm(cols, axis=0), Bv, atol=1e-12)
+
+
 def test_chebyshev_relation_and_tridiagonal_hbar():
     # A B_d = B_{d+1} Hbar to rounding, Hbar tridiagonal with c on the
     # diagonal, on a nonsymmetric convection-diffusion operator whose real
