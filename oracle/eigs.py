@@ -1,5 +1,5 @@
-"""Sketched Rayleigh-Ritz (Algorithm 2), its stabilized form (§6.5) and
-Rayleigh-Ritz (§6.1).
+"""Sketched Rayleigh-Ritz (Algorithm 2), its stabilized form (§6.5), restarted
+sRR on block Chebyshev bases (§7.2, §7.5) and Rayleigh-Ritz (§6.1).
 
 Test infrastructure only (see oracle/__init__.py).
 """
@@ -99,6 +99,50 @@ def srr_stabilized(A, w1, d, k, sketch, nev, trunc_tol=1e14, tau=1e-8, symmetric
     """Stabilized sRR on the truncated Arnoldi basis of Algorithm 2."""
     B, M, _, _ = krylov.trunc_arnoldi(A, w1, d, k, passes=passes, breakdown=breakdown)
     return srr_stabilized_from_basis(B, M, sketch, nev, trunc_tol, tau, symmetric)
+
+
+def srr_restarted(A, Omega, p, nev, lo, hi, restarts, sketch_for, tau=1e-8, trunc_tol=1e13, stabilized=True):
+    """Restarted sRR (§7.2) on block Chebyshev bases (§7.5).
+
+    X_0 = Omega (n x b).  Restart t: Q = orth(X_t) (Householder QR of the
+    start block); B = [B_1..B_p] from block_chebyshev_basis(A, Q, p, c, dx)
+    for the interval [lo, cut_t] that holds the unwanted part of the real
+    spectrum (c, dx its centre and half-width; cut_0 = hi, then the real part
+    of the b-th Ritz value of restart t-1), each column scaled to unit norm;
+    sRR on (B, A B) with the sketch sketch_for(t) -- the stabilized form of
+    §6.5 (default; the basis condition number passes 1/u within a few
+    restarts) or Algorithm 2's reduction; X_{t+1} = the real and imaginary
+    parts of the b leading Ritz vectors (the first b nonzero columns).
+    Stops when the residual estimates of the nev leading pairs are all
+    <= tau, or after `restarts` restarts.
+    Returns the last sRR result (b leading pairs) plus ``restarts`` (the
+    number run) and ``history`` (max estimate over the nev pairs, per restart).
+    """
+    b = Omega.shape[1]
+    X = np.array(Omega, dtype=np.float64, copy=True)
+    cut = hi
+    history = []
+    out = None
+    for t in range(restarts):
+        Q, _ = np.linalg.qr(X)
+        c, dx = 0.5 * (lo + cut), 0.5 * (cut - lo)
+        B = krylov.block_chebyshev_basis(A, Q, p, c, dx, 0.0)
+        B = B / np.linalg.norm(B, axis=0)
+        M = A @ B
+        if stabilized:
+            out = srr_stabilized_from_basis(B, M, sketch_for(t), b, trunc_tol=trunc_tol, tau=tau)
+        else:
+            out = srr_from_basis(B, M, sketch_for(t), b, tau=tau)
+        history.append(float(np.max(out["rhat"][:nev])))
+        if history[-1] <= tau:
+            break
+        cut = out["lam"][b - 1].real
+        Xr = out["X"]
+        X = np.hstack([Xr.real, Xr.imag])
+        X = X[:, np.linalg.norm(X, axis=0) > 1e-10][:, :b]
+    out = dict(out)
+    out.update(restarts=len(history), history=history)
+    return out
 
 
 def rr_matrix(B, M):

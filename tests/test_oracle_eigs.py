@@ -203,3 +203,57 @@ def test_srr_on_block_chebyshev_basis_finds_separated_top():
             tr = np.array([eigs.eig_residual(A, out["lam"][i], out["X"][:, i]) for i in range(6)])
             assert np.all(tr <= 1e-3)
     assert errs[16] <= 1e-5 and errs[8] > 0.1
+
+
+# ---------------------------------------------------------------------------
+# Restarted sRR (§7.2) on block Chebyshev bases (§7.5)
+# ---------------------------------------------------------------------------
+def test_restarted_srr_laplacian_2d_closed_form_with_double_eigenvalue():
+    # Dirichlet 5-point Laplacian on 24 x 24: eigenvalues
+    # 4 - 2 cos(i pi/25) - 2 cos(j pi/25); the top five include the double
+    # eigenvalue of (i, j) = (23, 24) and (24, 23), which a block basis
+    # resolves: both copies, with independent Ritz vectors
+    import scipy.sparse  # noqa: F401  (operators returns scipy sparse)
+    N, b, p, nev = 24, 8, 12, 5
+    A = operators.stencil5_matrix(N, N, (4.0, -1.0, -1.0, -1.0, -1.0))
+    h = np.pi / (N + 1)
+    ev = np.sort([4 - 2 * np.cos(i * h) - 2 * np.cos(j * h) for i in range(1, N + 1) for j in range(1, N + 1)])[::-1]
+    assert abs(ev[1] - ev[2]) < 1e-14 and ev[0] - ev[1] > 1e-2
+    Om = np.column_stack([synth.randn(400 + i, N * N) for i in range(b)])
+    d = b * p
+    skf = lambda t: (lambda M: sketch.sparse_sign_apply(13 + t, 2 * d, hashing.default_zeta(d), M))
+    out = eigs.srr_restarted(A, Om, p, nev, -0.1, 7.0, 40, skf, tau=8e-9)
+    assert out["restarts"] < 40 and out["history"][-1] <= 8e-9
+    lam = out["lam"][:nev].real
+    assert np.allclose(np.sort(lam)[::-1], ev[:nev], atol=1e-9)
+    X = out["X"][:, :nev].real
+    for i in range(nev):
+        assert eigs.eig_residual(A, lam[i], X[:, i]) <= 1e-8
+    dbl = [i for i in range(nev) if abs(lam[i] - ev[1]) < 1e-8]
+    # two copies whose Ritz vectors span the 2-D eigenspace (any basis of it
+    # is valid, so they need not be orthogonal, only independent)
+    assert len(dbl) == 2
+    assert np.linalg.svd(X[:, dbl], compute_uv=False)[-1] >= 0.1
+
+
+def test_restarted_srr_matches_arpack_on_clustered_spectrum():
+    # the eig workload's operator at 48 x 48 (convection-diffusion, Pe = 10,
+    # uniform random diagonal shift): its top eigenvalues are clustered
+    # (single-vector restarts stall near 3e-3).  Block Chebyshev restarts
+    # reach true residuals <= 1e-8 ||A|| and ARPACK's eigenvalues (scipy
+    # eigs, 'LR', tol 1e-13) within 1e-7.
+    import scipy.sparse.linalg as spla
+    N, b, p, nev = 48, 12, 16, 6
+    shift = synth.uniform(1, N * N)
+    A = operators.stencil5_matrix(N, N, synth.conv_diff_coef(N, 10.0), shift)
+    An = 8 + shift.max()
+    ref = np.sort(spla.eigs(A, k=nev + 4, which="LR", return_eigenvectors=False, tol=1e-13).real)[::-1]
+    Om = np.column_stack([synth.randn(200 + i, N * N) for i in range(b)])
+    d = b * p
+    skf = lambda t: (lambda M: sketch.sparse_sign_apply(7 + t, 2 * d, hashing.default_zeta(d), M))
+    out = eigs.srr_restarted(A, Om, p, nev, -0.5, 8.0, 30, skf, tau=1e-8 * An)
+    assert out["restarts"] < 30
+    lam = out["lam"][:nev]
+    tr = np.array([eigs.eig_residual(A, lam[i], out["X"][:, i]) for i in range(nev)]) / An
+    assert tr.max() <= 1e-8
+    assert np.abs(np.sort(lam.real)[::-1] - ref[:nev]).max() <= 1e-7
