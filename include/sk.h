@@ -74,17 +74,19 @@ sk_status sk_op_transpose(const sk_op* op, sk_op** opT);
 /* y = A x in FP64 (x, y: device, n doubles; must not alias). */
 sk_status sk_op_apply(const sk_op* op, const double* x, double* y, void* stream);
 
-/* Gradient of the bilinear form lam^T A x with respect to the operator's
- * parameters (not in the paper: the building block of the adjoint of a
- * solve, dL/dparams = -grad(lam^T A x) with A^T lam = dL/dx).
- * lam, x: device n doubles.  grad: device doubles, layout by op kind:
+/* grad = alpha * (gradient of the bilinear form lam^T A x with respect to the
+ * operator's parameters).  Not in the paper: the building block of the
+ * adjoint of a solve x = A^{-1} b, whose parameter gradient is
+ * dL/dparams = -grad(lam^T A x) with A^T lam = dL/dx, i.e. alpha = -1.
+ * lam, x: device n doubles; alpha: finite scale.  grad: device doubles, layout by op kind:
  *   diffusion: n entries, d/dtheta_P (interior faces pass half of
  *              (lam_P - lam_Q)(x_P - x_Q) to each cell, boundary faces lam_P x_P);
  *   stencil5:  5 entries d/dc[0..4], then n entries d/dshift_P = lam_P x_P if
  *              the op has a shift;
  *   CSR:       nnz entries d/dval_e = lam_row(e) x_col(e).
  * Asynchronous; no allocation beyond a small reduction buffer. */
-sk_status sk_op_param_grad(const sk_op* op, const double* lam, const double* x, double* grad, void* stream);
+sk_status sk_op_param_grad(const sk_op* op, const double* lam, const double* x, double alpha, double* grad,
+                           void* stream);
 
 int64_t sk_op_n(const sk_op* op);
 void sk_op_destroy(sk_op* op);
@@ -123,8 +125,8 @@ sk_status sketch_apply(const sk_sketch* S, const void* B, int64_t ldb, int ncols
  * layout and results are those of sketch_apply (SK_SPARSE_SIGN only).
  * Scratch: one file-scope device array of 32 MiB in libsk, held by every GPU
  * that loads the library until the process exits.  A sketch needing more
- * (about nchunks*(s+1)*4 + nchunks*2048*zeta*2 + partial sums, nchunks =
- * ceil(n/2048)) returns SK_EINVAL with the byte count; nothing is launched.
+ * (about nchunks*(s+1)*4 + nchunks*1024*zeta*2 + partial sums, nchunks =
+ * ceil(n/1024)) returns SK_EINVAL with the byte count; nothing is launched.
  * The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress) with that device current; make that first call
  * before any stream capture.  All calls share the one array and it keeps
@@ -237,8 +239,10 @@ sk_status sgmres_solve(const sk_op* A, const double* b, double* x, int d, int k,
  *   A: host array of nsys ops; b, x: host arrays of nsys*nrhs device
  *   pointers (job i*nrhs + r = system i, right-hand side r); each x is the
  *   initial guess in, the solution out.  per_job: host array of nsys*nrhs
- *   statuses (or NULL).  info: aggregate (cycles and matvecs summed, relres
- *   the worst job, ms summed over jobs except ms[5] = wall time).
+ *   statuses (or NULL).  job_info: host array of nsys*nrhs sk_info, each the
+ *   job's own diagnostics as sgmres_solve reports them (or NULL).  info:
+ *   aggregate (cycles and matvecs summed, relres the worst job, ms summed
+ *   over jobs except ms[5] = wall time).
  * Jobs run on opts->batch_workers host threads with one stream each, largest
  * systems first; `stream` is joined before and after.  Blocks until done.
  * Jobs launch their kernels directly on their streams (opts->use_graph is
@@ -247,7 +251,7 @@ sk_status sgmres_solve(const sk_op* A, const double* b, double* x, int d, int k,
  * ------------------------------------------------------------------------ */
 sk_status sgmres_solve_batched(int nsys, const sk_op* const* A, int nrhs, const double* const* b,
                                double* const* x, int d, int k, int s, double tol, const sk_opts* opts,
-                               sk_status* per_job, sk_info* info, void* stream);
+                               sk_status* per_job, sk_info* job_info, sk_info* info, void* stream);
 
 /* ------------------------------------------------------------------------
  * Sketched Rayleigh-Ritz (Algorithm 2, §6.3-§6.4): nev eigenpairs of A with

@@ -24,3 +24,22 @@ def loss_and_grad(nx, ny, theta, b, x_t):
     lam = lu.solve(gx, trans="T")
     gtheta = -operators.diffusion_var_theta_grad(nx, ny, lam, x)
     return float(np.sum((x - x_t) ** 2)), gtheta, lam, x
+
+
+def stencil_loss_and_grad(nx, ny, coef, shift, b, x_t):
+    """The same loss for the five-point operator of oracle.operators with
+    coefficients coef = (c_P, c_E, c_W, c_N, c_S) and diagonal shift:
+      lam = A^{-T} 2(x - x_t),  dL/db = lam,
+      dL/dc_q = -lam^T A_q x  (A_q: the q-th neighbour pattern, unit weight),
+      dL/dshift_P = -lam_P x_P.
+    Returns (L, dL/dc (5,), dL/dshift (n,), lam, x)."""
+    A = operators.stencil5_matrix(nx, ny, coef, shift).tocsc()
+    lu = spla.splu(A)
+    x = lu.solve(np.asarray(b, dtype=np.float64))
+    lam = lu.solve(2.0 * (x - x_t), trans="T")
+    gc = np.zeros(5)
+    for q in range(5):
+        e = np.zeros(5)
+        e[q] = 1.0
+        gc[q] = -lam @ (operators.stencil5_matrix(nx, ny, e) @ x)
+    return float(np.sum((x - x_t) ** 2)), gc, -lam * x, lam, x

@@ -105,8 +105,9 @@ class Op:
     def __matmul__(self, x):
         return self.apply(x)
 
-    def param_grad(self, lam, x):
-        """Gradient of lam^T A x with respect to the operator's parameters.
+    def param_grad(self, lam, x, alpha=1.0):
+        """alpha times the gradient of lam^T A x with respect to the
+        operator's parameters (the adjoint of a solve uses alpha = -1).
 
         diffusion: (n,) d/dtheta; stencil5: 5 coefficient entries (+ n shift
         entries if the op has a shift); CSR: (nnz,) d/dval.
@@ -120,7 +121,7 @@ class Op:
         else:
             m = self._keep[2].numel()
         g = torch.empty(m, dtype=torch.float64, device=lam.device)
-        N.check(N.lib.sk_op_param_grad(self._h, _ptr(lam), _ptr(x), _ptr(g), _stream()))
+        N.check(N.lib.sk_op_param_grad(self._h, _ptr(lam), _ptr(x), float(alpha), _ptr(g), _stream()))
         return g
 
     def __del__(self):
@@ -244,7 +245,9 @@ def sgmres_solve_batched(ops, bs, d, k, s, tol, x0s=None, **opts):
     """Batched restarted sGMRES over independent jobs.
 
     ops: list of nsys Op; bs: list of nsys lists of nrhs CUDA tensors.
-    Returns (xs like bs, per-job status list, aggregate info dict).
+    Returns (xs like bs, per-job status list, aggregate info dict); the
+    aggregate dict carries "jobs", the per-job info dicts in the order of
+    the flattened (system, right-hand side) list.
     """
     nsys = len(ops)
     nrhs = len(bs[0])
@@ -257,12 +260,15 @@ def sgmres_solve_batched(ops, bs, d, k, s, tol, x0s=None, **opts):
     PB = (C.c_void_p * (nsys * nrhs))(*[t.data_ptr() for t in flat_b])
     PX = (C.c_void_p * (nsys * nrhs))(*[t.data_ptr() for t in flat_x])
     stat = (C.c_int * (nsys * nrhs))()
+    jinfo = (N.SkInfo * (nsys * nrhs))()
     o = make_opts(**opts)
     info = N.SkInfo()
-    N.check(N.lib.sgmres_solve_batched(nsys, PA, nrhs, PB, PX, d, k, s, float(tol), C.byref(o), stat,
+    N.check(N.lib.sgmres_solve_batched(nsys, PA, nrhs, PB, PX, d, k, s, float(tol), C.byref(o), stat, jinfo,
                                        C.byref(info), _stream()), allow=(N.SK_OK, N.SK_ENOCONV))
     xs = [[flat_x[i * nrhs + r] for r in range(nrhs)] for i in range(nsys)]
-    return xs, list(stat), info.as_dict()
+    out = info.as_dict()
+    out["jobs"] = [jinfo[j].as_dict() for j in range(nsys * nrhs)]
+    return xs, list(stat), out
 
 
 def autotune_batch_workers(ops, bs, d, k, s, tol, candidates=(4, 8, 16, 32, 48), sample=48, **opts):
@@ -306,6 +312,27 @@ def srr_eigs(A, w1, nev, d, k, s, **opts):
                 info=info.as_dict())
 
 
+def _adjoint(op, x, gx, d, k, s, tol, opts):
+    """Backward of x = A^{-1} b: lam = A^{-T} dL/dx by sGMRES with A^T (the
+    library's transposed operator, the same kernels), then dL/db = lam and
+    dL/dparams = -d(lam^T A x)/dparams (sk_op_param_grad with alpha = -1)."""
+    gx = gx.detach().to(torch.float64).contiguous()
+    if float(gx.abs().max()) == 0.0:
+        lam = torch.zeros_like(gx)
+    else:
+        lam, info = sgmres_solve(op.T, gx, d, k, s, tol, **opts)
+        if info["status"] != N.SK_OK:
+            raise SkError(info["status"], "adjoint solve did not reach tol (relres %g)" % info["relres"])
+    return lam, op.param_grad(lam, x, alpha=-1.0)
+
+
+def _forward(op, b, d, k, s, tol, opts):
+    x, info = sgmres_solve(op, b.detach(), d, k, s, tol, **opts)
+    if info["status"] != N.SK_OK:
+        raise SkError(info["status"], "forward solve did not reach tol (relres %g)" % info["relres"])
+    return x, info
+
+
 class DiffusionSolve(torch.autograd.Function):
     """x = A(theta)^{-1} b by sGMRES, differentiable in theta and b.
 
@@ -320,9 +347,7 @@ class DiffusionSolve(torch.autograd.Function):
     @staticmethod
     def forward(ctx, theta, b, nx, ny, d, k, s, tol, opts):
         op = Op.diffusion_var(nx, ny, theta.detach())
-        x, info = sgmres_solve(op, b.detach(), d, k, s, tol, **opts)
-        if info["status"] != N.SK_OK:
-            raise SkError(info["status"], "forward solve did not reach tol (relres %g)" % info["relres"])
+        x, info = _forward(op, b, d, k, s, tol, opts)
         ctx.save_for_backward(theta.detach(), x)
         ctx.cfg = (nx, ny, d, k, s, tol, opts)
         ctx.info = info
@@ -332,19 +357,43 @@ class DiffusionSolve(torch.autograd.Function):
     def backward(ctx, gx):
         theta, x = ctx.saved_tensors
         nx, ny, d, k, s, tol, opts = ctx.cfg
-        op = Op.diffusion_var(nx, ny, theta)
-        opT = op.T
-        gx = gx.detach().to(torch.float64).contiguous()
-        if float(gx.abs().max()) == 0.0:
-            lam = torch.zeros_like(gx)
-        else:
-            lam, info = sgmres_solve(opT, gx, d, k, s, tol, **opts)
-            if info["status"] != N.SK_OK:
-                raise SkError(info["status"], "adjoint solve did not reach tol (relres %g)" % info["relres"])
-        gtheta = -op.param_grad(lam, x)
+        lam, gtheta = _adjoint(Op.diffusion_var(nx, ny, theta), x, gx, d, k, s, tol, opts)
         return gtheta, lam, None, None, None, None, None, None, None
 
 
 def diffusion_solve(theta, b, nx, ny, d=100, k=2, s=200, tol=1e-10, **opts):
     """Differentiable x = A(theta)^{-1} b (see DiffusionSolve)."""
     return DiffusionSolve.apply(theta, b, nx, ny, d, k, s, tol, opts)
+
+
+class StencilSolve(torch.autograd.Function):
+    """x = A(c, shift)^{-1} b by sGMRES for the five-point stencil operator
+    (Op.stencil5), differentiable in the five coefficients c, the diagonal
+    shift (if given) and b.  Backward: the adjoint solve with the transposed
+    stencil, then dL/dc and dL/dshift from sk_op_param_grad (alpha = -1)."""
+
+    @staticmethod
+    def forward(ctx, coef, shift, b, nx, ny, d, k, s, tol, opts):
+        cf = [float(v) for v in coef.detach().cpu()]
+        sh = shift.detach() if shift is not None else None
+        op = Op.stencil5(nx, ny, cf, sh)
+        x, info = _forward(op, b, d, k, s, tol, opts)
+        ctx.save_for_backward(x)
+        ctx.cfg = (cf, sh, nx, ny, d, k, s, tol, opts, coef.device, coef.dtype)
+        ctx.info = info
+        return x
+
+    @staticmethod
+    def backward(ctx, gx):
+        (x,) = ctx.saved_tensors
+        cf, sh, nx, ny, d, k, s, tol, opts, cdev, cdt = ctx.cfg
+        lam, g = _adjoint(Op.stencil5(nx, ny, cf, sh), x, gx, d, k, s, tol, opts)
+        gc = g[:5].to(device=cdev, dtype=cdt)
+        gs = g[5:] if sh is not None else None
+        return gc, gs, lam, None, None, None, None, None, None, None
+
+
+def stencil_solve(coef, b, nx, ny, shift=None, d=100, k=2, s=200, tol=1e-10, **opts):
+    """Differentiable x = A(coef, shift)^{-1} b (see StencilSolve); coef is a
+    tensor of the five coefficients (centre, E, W, N, S)."""
+    return StencilSolve.apply(coef, shift, b, nx, ny, d, k, s, tol, opts)

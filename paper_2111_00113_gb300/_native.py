@@ -63,7 +63,7 @@ def _load():
         "sk_op_transpose": (st, [P, C.POINTER(P)]),
         "sk_op_apply": (st, [P, P, P, P]),
         "sk_op_n": (I64, [P]),
-        "sk_op_param_grad": (st, [P, P, P, P, P]),
+        "sk_op_param_grad": (st, [P, P, P, D, P, P]),
         "sk_op_destroy": (None, [P]),
         "sketch_apply": (st, [C.POINTER(SkSketch), P, I64, I, I, P, P]),
         "sketch_apply_noalloc": (st, [C.POINTER(SkSketch), P, I64, I, I, P, P]),
@@ -72,7 +72,8 @@ def _load():
                                      C.POINTER(I), P]),
         "sgmres_solve": (st, [P, P, P, I, I, I, D, C.POINTER(SkOpts), C.POINTER(SkInfo), P]),
         "sgmres_solve_batched": (st, [I, C.POINTER(P), I, C.POINTER(P), C.POINTER(P), I, I, I, D,
-                                      C.POINTER(SkOpts), C.POINTER(C.c_int), C.POINTER(SkInfo), P]),
+                                      C.POINTER(SkOpts), C.POINTER(C.c_int), C.POINTER(SkInfo),
+                                      C.POINTER(SkInfo), P]),
         "srr_eigs": (st, [P, P, I, I, I, I, C.POINTER(SkOpts), C.POINTER(D), C.POINTER(D), P, P,
                           C.POINTER(D), C.POINTER(I), C.POINTER(SkInfo), P]),
         "sk_last_error": (C.c_char_p, []),

@@ -80,7 +80,7 @@ __global__ void op_apply_kernel(OpView<double> A, const double* __restrict__ x, 
 
 // d(lam^T A x)/dtheta for the variable-coefficient diffusion operator.
 __global__ void diffusion_grad_kernel(int nx, int ny, const double* __restrict__ lam, const double* __restrict__ x,
-                                      double* __restrict__ g) {
+                                      double alpha, double* __restrict__ g) {
   const int64_t n = (int64_t)nx * ny;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const int ix = (int)(i % nx);
@@ -91,14 +91,14 @@ __global__ void diffusion_grad_kernel(int nx, int ny, const double* __restrict__
     a += (ix > 0) ? 0.5 * (lP - lam[i - 1]) * (xP - x[i - 1]) : lP * xP;
     a += (iy + 1 < ny) ? 0.5 * (lP - lam[i + nx]) * (xP - x[i + nx]) : lP * xP;
     a += (iy > 0) ? 0.5 * (lP - lam[i - nx]) * (xP - x[i - nx]) : lP * xP;
-    g[i] = a;
+    g[i] = alpha * a;
   }
 }
 
 // d(lam^T A x)/dc for the five stencil coefficients (per-CTA partials, then
 // one fixed-order sum) and d/dshift_P = lam_P x_P.
 __global__ void stencil_grad_kernel(int nx, int ny, const double* __restrict__ lam, const double* __restrict__ x,
-                                    double* __restrict__ part, double* __restrict__ gshift) {
+                                    double alpha, double* __restrict__ part, double* __restrict__ gshift) {
   __shared__ double red[5 * 8];
   const int64_t n = (int64_t)nx * ny;
   double a[5] = {0, 0, 0, 0, 0};
@@ -111,25 +111,27 @@ __global__ void stencil_grad_kernel(int nx, int ny, const double* __restrict__ l
     if (ix > 0) a[2] += l * x[i - 1];
     if (iy + 1 < ny) a[3] += l * x[i + nx];
     if (iy > 0) a[4] += l * x[i - nx];
-    if (gshift) gshift[i] = l * x[i];
+    if (gshift) gshift[i] = alpha * (l * x[i]);
   }
   block_sum_k<5>(a, red);
   if (threadIdx.x == 0)
     for (int q = 0; q < 5; ++q) part[blockIdx.x * 5 + q] = a[q];
 }
 
-__global__ void sum_parts_kernel(const double* __restrict__ part, int nblk, int K, double* __restrict__ out) {
+__global__ void sum_parts_kernel(const double* __restrict__ part, int nblk, int K, double alpha,
+                                 double* __restrict__ out) {
   for (int q = threadIdx.x; q < K; q += blockDim.x) {
     double a = 0;
     for (int b = 0; b < nblk; ++b) a += part[b * K + q];
-    out[q] = a;
+    out[q] = alpha * a;
   }
 }
 
 __global__ void csr_grad_kernel(int64_t n, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
-                                const double* __restrict__ lam, const double* __restrict__ x, double* __restrict__ g) {
+                                const double* __restrict__ lam, const double* __restrict__ x, double alpha,
+                                double* __restrict__ g) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const double l = lam[i];
+    const double l = alpha * lam[i];
     for (int32_t e = rowptr[i]; e < rowptr[i + 1]; ++e) g[e] = l * x[col[e]];
   }
 }
@@ -256,21 +258,23 @@ sk_status sk_op_transpose(const sk_op* op, sk_op** opT) {
 
 int64_t sk_op_n(const sk_op* op) { return op ? op->n : 0; }
 
-sk_status sk_op_param_grad(const sk_op* op, const double* lam, const double* x, double* grad, void* stream) {
+sk_status sk_op_param_grad(const sk_op* op, const double* lam, const double* x, double alpha, double* grad,
+                           void* stream) {
   SK_CHECK_ARG(op != nullptr && lam != nullptr && x != nullptr && grad != nullptr, "NULL argument");
+  SK_CHECK_ARG(std::isfinite(alpha), "alpha must be finite");
   cudaStream_t st = (cudaStream_t)stream;
   int blocks = (int)((op->n + 255) / 256);
   if (blocks > 4 * num_sms()) blocks = 4 * num_sms();
   if (op->kind == OP_DIFFUSION) {
-    diffusion_grad_kernel<<<blocks, 256, 0, st>>>(op->nx, op->ny, lam, x, grad);
+    diffusion_grad_kernel<<<blocks, 256, 0, st>>>(op->nx, op->ny, lam, x, alpha, grad);
   } else if (op->kind == OP_STENCIL5) {
     Scratch sc(st);
     double* part = nullptr;
     SK_TRY(sc.alloc(&part, (size_t)blocks * 5));
-    stencil_grad_kernel<<<blocks, 256, 0, st>>>(op->nx, op->ny, lam, x, part, op->shift ? grad + 5 : nullptr);
-    sum_parts_kernel<<<1, 32, 0, st>>>(part, blocks, 5, grad);
+    stencil_grad_kernel<<<blocks, 256, 0, st>>>(op->nx, op->ny, lam, x, alpha, part, op->shift ? grad + 5 : nullptr);
+    sum_parts_kernel<<<1, 32, 0, st>>>(part, blocks, 5, alpha, grad);
   } else {
-    csr_grad_kernel<<<blocks, 256, 0, st>>>(op->n, op->rowptr, op->colind, lam, x, grad);
+    csr_grad_kernel<<<blocks, 256, 0, st>>>(op->n, op->rowptr, op->colind, lam, x, alpha, grad);
   }
   SK_CUDA(cudaGetLastError());
   return SK_OK;

@@ -801,7 +801,7 @@ extern "C" sk_status sgmres_solve(const sk_op* A, const double* b, double* x, in
 // ----------------------------------------------------------------------------
 extern "C" sk_status sgmres_solve_batched(int nsys, const sk_op* const* A, int nrhs, const double* const* b,
                                           double* const* x, int d, int k, int s, double tol, const sk_opts* opts,
-                                          sk_status* per_job, sk_info* info, void* stream) {
+                                          sk_status* per_job, sk_info* job_info, sk_info* info, void* stream) {
   SK_CHECK_ARG(nsys >= 1 && nrhs >= 1, "need nsys >= 1 and nrhs >= 1");
   SK_CHECK_ARG(A != nullptr && b != nullptr && x != nullptr, "NULL argument");
   SK_CHECK_ARG(d >= 1 && k >= 1 && k <= d && k <= kMaxK && s >= d + 1 && tol > 0 && d <= 768,
@@ -864,6 +864,7 @@ extern "C" sk_status sgmres_solve_batched(int nsys, const sk_op* const* A, int n
         const sk_status r = sgmres_impl(A[job / nrhs], b[job], x[job], d, k, s, tol, &o, &ji, ws, pinned);
         std::lock_guard<std::mutex> lk(mu);
         if (per_job) per_job[job] = r;
+        if (job_info) job_info[job] = ji;
         if (r != SK_OK && first_err == SK_OK) { first_err = r; first_msg = sk_last_error(); }
         cycles += ji.cycles;
         matvecs += ji.matvecs;

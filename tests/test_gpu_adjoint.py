@@ -131,3 +131,26 @@ def test_adjoint_workload_full_size_directional(skg):
     assert abs(L32 - L) <= 1e-3 * L
     assert np.linalg.norm(g32 - gth) <= 5e-2 * np.linalg.norm(gth)
     assert np.linalg.norm(gb32 - gb) <= 5e-2 * np.linalg.norm(gb)
+
+
+def test_stencil_solve_gradients_match_oracle(skg):
+    # the differentiable solve for the five-point operator: gradients with
+    # respect to the five coefficients, the diagonal shift and b against the
+    # oracle's dense adjoint (oracle/adjoint.py stencil_loss_and_grad)
+    import torch
+    N = 24
+    coef = np.array(synth.conv_diff_coef(N, 20.0))
+    shift = synth.uniform(8, N * N)
+    b = synth.randn(9, N * N)
+    xt = synth.randn(10, N * N) * 0.01
+    c = torch.tensor(coef, dtype=torch.float64, requires_grad=True)
+    sh = _t(shift).requires_grad_(True)
+    bb = _t(b).requires_grad_(True)
+    x = skg.stencil_solve(c, bb, N, N, shift=sh, d=100, k=2, s=200, tol=1e-13)
+    L = torch.sum((x - _t(xt)) ** 2)
+    L.backward()
+    Lr, gc, gs, lam, _ = adjoint.stencil_loss_and_grad(N, N, coef, shift, b, xt)
+    assert abs(L.item() - Lr) <= 1e-9 * Lr
+    assert np.allclose(c.grad.numpy(), gc, rtol=1e-7, atol=1e-9 * np.abs(gc).max())
+    assert np.linalg.norm(sh.grad.cpu().numpy() - gs) <= 1e-7 * np.linalg.norm(gs)
+    assert np.linalg.norm(bb.grad.cpu().numpy() - lam) <= 1e-7 * np.linalg.norm(lam)

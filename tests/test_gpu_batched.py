@@ -80,3 +80,61 @@ def test_batched_workload_full(skg):
             else:
                 assert rel < 0.1
     assert checked >= 8
+
+
+def _batched_golden():
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(__file__), "golden", "batched_oracle.json")) as fh:
+        return json.load(fh)
+
+
+def test_batched_jobs_match_oracle_history(skg):
+    # jobs of the batched workload of different sizes (129^2 .. 485^2), one
+    # right-hand side each drawn on the host, FP64 basis, the oracle's sketch;
+    # tests/golden/batched_oracle.json holds the FP64 oracle's residual after
+    # every cycle (written by make_batched_reference.py from the oracle only).
+    # Cycle by cycle (restarting from the returned x is the next cycle of
+    # the same run): each job's residual within 1.5x of the oracle's; then
+    # the uninterrupted batched solve: cycles within +-1 of the oracle's and
+    # the final residual within 1.5x of the oracle's at that cycle.  FP32
+    # basis: every job reaches tol within the oracle's cycles + 2.
+    import torch
+    ref = _batched_golden()
+    W = synth.WORKLOADS["batched"]
+    sides, pes = synth.batch_systems(W["seed"], W["nsys"])
+    ops, bs, mats, fs, hist = [], [], [], [], []
+    for job in ref["jobs"]:
+        i = job["system"]
+        N = int(sides[i])
+        assert N == job["N"]
+        coef = synth.conv_diff_coef(N, pes[i])
+        ops.append(skg.Op.stencil5(N, N, coef))
+        mats.append(operators.stencil5_matrix(N, N, coef))
+        f = synth.randn(synth.batch_rhs_seed(i, 0), N * N)
+        fs.append(f)
+        bs.append([torch.tensor(f, device="cuda")])
+        hist.append(job["relres"])
+    kw = dict(zeta=W["zeta"], seed=7, basis=torch.float64)
+    d, k, s = W["d"], W["k"], W["s"]
+    xs = None
+    for c in range(max(len(h) for h in hist)):
+        xs, stat, _ = skg.sgmres_solve_batched(ops, bs, d, k, s, 1e-300, x0s=xs, maxit=1, batch_workers=3, **kw)
+        for j in range(len(ops)):
+            if c < len(hist[j]):
+                rel = _rel(mats[j], fs[j], xs[j][0].cpu().numpy())
+                assert rel <= 1.5 * hist[j][c] and hist[j][c] <= 1.5 * rel, (j, c, rel, hist[j][c])
+    xs, stat, info = skg.sgmres_solve_batched(ops, bs, d, k, s, W["tol"], batch_workers=3, **kw)
+    assert all(st == 0 for st in stat), stat
+    for j, ji in enumerate(info["jobs"]):
+        assert abs(ji["cycles"] - len(hist[j])) <= 1, (j, ji["cycles"], len(hist[j]))
+        rel = _rel(mats[j], fs[j], xs[j][0].cpu().numpy())
+        assert rel <= W["tol"]
+        assert rel <= 1.5 * hist[j][min(ji["cycles"], len(hist[j])) - 1]
+        assert ji["relres"] == pytest.approx(rel, rel=1e-6)
+    xs, stat, info = skg.sgmres_solve_batched(ops, bs, d, k, s, W["tol"], batch_workers=3,
+                                              **dict(kw, basis=torch.float32))
+    assert all(st == 0 for st in stat), stat
+    for j, ji in enumerate(info["jobs"]):
+        assert ji["cycles"] <= len(hist[j]) + 2, (j, ji["cycles"], len(hist[j]))
+        assert _rel(mats[j], fs[j], xs[j][0].cpu().numpy()) <= W["tol"]

@@ -59,3 +59,34 @@ def test_adjoint_gradient_equals_forward_mode_derivatives():
         db = synth.randn(30 + q, n)
         dLb = 2.0 * (x - xt) @ np.linalg.solve(A, db)
         assert abs(dLb - lam @ db) <= 1e-10 * max(1.0, abs(dLb))
+
+
+def test_stencil_adjoint_gradient_matches_central_differences():
+    # coefficients and shift of the five-point operator: central differences
+    # of the dense loss (a dropped sign or a transposed neighbour fails)
+    nx, ny = 7, 5
+    n = nx * ny
+    coef = np.array([4.0, -0.7, -1.3, -0.9, -1.1])
+    shift = synth.uniform(3, n)
+    b = synth.randn(4, n)
+    xt = synth.randn(5, n) * 0.1
+
+    def loss(c, sh, bv):
+        A = operators.stencil5_matrix(nx, ny, c, sh).toarray()
+        x = np.linalg.solve(A, bv)
+        return np.sum((x - xt) ** 2)
+
+    L, gc, gs, lam, x = adjoint.stencil_loss_and_grad(nx, ny, coef, shift, b, xt)
+    assert abs(L - loss(coef, shift, b)) <= 1e-12 * L
+    for q in range(5):
+        e = np.zeros(5)
+        e[q] = 1e-6
+        fd = (loss(coef + e, shift, b) - loss(coef - e, shift, b)) / 2e-6
+        assert abs(fd - gc[q]) <= 1e-6 * max(1.0, abs(gc[q])), (q, fd, gc[q])
+    for p in range(0, n, 4):
+        e = np.zeros(n)
+        e[p] = 1e-6
+        fd = (loss(coef, shift + e, b) - loss(coef, shift - e, b)) / 2e-6
+        assert abs(fd - gs[p]) <= 1e-6 * max(1.0, abs(gs[p]))
+        fd = (loss(coef, shift, b + e) - loss(coef, shift, b - e)) / 2e-6
+        assert abs(fd - lam[p]) <= 1e-6 * max(1.0, abs(lam[p]))
