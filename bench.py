@@ -320,7 +320,8 @@ def run_ours(args):
     W, N, coef, f, b = _problem(dev)
     A = skg.Op.stencil5(N, N, coef)
     form = {"f32": torch.float32, "bf16": torch.bfloat16, "f64": torch.float64}[args.form]
-    kw = dict(zeta=W["zeta"], seed=7, basis=form, sketch=args.sketch, persistent=args.persistent)
+    kw = dict(zeta=W["zeta"], seed=7, basis=form, sketch=args.sketch, persistent=args.persistent,
+              pipeline=not args.no_pipeline)
     x = torch.zeros_like(b)
 
     def solve(basis=form):
@@ -424,6 +425,8 @@ def run_ours(args):
                                "s=600, zeta=12, tol=1e-6",
                    "form": "%s basis/SpMV, FP64 residual/update/QR" % args.form.upper(), "sketch": args.sketch,
                    "basis_kernel": "persistent" if args.persistent else "3 launches per Arnoldi step",
+                   "cycle": "sequential" if (args.no_pipeline or args.persistent) else
+                            "pipelined (block sketch + QR panels overlapped with the basis passes)",
                    "l2": "inputs larger than L2 (basis %.2f GB per cycle)" % (esz * n * (d + 1) / 1e9),
                    "parallelism": "replicas" if ws > 1 else "single GPU"},
         "converged": ok, "cycles": cycles, "relres": last["relres"],
@@ -469,6 +472,8 @@ def build_parser():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-baseline", action="store_true")
     ap.add_argument("--persistent", action="store_true", help="one cooperative kernel per basis build")
+    ap.add_argument("--no-pipeline", action="store_true",
+                    help="run each cycle's phases one after another (no sketch/QR overlap with the basis)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the sketch, sRR, batched and Laplacian measurements")
     return ap

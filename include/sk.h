@@ -182,6 +182,11 @@ typedef struct {
                               solve uses exactly that prefix.  A positive multiple of 16, at most
                               1024; truncated-Arnoldi basis only (SK_EINVAL otherwise); no CUDA
                               graph and no persistent kernel; the host reads one flag per chunk */
+  int pipeline;            /* sgmres_solve with a captured cycle (use_graph), the truncated-Arnoldi
+                              basis and 3 launches per step: 1 (default) = sketch each finished
+                              block of 16 basis columns and add the panels it completes to the QR
+                              of S A B on a second, lower-priority stream while the basis passes
+                              continue (same arithmetic, overlapped); 0 = one phase after another */
 } sk_opts;
 
 void sk_opts_default(sk_opts* o);
@@ -197,6 +202,8 @@ typedef struct {
   float ms[6];         /* device ms summed over cycles (CUDA events on the call's stream):
                           [0] residual r = b - A x, [1] basis, [2] sketches (g = S r, S B),
                           [3] small dense solve, [4] solution update, [5] whole call.
+                          pipelined cycles: [2] is the sketch and QR work left after the
+                          basis passes end (the part not overlapped), [3] the LS solve.
                           iter_chunk > 0: [1] is the whole chunk loop (basis, S B, QR, the
                           per-chunk test), [2] is g = S r and [3] the final solve */
   long long launches;  /* CUDA kernels launched by the call */

@@ -173,12 +173,14 @@ def sketch_apply_noalloc(B, s, zeta=0, seed=7):
 
 def make_opts(basis=torch.float64, sketch="sparse", zeta=0, seed=7, stab_tol=0.0, maxit=10000, cgs_passes=2,
               tau=1e-8, symmetric=False, breakdown=0.0, use_graph=True, persistent=False, batch_workers=0,
-              cheb=None, barrier_spins=0, iter_chunk=0):
+              cheb=None, barrier_spins=0, iter_chunk=0, pipeline=True):
     """Solver options.  cheb=(c, dx, dy) selects the Chebyshev basis (§4.3)
     for a spectrum inside [c - dx, c + dx] x [-dy, dy].  iter_chunk > 0
     selects iterative sGMRES (§5.2): the cycle grows the basis iter_chunk
     columns at a time and stops at the first prefix whose residual estimate
-    meets the target."""
+    meets the target.  pipeline=False runs the cycle's phases one after
+    another instead of overlapping the sketch and QR of finished basis
+    blocks with the basis passes."""
     o = N.SkOpts()
     N.lib.sk_opts_default(C.byref(o))
     o.sketch = _KIND[sketch]
@@ -196,6 +198,7 @@ def make_opts(basis=torch.float64, sketch="sparse", zeta=0, seed=7, stab_tol=0.0
     o.batch_workers = int(batch_workers)
     o.barrier_spins = int(barrier_spins)
     o.iter_chunk = int(iter_chunk)
+    o.pipeline = int(bool(pipeline))
     if cheb is not None:
         o.basis_kind = 1
         o.cheb_c, o.cheb_dx, o.cheb_dy = (float(v) for v in cheb)

@@ -31,7 +31,7 @@ class SkOpts(C.Structure):
         ("maxit", C.c_int), ("basis", C.c_int), ("cgs_passes", C.c_int), ("tau", C.c_double),
         ("symmetric", C.c_int), ("breakdown", C.c_double), ("use_graph", C.c_int), ("persistent", C.c_int),
         ("batch_workers", C.c_int), ("basis_kind", C.c_int), ("cheb_c", C.c_double), ("cheb_dx", C.c_double),
-        ("cheb_dy", C.c_double), ("barrier_spins", C.c_int), ("iter_chunk", C.c_int),
+        ("cheb_dy", C.c_double), ("barrier_spins", C.c_int), ("iter_chunk", C.c_int), ("pipeline", C.c_int),
     ]
 
 

@@ -179,6 +179,7 @@ void sk_opts_default(sk_opts* o) {
   o->cheb_c = o->cheb_dx = o->cheb_dy = 0;
   o->barrier_spins = 0;
   o->iter_chunk = 0;
+  o->pipeline = 1;
 }
 
 static sk_op* new_op() {

@@ -353,18 +353,29 @@ dots_kernel(BasisParams p, OpView<typename Compute<T>::type> A, int j) {
   if (brk) *p.stop = j + 1;
 }
 
+// prio != 0 gives the launch that priority (the pipelined cycle raises the
+// basis passes above the sketch and QR work that runs beside them).
 template <typename K, typename... Args>
-static cudaError_t launch_pdl(K kernel, int grid, cudaStream_t st, bool pdl, Args... args) {
+static cudaError_t launch_pdl(K kernel, int grid, cudaStream_t st, bool pdl, int prio, Args... args) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
   cfg.blockDim = dim3(kBasisThreads);
   cfg.dynamicSmemBytes = 0;
   cfg.stream = st;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchAttribute attr[2];
+  int na = 0;
+  if (pdl) {
+    attr[na].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[na].val.programmaticStreamSerializationAllowed = 1;
+    ++na;
+  }
+  if (prio != 0) {
+    attr[na].id = cudaLaunchAttributePriority;
+    attr[na].val.priority = prio;
+    ++na;
+  }
   cfg.attrs = attr;
-  cfg.numAttrs = pdl ? 1 : 0;
+  cfg.numAttrs = na;
   return cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 
@@ -463,8 +474,8 @@ template <typename T, int G>
 static sk_status enqueue_cheb_t(const BasisParams& p, const OpView<typename Compute<T>::type>& A, cudaStream_t st) {
   using C = typename Compute<T>::type;
   const int g = p.nblk;
-  SK_CUDA(launch_pdl(form_kernel<T, 2, G, false>, g, st, false, p, A, 0));  // v_0 = r/||r||
-  for (int c = 1; c <= p.d; ++c) SK_CUDA(launch_pdl(cheb_kernel<T, G>, g, st, true, p, A, c));
+  SK_CUDA(launch_pdl(form_kernel<T, 2, G, false>, g, st, false, p.prio, p, A, 0));  // v_0 = r/||r||
+  for (int c = 1; c <= p.d; ++c) SK_CUDA(launch_pdl(cheb_kernel<T, G>, g, st, true, p.prio, p, A, c));
   cheb_finalize_kernel<C><<<p.d + 1, kBasisThreads, 0, st>>>(p, g);
   SK_CUDA(cudaGetLastError());
   return SK_OK;
@@ -509,11 +520,11 @@ static sk_status enqueue_basis_t(const BasisParams& p, const OpView<typename Com
   // steps [j_begin, j_end) (j_end = 0: all d); the first launch follows
   // memset/plain nodes or other kernels: no programmatic edge
   const int jb = p.j_begin, je = p.j_end > 0 ? p.j_end : p.d;
-  if (jb == 0) SK_CUDA(launch_pdl(form_kernel<T, KM, G, SM>, g, st, false, p, A, 0));
+  if (jb == 0) SK_CUDA(launch_pdl(form_kernel<T, KM, G, SM>, g, st, false, p.prio, p, A, 0));
   for (int j = jb; j < je; ++j) {
-    SK_CUDA(launch_pdl(dots_kernel<T, KM, G, SM, 1>, g, st, jb == 0 || j > jb, p, A, j));
-    if (p.passes == 2) SK_CUDA(launch_pdl(dots_kernel<T, KM, G, SM, 2>, g, st, true, p, A, j));
-    SK_CUDA(launch_pdl(form_kernel<T, KM, G, SM>, g, st, true, p, A, j + 1));
+    SK_CUDA(launch_pdl(dots_kernel<T, KM, G, SM, 1>, g, st, jb == 0 || j > jb || p.pdl_resume, p.prio, p, A, j));
+    if (p.passes == 2) SK_CUDA(launch_pdl(dots_kernel<T, KM, G, SM, 2>, g, st, true, p.prio, p, A, j));
+    SK_CUDA(launch_pdl(form_kernel<T, KM, G, SM>, g, st, true, p.prio, p, A, j + 1));
   }
   return SK_OK;
 }

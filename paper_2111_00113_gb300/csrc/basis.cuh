@@ -34,6 +34,9 @@ struct BasisParams {
   int j_begin, j_end; // truncated Arnoldi: steps [j_begin, j_end) of this launch
                       // sequence (j_end = 0: all d); step j forms b_{j+1}.
                       // j_begin > 0 resumes a build whose steps < j_begin ran
+  int pdl_resume;     // j_begin > 0: the previous node in the stream is the form
+                      // kernel of step j_begin - 1 (programmatic edge allowed)
+  int prio;           // launch priority of the basis kernels (0: the stream's)
   // Chebyshev basis (kind == SK_BASIS_CHEBYSHEV): B holds the recurrence's
   // vectors v_j (scaled by powers of two, not normalised); sigma[j] =
   // ||v_j||, and Hbar = H_v diag(1/sigma) so that S B Hbar = S A B diag(1/sigma)

@@ -260,9 +260,11 @@ struct SketchPlan {
 sk_status plan_create(SketchPlan* p, const sk_sketch* S, Scratch& scratch, cudaStream_t st);
 sk_status plan_apply(const SketchPlan& p, const void* B, int64_t ldb, int ncols, sk_dtype dtype,
                      double* SB, Scratch& scratch, cudaStream_t st);
-size_t plan_ws_doubles(const SketchPlan& p, int ncols, sk_dtype dtype);
+// block = true: a sketch of basis columns inside a solver (fixed grouping,
+// the same per-column summation order for any column count; see sketch.cu).
+size_t plan_ws_doubles(const SketchPlan& p, int ncols, sk_dtype dtype, bool block = false);
 sk_status plan_apply_ws(const SketchPlan& p, const void* B, int64_t ldb, int ncols, sk_dtype dtype, double* SB,
-                        double* partial, cudaStream_t st);
+                        double* partial, cudaStream_t st, bool block = false);
 sk_status check_plan_status(const SketchPlan& p, cudaStream_t st);
 int default_zeta_for(int d);
 
@@ -273,8 +275,8 @@ struct SrhtPlan {
   int32_t* rows = nullptr;        // s sampled Hadamard rows
 };
 sk_status srht_plan_create(SrhtPlan* p, const sk_sketch* S, Scratch& scratch, cudaStream_t st);
-size_t srht_ws_doubles(const SrhtPlan& p, int ncols);
+size_t srht_ws_doubles(const SrhtPlan& p, int ncols, bool block = false);
 sk_status srht_apply_ws(const SrhtPlan& p, const void* B, int64_t ldb, int ncols, sk_dtype dtype, double* SB,
-                        double* partial, cudaStream_t st);
+                        double* partial, cudaStream_t st, bool block = false);
 
 }  // namespace sk

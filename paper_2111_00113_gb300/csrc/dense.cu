@@ -373,16 +373,15 @@ qr_panel_cluster_kernel(double* __restrict__ Aug, int s, int p0, int nbc, double
   }
 }
 
-// Column c = c0 + blockIdx.x of Aug gets Q_p^T: a <- a - V T^T (V^T a).
-__global__ void __launch_bounds__(kQrTrailThreads)
-qr_trailing_kernel(double* __restrict__ Aug, int s, int p0, int nbc, int c0, const double* __restrict__ Tws) {
-  __shared__ double red[kQrTrailThreads / 32][kQrNb];
-  __shared__ double u[kQrNb];
-  __shared__ double w[kQrNb];
+// One column a (rows p0..s-1 used) gets Q_p^T of panel p: a <- a - V T^T
+// (V^T a), V = the panel's reflectors (columns p0.., rows from their
+// diagonal), T its compact-WY factor.  The whole CTA takes part; `red`, `u`
+// and `w` are its shared scratch.  Ends with every thread's writes to a
+// pending (the caller synchronises before re-reading a).
+__device__ __forceinline__ void wy_apply_column(double* __restrict__ a, const double* __restrict__ V, int s, int p0,
+                                                int nbc, const double* __restrict__ Tp,
+                                                double (*red)[kQrNb], double* u, double* w) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const int c = c0 + blockIdx.x;
-  double* a = Aug + (int64_t)c * s;
-  const double* V = Aug + (int64_t)p0 * s;
   double acc[kQrNb];
 #pragma unroll
   for (int i = 0; i < kQrNb; ++i) acc[i] = 0;
@@ -406,7 +405,7 @@ qr_trailing_kernel(double* __restrict__ Aug, int s, int p0, int nbc, int c0, con
     __syncwarp();
     if (lane < kQrNb) {
       double t = 0;
-      for (int l = 0; l <= lane && l < nbc; ++l) t += Tws[l * kQrNb + lane] * u[l];
+      for (int l = 0; l <= lane && l < nbc; ++l) t += Tp[l * kQrNb + lane] * u[l];
       w[lane] = (lane < nbc) ? t : 0.0;
     }
   }
@@ -421,8 +420,39 @@ qr_trailing_kernel(double* __restrict__ Aug, int s, int p0, int nbc, int c0, con
   }
 }
 
+// Column c = c0 + blockIdx.x of Aug gets Q_p^T: a <- a - V T^T (V^T a).
+__global__ void __launch_bounds__(kQrTrailThreads)
+qr_trailing_kernel(double* __restrict__ Aug, int s, int p0, int nbc, int c0, const double* __restrict__ Tws) {
+  __shared__ double red[kQrTrailThreads / 32][kQrNb];
+  __shared__ double u[kQrNb];
+  __shared__ double w[kQrNb];
+  const int c = c0 + blockIdx.x;
+  wy_apply_column(Aug + (int64_t)c * s, Aug + (int64_t)p0 * s, s, p0, nbc, Tws, red, u, w);
+}
+
+// Left-looking form of the trailing updates: column c = c0 + blockIdx.x
+// gets Q_{np-1}^T ... Q_0^T, the full panels 0..np-1 applied in order (the
+// per-panel arithmetic of qr_trailing_kernel, so a column ends bit-identical
+// to the right-looking factorisation).
+__global__ void __launch_bounds__(kQrTrailThreads)
+qr_left_kernel(double* __restrict__ Aug, int s, int np, int c0, const double* __restrict__ Tws) {
+  __shared__ double red[kQrTrailThreads / 32][kQrNb];
+  __shared__ double u[kQrNb];
+  __shared__ double w[kQrNb];
+  double* a = Aug + (int64_t)(c0 + blockIdx.x) * s;
+  for (int p = 0; p < np; ++p) {
+    __syncthreads();  // the previous panel's writes to a are visible to every thread
+    wy_apply_column(a, Aug + (int64_t)p * kQrNb * s, s, p * kQrNb, kQrNb, Tws + (int64_t)p * kQrNb * kQrNb, red, u,
+                    w);
+  }
+}
+
 // Factor panel [p0, p0+nbc) of Aug in place: the 8-CTA cluster kernel when
-// the panel is tall enough, else one CTA (shared or global memory).
+// the panel is tall enough, else one CTA (shared or global memory).  (One
+// CTA holding a 600 x 16 panel in registers was tried: slower, 2.9 against
+// 2.0 ms of QR per cycle, because one SM's FP64 pipe issues one warp
+// instruction per 16 cycles and the per-column products and reductions of
+// the whole panel then queue on it.)
 static sk_status factor_panel(double* Aug, int s, int p0, int nbc, double* rdiag, double* tau, double* T,
                               cudaStream_t st) {
   const int per = (s - p0 + kQrCluster - 1) / kQrCluster;
@@ -469,10 +499,10 @@ sk_status enqueue_qr(double* Aug, int s, int nq, int ncols, double* rdiag, doubl
 // Columns [c0, c1) joined a QR whose columns [0, c0) are factored (c0 a
 // multiple of the panel width) and whose column zc has received those
 // panels' reflectors.  Every earlier panel is applied to the new columns in
-// order (left-looking), then the new panels are factored, each applied to
-// the new columns right of it and to column zc.  Column by column this is
-// the arithmetic of enqueue_qr: the same reflectors, in the same order,
-// through the same per-column trailing kernel.  Returns the launch count
+// order (left-looking, one launch), then the new panels are factored, each
+// applied to the new columns right of it and to column zc.  Column by
+// column this is the arithmetic of enqueue_qr: the same reflectors, in the
+// same order, through the same per-column update.  Returns the launch count
 // through *launches.
 sk_status enqueue_qr_append(double* Aug, int s, int c0, int c1, int zc, double* rdiag, double* tau, double* Tws,
                             long long* launches, cudaStream_t st) {
@@ -481,9 +511,8 @@ sk_status enqueue_qr_append(double* Aug, int s, int c0, int c1, int zc, double* 
     return SK_EINVAL;
   }
   long long nl = 0;
-  for (int p0 = 0; p0 < c0; p0 += kQrNb) {
-    const double* T = Tws + (int64_t)(p0 / kQrNb) * kQrNb * kQrNb;
-    qr_trailing_kernel<<<c1 - c0, kQrTrailThreads, 0, st>>>(Aug, s, p0, kQrNb, c0, T);
+  if (c0 > 0) {
+    qr_left_kernel<<<c1 - c0, kQrTrailThreads, 0, st>>>(Aug, s, c0 / kQrNb, c0, Tws);
     ++nl;
   }
   for (int p0 = c0; p0 < c1; p0 += kQrNb) {

@@ -640,15 +640,27 @@ struct GatherShape {
   int W, ntiles, ngroups, cpg;
 };
 
-static GatherShape gather_shape(const SketchPlan& p, int ncols, sk_dtype dtype) {
+// block = a sketch of basis columns inside a solver: the chunk grouping is
+// fixed (kBlockGroups groups whatever the column count) and the kernel is
+// chosen by element type alone, so every column is summed in the same order
+// whether the basis is sketched whole or in blocks of columns.
+static constexpr int kBlockGroups = 64;
+
+static GatherShape gather_shape(const SketchPlan& p, int ncols, sk_dtype dtype, bool block) {
   GatherShape g;
   const size_t csize = dtype == SK_F64 ? 8 : 4;
   const int rows_w = kRowsBytes / (int)csize;
-  g.col = dtype == SK_F64 && ncols == 1 && p.s <= kRowsMaxS && 2 * col_buf_bytes(p.s, p.zeta) <= (size_t)kDynSmemLimit;
-  g.rows = !g.col && (dtype == SK_F32 || dtype == SK_F64) && p.s <= kRowsMaxS && ncols >= rows_w &&
+  g.col = !block && dtype == SK_F64 && ncols == 1 && p.s <= kRowsMaxS &&
+          2 * col_buf_bytes(p.s, p.zeta) <= (size_t)kDynSmemLimit;
+  g.rows = !g.col && (dtype == SK_F32 || dtype == SK_F64) && p.s <= kRowsMaxS && (ncols >= rows_w || block) &&
            2 * rows_buf_bytes(p.s, p.zeta) <= (size_t)kDynSmemLimit;
   g.W = g.col ? 1 : g.rows ? rows_w : pick_width(p.s, p.zeta, ncols, csize);
   g.ntiles = (ncols + g.W - 1) / g.W;
+  if (block) {
+    g.cpg = (p.nchunks + kBlockGroups - 1) / kBlockGroups;
+    g.ngroups = (p.nchunks + g.cpg - 1) / g.cpg;
+    return g;
+  }
   const int target = num_sms();
   int ngroups = (target + g.ntiles - 1) / g.ntiles;
   if (ngroups > p.nchunks) ngroups = p.nchunks;
@@ -671,14 +683,14 @@ static sk_status launch_rows(const SketchPlan& p, const T* B, int64_t ldb, int n
   return SK_OK;
 }
 
-size_t plan_ws_doubles(const SketchPlan& p, int ncols, sk_dtype dtype) {
-  const GatherShape g = gather_shape(p, ncols, dtype);
+size_t plan_ws_doubles(const SketchPlan& p, int ncols, sk_dtype dtype, bool block) {
+  const GatherShape g = gather_shape(p, ncols, dtype, block);
   return (size_t)g.ngroups * ncols * p.s;
 }
 
 sk_status plan_apply_ws(const SketchPlan& p, const void* B, int64_t ldb, int ncols, sk_dtype dtype, double* SB,
-                        double* partial, cudaStream_t st) {
-  const GatherShape g = gather_shape(p, ncols, dtype);
+                        double* partial, cudaStream_t st, bool block) {
+  const GatherShape g = gather_shape(p, ncols, dtype, block);
   sk_status stt;
   if (g.col) {
     const size_t smem = 2 * col_buf_bytes(p.s, p.zeta);

@@ -218,13 +218,15 @@ struct Sketcher {
     zeta = sp.zeta;
     return check_plan_status(sp, st);
   }
-  size_t ws(int ncols, sk_dtype dt) const {
-    return kind == SK_SRHT ? srht_ws_doubles(hp, ncols) : plan_ws_doubles(sp, ncols, dt);
+  // block = basis columns (a fixed summation order per column, whether the
+  // basis is sketched whole or in blocks); false for the residual
+  size_t ws(int ncols, sk_dtype dt, bool block) const {
+    return kind == SK_SRHT ? srht_ws_doubles(hp, ncols, block) : plan_ws_doubles(sp, ncols, dt, block);
   }
-  sk_status apply(const void* B, int64_t ldb, int ncols, sk_dtype dt, double* out, double* ws,
-                  cudaStream_t st) const {
-    if (kind == SK_SRHT) return srht_apply_ws(hp, B, ldb, ncols, dt, out, ws, st);
-    return plan_apply_ws(sp, B, ldb, ncols, dt, out, ws, st);
+  sk_status apply(const void* B, int64_t ldb, int ncols, sk_dtype dt, double* out, double* ws, cudaStream_t st,
+                  bool block) const {
+    if (kind == SK_SRHT) return srht_apply_ws(hp, B, ldb, ncols, dt, out, ws, st, block);
+    return plan_apply_ws(sp, B, ldb, ncols, dt, out, ws, st, block);
   }
 };
 
@@ -402,8 +404,8 @@ extern "C" sk_status trunc_arnoldi_basis(const sk_op* A, const double* r0, int d
     double* SBfull = nullptr;
     double* ws = nullptr;
     SK_TRY(sc.alloc(&SBfull, (size_t)S->s * (d + 1)));
-    SK_TRY(sc.alloc(&ws, sk.ws(d + 1, basis_dtype)));
-    SK_TRY(sk.apply(B, A->n, d + 1, basis_dtype, SBfull, ws, st));
+    SK_TRY(sc.alloc(&ws, sk.ws(d + 1, basis_dtype, true)));
+    SK_TRY(sk.apply(B, A->n, d + 1, basis_dtype, SBfull, ws, st, true));
     if (SB) SK_TRY(enqueue_copy_sb(SBfull, S->s, d, bb.bp.stop, SB, st));
     if (SAB) SK_TRY(enqueue_hbar_product(SBfull, bb.bp.Hbar, S->s, d, bb.hbar_k(), bb.bp.stop, SAB, st));
   }
@@ -441,6 +443,14 @@ struct SolveState {
   double* out;      // device: [rho2, rhat, kappa, width]
   double* h_out;    // pinned host copy (+ one int: the persistent kernel's error word)
   int* h_err;
+  // pipelined cycle: side stream for the sketch and QR of finished basis
+  // blocks, its fork/join events, one event per block, the basis priority
+  bool pipe;
+  cudaStream_t side, qrs;   // block sketches; QR panels
+  cudaEvent_t fork, join;
+  cudaEvent_t* blk;         // per block: basis columns formed (main), then sketched (side)
+  cudaEvent_t* skd;
+  int prio_hi;
 };
 
 static sk_status enqueue_residual(const SolveState& S, const OpView<double>& Av, const double* b, const double* x,
@@ -464,11 +474,11 @@ static sk_status mark(cudaEvent_t* ev, int which, cudaStream_t st, bool capturin
 static sk_status enqueue_cycle(SolveState& S, const sk_op* A, const OpView<double>& Av, const double* b, double* x,
                                cudaStream_t st, cudaEvent_t* ev, bool capturing) {
   SK_TRY(mark(ev, EV_START, st, capturing));
-  SK_TRY(S.sketch.apply(S.r, S.n, 1, SK_F64, S.g, S.ws_r, st));
+  SK_TRY(S.sketch.apply(S.r, S.n, 1, SK_F64, S.g, S.ws_r, st, false));
   SK_TRY(mark(ev, EV_G, st, capturing));
   SK_TRY(enqueue_basis_build(S.bb, A, st));
   SK_TRY(mark(ev, EV_BASIS, st, capturing));
-  SK_TRY(S.sketch.apply(S.bb.bp.B, S.bb.bp.ldb, S.d + 1, S.o.basis, S.SB, S.ws_B, st));
+  SK_TRY(S.sketch.apply(S.bb.bp.B, S.bb.bp.ldb, S.d + 1, S.o.basis, S.SB, S.ws_B, st, true));
   SK_TRY(mark(ev, EV_SB, st, capturing));
   SK_TRY(enqueue_hbar_product(S.SB, S.bb.bp.Hbar, S.s, S.d, S.bb.hbar_k(), S.bb.bp.stop, S.Aug, st));
   SK_CUDA(cudaMemcpyAsync(S.Aug + (size_t)S.d * S.s, S.g, sizeof(double) * S.s, cudaMemcpyDeviceToDevice, st));
@@ -489,6 +499,86 @@ static sk_status enqueue_cycle(SolveState& S, const sk_op* A, const OpView<doubl
   return SK_OK;
 }
 
+// One restart cycle in pipelined form.  The truncated-Arnoldi passes run on
+// `st` at raised priority, in blocks of kQrNb steps; after each block its
+// basis columns (still partly in L2) are sketched on the side stream, and
+// every panel of C = (S B_{d+1}) Hbar whose columns the sketched part of
+// B_{d+1} completes (column j needs b_0 .. b_{j+1}) joins the Householder
+// QR: the earlier panels' reflectors applied left-looking, the panel
+// factored, its reflectors applied to g = S r in column d.  The side work
+// overlaps the next blocks' basis passes, which are latency bound and leave
+// most of the GPU idle.  After the last block the streams join for the LS
+// solve, the update and the residual.  Column by column the arithmetic is
+// that of enqueue_cycle (same kernels, same order per column), so the two
+// forms give identical results.
+static sk_status enqueue_cycle_pipelined(SolveState& S, const sk_op* A, const OpView<double>& Av, const double* b,
+                                         double* x, cudaStream_t st, cudaEvent_t* ev, bool capturing) {
+  const int d = S.d, s = S.s;
+  const size_t esz = dtype_size(S.o.basis);
+  BasisParams& bp = S.bb.bp;
+  cudaStream_t sd = S.side, sq = S.qrs;
+  SK_TRY(mark(ev, EV_START, st, capturing));
+  SK_TRY(mark(ev, EV_G, st, capturing));
+  SK_CUDA(cudaEventRecord(S.fork, st));
+  SK_CUDA(cudaStreamWaitEvent(sq, S.fork, 0));
+  SK_TRY(S.sketch.apply(S.r, S.n, 1, SK_F64, S.g, S.ws_r, sq, false));
+  SK_CUDA(cudaMemcpyAsync(S.Aug + (size_t)d * s, S.g, sizeof(double) * s, cudaMemcpyDeviceToDevice, sq));
+  init_stop_kernel<<<1, 1, 0, st>>>(bp.stop, d + 1, bp.nanflag);
+  SK_CUDA(cudaMemsetAsync(bp.Hbar, 0, sizeof(double) * (size_t)(d + 1) * d, st));
+  const int nb = (d + 1 + kQrNb - 1) / kQrNb;
+  const int npanels = (d + kQrNb - 1) / kQrNb;
+  int panels = 0, prev = 0;
+  sk_status rs = SK_OK;
+  for (int t = 0; t < nb && rs == SK_OK; ++t) {
+    // main: steps [prev, je) form basis columns up to je
+    const int je = std::min(kQrNb * t + kQrNb - 1, d);
+    bp.j_begin = prev;
+    bp.j_end = je;
+    bp.pdl_resume = prev > 0;
+    bp.prio = S.prio_hi;
+    rs = enqueue_basis(bp, A, st);
+    prev = je;
+    if (rs != SK_OK) break;
+    SK_CUDA(cudaEventRecord(S.blk[t], st));
+    // side: sketch of the block's columns
+    SK_CUDA(cudaStreamWaitEvent(sd, S.blk[t], 0));
+    const int c0 = kQrNb * t, c1 = std::min(c0 + kQrNb, d + 1);
+    rs = S.sketch.apply((const unsigned char*)bp.B + (size_t)c0 * bp.ldb * esz, bp.ldb, c1 - c0, S.o.basis,
+                        S.SB + (size_t)c0 * s, S.ws_B, sd, true);
+    if (rs != SK_OK) break;
+    SK_CUDA(cudaEventRecord(S.skd[t], sd));
+    // QR stream: the panels this block completes
+    bool waited = false;
+    while (rs == SK_OK && panels < npanels && std::min(kQrNb * panels + kQrNb, d) <= c1 - 1) {
+      if (!waited) SK_CUDA(cudaStreamWaitEvent(sq, S.skd[t], 0));
+      waited = true;
+      const int q0 = kQrNb * panels, q1 = std::min(q0 + kQrNb, d);
+      rs = enqueue_hbar_product_cols(S.SB, bp.Hbar, s, d, S.bb.hbar_k(), bp.stop, q0, q1, S.Aug, sq);
+      if (rs == SK_OK) rs = enqueue_qr_append(S.Aug, s, q0, q1, d, S.rdiag, S.tau, S.Tws, nullptr, sq);
+      ++panels;
+    }
+  }
+  bp.j_begin = bp.j_end = 0;
+  bp.pdl_resume = 0;
+  bp.prio = 0;
+  SK_TRY(rs);
+  SK_TRY(mark(ev, EV_BASIS, st, capturing));
+  // the sketch stream's last block precedes the last panels on the QR stream
+  SK_CUDA(cudaStreamWaitEvent(sq, S.skd[nb - 1], 0));
+  SK_CUDA(cudaEventRecord(S.join, sq));
+  SK_CUDA(cudaStreamWaitEvent(st, S.join, 0));
+  SK_TRY(mark(ev, EV_SB, st, capturing));
+  SK_TRY(enqueue_ls_solve(S.Aug, S.rdiag, s, d, S.o.stab_tol, S.y, S.out + 1, st));
+  SK_TRY(mark(ev, EV_SMALL, st, capturing));
+  SK_TRY(enqueue_update(x, bp.B, bp.ldb, S.n, d, S.o.basis, S.y, S.out + 1, st));
+  SK_TRY(mark(ev, EV_UPDATE, st, capturing));
+  SK_TRY(enqueue_residual(S, Av, b, x, st));
+  SK_CUDA(cudaMemcpyAsync(S.out, bp.rho2, sizeof(double), cudaMemcpyDeviceToDevice, st));
+  SK_TRY(mark(ev, EV_RES, st, capturing));
+  SK_CUDA(cudaMemcpyAsync(S.h_out, S.out, 4 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  return SK_OK;
+}
+
 // One cycle of iterative sGMRES (§5.2; restart on kappa, §5.3).  The basis
 // grows o.iter_chunk columns at a time; after each chunk its new columns are
 // sketched, S A B's QR grows by them (enqueue_qr_append: the reflectors of
@@ -505,7 +595,7 @@ static sk_status run_iterative_cycle(SolveState& S, const sk_op* A, const OpView
   BasisParams& bp = S.bb.bp;
   long long nl = 0;
   SK_TRY(mark(ev, EV_START, st, false));
-  SK_TRY(S.sketch.apply(S.r, S.n, 1, SK_F64, S.g, S.ws_r, st));
+  SK_TRY(S.sketch.apply(S.r, S.n, 1, SK_F64, S.g, S.ws_r, st, false));
   nl += 2;
   SK_TRY(mark(ev, EV_G, st, false));
   init_stop_kernel<<<1, 1, 0, st>>>(bp.stop, d + 1, bp.nanflag);
@@ -525,7 +615,7 @@ static sk_status run_iterative_cycle(SolveState& S, const sk_op* A, const OpView
     // the chunk's new basis columns: b_{c0+1} .. b_{c1} (0-based), and b_0 first
     const int s0 = c0 == 0 ? 0 : c0 + 1;
     SK_TRY(S.sketch.apply((const unsigned char*)bp.B + (size_t)s0 * bp.ldb * esz, bp.ldb, c1 + 1 - s0, S.o.basis,
-                          S.SB + (size_t)s0 * s, S.ws_B, st));
+                          S.SB + (size_t)s0 * s, S.ws_B, st, true));
     nl += 2;
     SK_TRY(enqueue_hbar_product_cols(S.SB, bp.Hbar, s, d, S.bb.hbar_k(), bp.stop, c0, c1, S.Aug, st));
     ++nl;
@@ -605,6 +695,41 @@ static sk_status sgmres_impl(const sk_op* A, const double* b, double* x, int d, 
   Scratch sc(st);
   SK_TRY(S.bb.alloc(S.n, d, k, S.o.basis, S.o.cgs_passes, S.o.breakdown, sc, nullptr, A, S.o.persistent != 0));
   SK_TRY(S.bb.set_kind(S.o, sc));
+  // the pipelined cycle: captured truncated-Arnoldi cycles of the 3-launch basis
+  S.pipe = S.o.pipeline != 0 && S.o.use_graph && !iter && !S.bb.cheb() && !S.bb.persistent;
+  struct PipeFree {
+    SolveState* S;
+    ~PipeFree() {
+      if (S->side) cudaStreamDestroy(S->side);
+      if (S->qrs) cudaStreamDestroy(S->qrs);
+      if (S->fork) cudaEventDestroy(S->fork);
+      if (S->join) cudaEventDestroy(S->join);
+      const int nb = (S->d + 1 + kQrNb - 1) / kQrNb;
+      for (cudaEvent_t* e : {S->blk, S->skd}) {
+        if (!e) continue;
+        for (int t = 0; t < nb; ++t)
+          if (e[t]) cudaEventDestroy(e[t]);
+        delete[] e;
+      }
+    }
+  } pf{&S};
+  if (S.pipe) {
+    int least = 0, greatest = 0;
+    SK_CUDA(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+    S.prio_hi = greatest;
+    SK_CUDA(cudaStreamCreateWithPriority(&S.side, cudaStreamNonBlocking, least));
+    SK_CUDA(cudaStreamCreateWithPriority(&S.qrs, cudaStreamNonBlocking, least));
+    SK_CUDA(cudaEventCreateWithFlags(&S.fork, cudaEventDisableTiming));
+    SK_CUDA(cudaEventCreateWithFlags(&S.join, cudaEventDisableTiming));
+    const int nb = (d + 1 + kQrNb - 1) / kQrNb;
+    S.blk = new cudaEvent_t[nb];
+    S.skd = new cudaEvent_t[nb];
+    for (int t = 0; t < nb; ++t) S.blk[t] = S.skd[t] = nullptr;
+    for (int t = 0; t < nb; ++t) {
+      SK_CUDA(cudaEventCreateWithFlags(&S.blk[t], cudaEventDisableTiming));
+      SK_CUDA(cudaEventCreateWithFlags(&S.skd[t], cudaEventDisableTiming));
+    }
+  }
   sk_sketch sks;
   sks.kind = S.o.sketch;
   sks.n = S.n;
@@ -621,15 +746,16 @@ static sk_status sgmres_impl(const sk_op* A, const double* b, double* x, int d, 
   SK_TRY(sc.alloc(&S.tau, d));
   SK_TRY(sc.alloc(&S.Tws, (size_t)((d + kQrNb - 1) / kQrNb) * kQrNb * kQrNb));
   SK_TRY(sc.alloc(&S.y, d));
-  SK_TRY(sc.alloc(&S.ws_r, S.sketch.ws(1, SK_F64)));
+  SK_TRY(sc.alloc(&S.ws_r, S.sketch.ws(1, SK_F64, false)));
   {
     // iterative cycles sketch 1..iter_chunk+1 columns at a time: room for
     // the largest of those shapes too
-    size_t wsb = S.sketch.ws(d + 1, S.o.basis);
+    size_t wsb = S.sketch.ws(d + 1, S.o.basis, true);
     for (int c = 1; iter && c <= S.o.iter_chunk + 1 && c <= d + 1; ++c) {
-      const size_t w = S.sketch.ws(c, S.o.basis);
+      const size_t w = S.sketch.ws(c, S.o.basis, true);
       if (w > wsb) wsb = w;
     }
+
     SK_TRY(sc.alloc(&S.ws_B, wsb));
   }
   int* chk = nullptr;
@@ -706,7 +832,8 @@ static sk_status sgmres_impl(const sk_op* A, const double* b, double* x, int d, 
       SK_CUDA(cudaStreamSynchronize(st));
     }
     SK_CUDA(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
-    sk_status cs = enqueue_cycle(S, A, Av, b, x, cap, ev, true);
+    sk_status cs = S.pipe ? enqueue_cycle_pipelined(S, A, Av, b, x, cap, ev, true)
+                          : enqueue_cycle(S, A, Av, b, x, cap, ev, true);
     cudaError_t ce = cudaStreamEndCapture(cap, &graph);
     if (cs != SK_OK) { if (own) cudaStreamDestroy(own); return cs; }
     if (ce != cudaSuccess) { if (own) cudaStreamDestroy(own); return cuda_fail(ce, "cudaStreamEndCapture"); }
@@ -1090,7 +1217,7 @@ extern "C" sk_status srr_eigs(const sk_op* A, const double* w1, int nev, int d, 
   double *SB, *ws, *Aug, *rdiag, *tau, *Tws, *Mhat, *etau, *wr, *wi, *Wre, *Wim, *Yre, *Yim, *res, *part;
   int *sel, *estat;
   SK_TRY(sc.alloc(&SB, (size_t)s * (d + 1)));
-  SK_TRY(sc.alloc(&ws, skt.ws(d + 1, o.basis)));
+  SK_TRY(sc.alloc(&ws, skt.ws(d + 1, o.basis, true)));
   SK_TRY(sc.alloc(&Aug, (size_t)s * 2 * d));
   SK_TRY(sc.alloc(&rdiag, d));
   SK_TRY(sc.alloc(&tau, d));
@@ -1108,7 +1235,7 @@ extern "C" sk_status srr_eigs(const sk_op* A, const double* w1, int nev, int d, 
   SK_TRY(sc.alloc(&estat, 1));
   SK_CUDA(cudaMemsetAsync(estat, 0, sizeof(int), st));
   // C = S B (columns 0..d-1), D = S A B = (S B_{d+1}) Hbar; QR of C, Q^T applied to D
-  SK_TRY(skt.apply(bb.bp.B, bb.bp.ldb, d + 1, o.basis, SB, ws, st));
+  SK_TRY(skt.apply(bb.bp.B, bb.bp.ldb, d + 1, o.basis, SB, ws, st, true));
   SK_TRY(enqueue_copy_sb(SB, s, d, bb.bp.stop, Aug, st));
   SK_TRY(enqueue_hbar_product(SB, bb.bp.Hbar, s, d, k, bb.bp.stop, Aug + (size_t)s * d, st));
   SK_TRY(enqueue_qr(Aug, s, d, 2 * d, rdiag, tau, Tws, st));

@@ -126,10 +126,16 @@ static sk_status srht_launch(const SrhtPlan& p, const T* B, int64_t ldb, int nco
   return SK_OK;
 }
 
-static void srht_shape(const SrhtPlan& p, int ncols, int* ngroups_out, int* bpg_out, int* data_blocks_out) {
+// block = a sketch of basis columns inside a solver: a fixed number of
+// groups per column, so each column's sum has the same order whatever the
+// column count.
+static constexpr int kSrhtBlockGroups = 16;
+
+static void srht_shape(const SrhtPlan& p, int ncols, bool block, int* ngroups_out, int* bpg_out,
+                       int* data_blocks_out) {
   const int data_blocks = (int)((p.n + (1ll << p.b) - 1) >> p.b);
   const int target = 2 * num_sms();
-  int ngroups = (target + ncols - 1) / ncols;
+  int ngroups = block ? kSrhtBlockGroups : (target + ncols - 1) / ncols;
   if (ngroups > data_blocks) ngroups = data_blocks;
   if (ngroups < 1) ngroups = 1;
   const int bpg = (data_blocks + ngroups - 1) / ngroups;
@@ -163,16 +169,16 @@ sk_status srht_plan_create(SrhtPlan* p, const sk_sketch* S, Scratch& scratch, cu
   return SK_OK;
 }
 
-size_t srht_ws_doubles(const SrhtPlan& p, int ncols) {
+size_t srht_ws_doubles(const SrhtPlan& p, int ncols, bool block) {
   int ngroups, bpg, db;
-  srht_shape(p, ncols, &ngroups, &bpg, &db);
+  srht_shape(p, ncols, block, &ngroups, &bpg, &db);
   return (size_t)ngroups * ncols * p.s;
 }
 
 sk_status srht_apply_ws(const SrhtPlan& p, const void* B, int64_t ldb, int ncols, sk_dtype dtype, double* SB,
-                        double* partial, cudaStream_t st) {
+                        double* partial, cudaStream_t st, bool block) {
   int ngroups, bpg, data_blocks;
-  srht_shape(p, ncols, &ngroups, &bpg, &data_blocks);
+  srht_shape(p, ncols, block, &ngroups, &bpg, &data_blocks);
   sk_status stt;
   if (dtype == SK_F64) stt = srht_launch<double>(p, (const double*)B, ldb, ncols, partial, ngroups, bpg, data_blocks, st);
   else if (dtype == SK_F32) stt = srht_launch<float>(p, (const float*)B, ldb, ncols, partial, ngroups, bpg, data_blocks, st);

@@ -79,6 +79,29 @@ def test_graph_and_eager_agree(skg):
     assert torch.allclose(xg, xe, rtol=0, atol=1e-12 * xg.abs().max().item())
 
 
+@pytest.mark.parametrize("dtype,kind,d", [("f64", "sparse", 47), ("f32", "sparse", 75), ("f32", "sparse", 16),
+                                          ("bf16", "sparse", 40), ("f64", "srht", 33), ("f32", "sparse", 15)])
+def test_pipelined_cycle_equals_sequential(skg, dtype, kind, d):
+    # the pipelined cycle (each finished block of 16 basis columns sketched
+    # and added to the QR on a second stream while the basis passes go on)
+    # performs per column the arithmetic of the one-phase-after-another
+    # cycle: the iterates agree bit for bit after every cycle.  Sizes cover a
+    # last block of 1 column (d = 16), d < 16, and ragged panels.
+    import torch
+    N = 96
+    coef, A, f = _problem(N, 30.0, 12)
+    op = skg.Op.stencil5(N, N, coef)
+    b = torch.tensor(f, device="cuda")
+    tdt = {"f64": torch.float64, "f32": torch.float32, "bf16": torch.bfloat16}[dtype]
+    kw = dict(basis=tdt, sketch=kind, zeta=hashing.default_zeta(d), seed=5)
+    xp = xs = None
+    for c in range(3):
+        xp, ip = skg.sgmres_solve(op, b, d, 2, 2 * d, 1e-300, x0=xp, maxit=1, pipeline=True, **kw)
+        xs, is_ = skg.sgmres_solve(op, b, d, 2, 2 * d, 1e-300, x0=xs, maxit=1, pipeline=False, **kw)
+        assert torch.equal(xp, xs), (c, float((xp - xs).abs().max()))
+        assert ip["relres"] == is_["relres"]
+
+
 def test_initial_guess_and_zero_rhs(skg):
     import torch
     N = 32
