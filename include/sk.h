@@ -182,6 +182,12 @@ typedef struct {
                               solve uses exactly that prefix.  A positive multiple of 16, at most
                               1024; truncated-Arnoldi basis only (SK_EINVAL otherwise); no CUDA
                               graph and no persistent kernel; the host reads one flag per chunk */
+  double srr_trunc_tol;    /* sRR (srr_eigs, srr_basis, srr_restarted): <= 0 (default) = Algorithm 2's
+                              reduction (QR of S B, M-hat = T^{-1} U^T S A B); > 0 = the stabilized
+                              form of §6.5 eq. (qz): thin SVD S B = U Sigma V^T (column-pivoted
+                              Householder QR, then one-sided Jacobi on R^T), keeping the singular
+                              values with sigma_1 / sigma_i <= srr_trunc_tol, and the eigenproblem
+                              (U_r^T S A B V_r) z = theta Sigma_r z */
   int pipeline;            /* sgmres_solve with a captured cycle (use_graph), the truncated-Arnoldi
                               basis and 3 launches per step: 1 (default) = sketch each finished
                               block of 16 basis columns and add the panels it completes to the QR
@@ -271,6 +277,44 @@ sk_status sgmres_solve_batched(int nsys, const sk_op* const* A, int nrhs, const 
 sk_status srr_eigs(const sk_op* A, const double* w1, int nev, int d, int k, int s, const sk_opts* opts,
                    double* lam_re, double* lam_im, double* X_re, double* X_im, double* rhat,
                    int* nconv, sk_info* info, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Sketched Rayleigh-Ritz on a caller's basis (§6.3: sRR needs only a basis
+ * B and the products A B; §6.5 for the stabilized form).
+ *   B: device n x d, column-major, leading dimension ldb >= n, `dtype`; A B
+ *   is formed column by column on the GPU (FP64).  s >= d sketch rows; opts:
+ *   sketch kind/zeta/seed, tau, symmetric, srr_trunc_tol (> 0: stabilized).
+ *   Outputs as srr_eigs; rank (host int or NULL): the singular values the
+ *   stabilized form kept (d for Algorithm 2).  3 <= d <= 232, nev <= 32.
+ *   SK_EILLCOND if the stabilized form keeps fewer than max(3, nev).
+ * ------------------------------------------------------------------------ */
+sk_status srr_basis(const sk_op* A, const void* B, int64_t ldb, int d, sk_dtype dtype, int nev, int s,
+                    const sk_opts* opts, double* lam_re, double* lam_im, double* X_re, double* X_im,
+                    double* rhat, int* nconv, int* rank, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Restarted sRR (§7.2) on block Chebyshev bases (§7.5).  The paper leaves
+ * the restart strategy open; this library restarts from the Krylov space of
+ * the current Ritz vectors, built by the block Chebyshev recurrence for the
+ * unwanted part of the real spectrum, as follows.  X_0 = Omega (device,
+ * n x b FP64).  Restart t: Q = orth(X_t); B_0 = Q, B_1 = (A - c) B_0 / (2 rho),
+ * B_j = ((A - c) B_{j-1} - (rho/4) B_{j-2}) / rho for the interval [lo, cut_t]
+ * (c its centre, rho its half-width; cut_0 = hi, then the real part of the
+ * b-th Ritz value of restart t-1); the d = b p columns of B_0..B_{p-1}
+ * scaled to unit norm; the stabilized sRR of §6.5 (srr_trunc_tol, default
+ * 1e13 here) with a fresh sparse sketch (seed opts->seed + t, s = 2d); X_{t+1}
+ * = the real parts, then the imaginary parts, of the b leading Ritz vectors
+ * (the first b with norm > 1e-10).  Stops when the nev leading residual
+ * estimates are <= opts->tau, or after max_restarts.
+ *   1 <= nev <= b <= 32, 3 <= b p <= 232, lo < hi (lo below the spectrum).
+ *   Outputs: the nev leading pairs of the last restart (as srr_eigs);
+ *   restarts (host int): restarts run; history (host, max_restarts doubles or
+ *   NULL): each restart's largest estimate over the nev leading pairs.
+ *   Returns SK_OK when all nev estimates are <= tau, else SK_ENOCONV.
+ * ------------------------------------------------------------------------ */
+sk_status srr_restarted(const sk_op* A, const double* Omega, int b, int p, int nev, double lo, double hi,
+                        int max_restarts, const sk_opts* opts, double* lam_re, double* lam_im, double* X_re,
+                        double* X_im, double* rhat, int* nconv, int* restarts, double* history, void* stream);
 
 const char* sk_last_error(void);
 const char* sk_status_string(sk_status st);

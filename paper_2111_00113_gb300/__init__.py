@@ -173,7 +173,7 @@ def sketch_apply_noalloc(B, s, zeta=0, seed=7):
 
 def make_opts(basis=torch.float64, sketch="sparse", zeta=0, seed=7, stab_tol=0.0, maxit=10000, cgs_passes=2,
               tau=1e-8, symmetric=False, breakdown=0.0, use_graph=True, persistent=False, batch_workers=0,
-              cheb=None, barrier_spins=0, iter_chunk=0, pipeline=True):
+              cheb=None, barrier_spins=0, iter_chunk=0, pipeline=True, trunc_tol=0.0):
     """Solver options.  cheb=(c, dx, dy) selects the Chebyshev basis (§4.3)
     for a spectrum inside [c - dx, c + dx] x [-dy, dy].  iter_chunk > 0
     selects iterative sGMRES (§5.2): the cycle grows the basis iter_chunk
@@ -199,6 +199,7 @@ def make_opts(basis=torch.float64, sketch="sparse", zeta=0, seed=7, stab_tol=0.0
     o.barrier_spins = int(barrier_spins)
     o.iter_chunk = int(iter_chunk)
     o.pipeline = int(bool(pipeline))
+    o.srr_trunc_tol = float(trunc_tol)
     if cheb is not None:
         o.basis_kind = 1
         o.cheb_c, o.cheb_dx, o.cheb_dy = (float(v) for v in cheb)
@@ -313,6 +314,52 @@ def srr_eigs(A, w1, nev, d, k, s, **opts):
     lam = torch.tensor([complex(a, b) for a, b in zip(lre, lim)], dtype=torch.complex128)
     return dict(lam=lam, X=torch.complex(Xr, Xi), rhat=torch.tensor(list(rh)), nconv=nconv.value,
                 info=info.as_dict())
+
+
+def srr_basis(A, B, nev, s, **opts):
+    """Sketched Rayleigh-Ritz on a given basis B (n x d CUDA tensor, float64/
+    float32/bfloat16): A B is formed on the GPU, then Algorithm 2's reduction,
+    or the stabilized form of §6.5 with opts trunc_tol > 0.  Returns
+    dict(lam, X, rhat, nconv, rank)."""
+    Bc = colmajor(B)
+    if Bc.dtype not in _DT:
+        raise ValueError("dtype must be float64, float32 or bfloat16")
+    n, d = Bc.shape
+    o = make_opts(**opts)
+    lre = (C.c_double * nev)()
+    lim = (C.c_double * nev)()
+    rh = (C.c_double * nev)()
+    Xr = empty_colmajor(n, nev, torch.float64, Bc.device)
+    Xi = empty_colmajor(n, nev, torch.float64, Bc.device)
+    nconv = C.c_int(0)
+    rank = C.c_int(0)
+    N.check(N.lib.srr_basis(A._h, _ptr(Bc), Bc.stride(1) if d > 1 else n, d, _DT[Bc.dtype], nev, s, C.byref(o),
+                            lre, lim, _ptr(Xr), _ptr(Xi), rh, C.byref(nconv), C.byref(rank), _stream()))
+    lam = torch.tensor([complex(a, b) for a, b in zip(lre, lim)], dtype=torch.complex128)
+    return dict(lam=lam, X=torch.complex(Xr, Xi), rhat=torch.tensor(list(rh)), nconv=nconv.value, rank=rank.value)
+
+
+def srr_restarted(A, Omega, p, nev, lo, hi, max_restarts, **opts):
+    """Restarted sRR (§7.2) on block Chebyshev bases (§7.5) from the start
+    block Omega (n x b, float64); [lo, hi] brackets the real spectrum.
+    Returns dict(lam, X, rhat, nconv, restarts, history, status)."""
+    Om = colmajor(_dev_f64(Omega) if Omega.dim() == 1 else Omega.to(torch.float64))
+    n, b = Om.shape
+    o = make_opts(**opts)
+    lre = (C.c_double * nev)()
+    lim = (C.c_double * nev)()
+    rh = (C.c_double * nev)()
+    hist = (C.c_double * max_restarts)()
+    Xr = empty_colmajor(n, nev, torch.float64, Om.device)
+    Xi = empty_colmajor(n, nev, torch.float64, Om.device)
+    nconv = C.c_int(0)
+    nres = C.c_int(0)
+    st = N.check(N.lib.srr_restarted(A._h, _ptr(Om), b, p, nev, float(lo), float(hi), max_restarts, C.byref(o), lre,
+                                     lim, _ptr(Xr), _ptr(Xi), rh, C.byref(nconv), C.byref(nres), hist, _stream()),
+                 allow=(N.SK_OK, N.SK_ENOCONV))
+    lam = torch.tensor([complex(a, b) for a, b in zip(lre, lim)], dtype=torch.complex128)
+    return dict(lam=lam, X=torch.complex(Xr, Xi), rhat=torch.tensor(list(rh)), nconv=nconv.value,
+                restarts=nres.value, history=list(hist)[:nres.value], status=st)
 
 
 def _adjoint(op, x, gx, d, k, s, tol, opts):

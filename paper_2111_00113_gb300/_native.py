@@ -17,7 +17,7 @@ SK_SPARSE_SIGN, SK_SRHT = 0, 1
 EXPORTED = [
     "sk_op_stencil5", "sk_op_diffusion_var", "sk_op_csr", "sk_op_transpose", "sk_op_apply", "sk_op_n",
     "sk_op_destroy", "sketch_apply", "sketch_apply_noalloc", "sk_opts_default", "trunc_arnoldi_basis", "sgmres_solve", "srr_eigs",
-    "sk_last_error", "sk_status_string", "sk_op_param_grad", "sgmres_solve_batched",
+    "sk_last_error", "sk_status_string", "sk_op_param_grad", "sgmres_solve_batched", "srr_basis", "srr_restarted",
 ]
 
 
@@ -31,7 +31,8 @@ class SkOpts(C.Structure):
         ("maxit", C.c_int), ("basis", C.c_int), ("cgs_passes", C.c_int), ("tau", C.c_double),
         ("symmetric", C.c_int), ("breakdown", C.c_double), ("use_graph", C.c_int), ("persistent", C.c_int),
         ("batch_workers", C.c_int), ("basis_kind", C.c_int), ("cheb_c", C.c_double), ("cheb_dx", C.c_double),
-        ("cheb_dy", C.c_double), ("barrier_spins", C.c_int), ("iter_chunk", C.c_int), ("pipeline", C.c_int),
+        ("cheb_dy", C.c_double), ("barrier_spins", C.c_int), ("iter_chunk", C.c_int), ("srr_trunc_tol", C.c_double),
+        ("pipeline", C.c_int),
     ]
 
 
@@ -76,6 +77,10 @@ def _load():
                                       C.POINTER(SkInfo), P]),
         "srr_eigs": (st, [P, P, I, I, I, I, C.POINTER(SkOpts), C.POINTER(D), C.POINTER(D), P, P,
                           C.POINTER(D), C.POINTER(I), C.POINTER(SkInfo), P]),
+        "srr_basis": (st, [P, P, I64, I, I, I, I, C.POINTER(SkOpts), C.POINTER(D), C.POINTER(D), P, P,
+                           C.POINTER(D), C.POINTER(I), C.POINTER(I), P]),
+        "srr_restarted": (st, [P, P, I, I, I, D, D, I, C.POINTER(SkOpts), C.POINTER(D), C.POINTER(D), P, P,
+                               C.POINTER(D), C.POINTER(I), C.POINTER(I), C.POINTER(D), P]),
         "sk_last_error": (C.c_char_p, []),
         "sk_status_string": (C.c_char_p, [I]),
     }

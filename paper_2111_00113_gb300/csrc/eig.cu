@@ -1,15 +1,12 @@
 // Dense nonsymmetric eigensolver for the sketched Rayleigh-Ritz matrix
-// M-hat (d x d, FP64, d <= 256): Algorithm 2's "solve eigenvalue problem"
+// M-hat (d x d, FP64, d <= 232): Algorithm 2's "solve eigenvalue problem"
 // step, written for one GPU.
 //
 //   1. Householder reduction to upper Hessenberg form H = P^T M P (one CTA;
 //      reflectors kept below the subdiagonal).
-//   2. Eigenvalues of H by the implicitly shifted double-shift (Francis) QR
-//      iteration with deflation on small subdiagonals and exceptional shifts
-//      (Golub & Van Loan §7.5), eigenvalues only; H lives in shared memory in
-//      a packed band-upper layout (row i keeps columns >= i-3, which holds
-//      the bulge); each 3x3 reflector's row and column updates are spread over
-//      the CTA's threads.
+//   2. Eigenvalues of H by the implicit double-shift QR iteration (Golub &
+//      Van Loan, Algorithms 7.5.1 and 7.5.2), eigenvalues only, run by one
+//      warp on H packed by columns in shared memory (francis_kernel).
 //   3. Eigenvectors for the selected eigenvalues by inverse iteration on the
 //      Hessenberg matrix, (H - lambda I) y = y_prev in complex arithmetic with
 //      partial pivoting between adjacent rows (one CTA per eigenvalue), then
@@ -20,7 +17,7 @@
 
 namespace sk {
 
-static constexpr int kEigMaxN = 256;
+static constexpr int kEigMaxN = 256;  // per-CTA work arrays of the reduction and inverse iteration
 static constexpr int kEigThreads = 256;
 
 __device__ __forceinline__ double block_sum_d(double v, double* sh) {
@@ -97,209 +94,293 @@ hessenberg_kernel(double* __restrict__ H, int n, double* __restrict__ tau) {
   }
 }
 
-// ---- 2. Francis double-shift QR, eigenvalues only ------------------------------------
-struct Band {
+// ---- 2. Eigenvalues of H by the implicit double-shift QR iteration ---------------------
+// Written from the description of the Francis QR step and of the practical
+// QR algorithm in Golub & Van Loan, "Matrix Computations" (4th ed.),
+// Algorithms 7.5.1 and 7.5.2: the shifts are the two eigenvalues of the
+// trailing 2 x 2 block of the active window, entered implicitly through the
+// first column of (H - a I)(H - b I) = H^2 - s H + t I (s = a + b, t = a b),
+// and the bulge they create is chased down the subdiagonal with 3 x 3
+// Householder reflectors; a subdiagonal entry below eps (|h_{l,l}| +
+// |h_{l-1,l-1}|) is set to zero and splits the problem; 1 x 1 and 2 x 2
+// blocks at the bottom of the window give eigenvalues.  Eigenvalues only:
+// the reflectors touch the active window's rows and columns, nothing else.
+//
+// One CTA does the whole iteration (the work split is described at
+// francis_kernel).  H lives in shared memory, packed by columns: column j
+// keeps rows 0 .. min(j + 3, n - 1), which holds the Hessenberg part and the
+// bulge.
+static constexpr int kFrancisMaxN = 232;  // packed storage of n = 232 fills 221.7 KB
+
+__host__ __device__ inline int francis_col_len(int j, int n) { return (j + 4 < n) ? j + 4 : n; }
+
+size_t francis_smem_bytes(int n) {
+  size_t o = 0;
+  for (int j = 0; j < n; ++j) o += (size_t)francis_col_len(j, n);
+  return o * sizeof(double) + (size_t)(n + 1) * sizeof(int);
+}
+
+struct PackedH {
   double* a;
   const int* off;
-  __device__ __forceinline__ double& at(int i, int j) const { return a[off[i] + j - max(0, i - 3)]; }
+  __device__ __forceinline__ double& at(int i, int j) const { return a[off[j] + i]; }
 };
 
-__global__ void __launch_bounds__(kEigThreads)
-hqr_kernel(const double* __restrict__ Hg, const double* __restrict__ tau, int n, double* __restrict__ wr,
-           double* __restrict__ wi, int* __restrict__ status) {
-  extern __shared__ double sm[];
-  __shared__ int off[kEigMaxN + 1];
-  __shared__ double sh[32];
-  __shared__ int s_l, s_m;
-  __shared__ double s_shift[3];  // x, y, w of the shift polynomial
-  __shared__ double s_ref[6];    // the current 3x3 reflector (vx, vy, vz, q2, r2) and a non-zero flag
-  if (threadIdx.x == 0) {
+// Householder reflector for (x, y, z): v = (x - alpha, y, z) with alpha =
+// -sign(x) ||(x, y, z)||, returned scaled so that the reflector is I - v v^T
+// (v^T v = 2); v = 0 (the identity) for a zero vector.  The input is scaled
+// by a power of two (exact, from the exponent bits) so that squaring neither
+// overflows nor underflows.  Branch-free, so the compiler can interleave
+// this dependent FP64 chain with independent updates.
+__device__ __forceinline__ void house3(double x, double y, double z, double& alpha, double& v0, double& v1,
+                                       double& v2) {
+  const double m = fmax(fabs(x), fmax(fabs(y), fabs(z)));
+  int ex = (int)((__double_as_longlong(m) >> 52) & 0x7ff);
+  ex = min(max(ex, 1), 2045);
+  const double sc = __longlong_as_double((long long)(2046 - ex) << 52);  // 2^(1023 - ex)
+  const double isc = __longlong_as_double((long long)ex << 52);          // 2^(ex - 1023)
+  const double xs = x * sc, ys = y * sc, zs = z * sc;
+  const double nrm = sqrt(xs * xs + ys * ys + zs * zs);
+  const double as = (xs >= 0.0) ? -nrm : nrm;
+  const bool nz = m > 0.0;
+  // w = (xs - as, ys, zs), w^T w = 2 nrm (nrm + |xs|); v = w sqrt(2 / w^T w)
+  const double f = nz ? rsqrt(nrm * (nrm + fabs(xs))) : 0.0;
+  alpha = as * isc;
+  v0 = (xs - as) * f;
+  v1 = ys * f;
+  v2 = zs * f;
+}
+
+// One CTA of kFrancisWarps warps; warp 0 is the chain warp.  Each SM
+// sub-partition has its own FP64 unit (on this GPU a warp's FP64
+// instruction issues once per 64 cycles on its sub-partition), so the far
+// updates of a bulge step go to the other warps, in parallel with warp 0's
+// near updates and the next reflector's dependent chain.  Bulge step k, with
+// reflector k acting on rows k..k+2 and columns k..k+2:
+//   near(k), warp 0: rows k..k+2 of columns c0..k+3 (c0 = k, or lo for the
+//     first step), then rows k..k+3 of columns k..k+2; then reflector k+1
+//     from rows k+1..k+3 of column k;
+//   far(k), other warps: rows k..k+2 of columns k+4..hi, rows lo..k-1 of
+//     columns k..k+2.
+// near(k) and far(k) touch disjoint entries, far(k) reads nothing near(k)
+// writes, and near(k) reads far(k-1)'s results only after the barrier that
+// opens step k, so every entry sees the updates of the plain
+// row-then-column order, in that order.
+static constexpr int kFrancisWarps = 4;
+static constexpr int kFrancisThreads = 32 * kFrancisWarps;
+
+__global__ void __launch_bounds__(kFrancisThreads)
+francis_kernel(const double* __restrict__ Hg, const double* __restrict__ tau, int n, double* __restrict__ wr,
+               double* __restrict__ wi, int* __restrict__ status) {
+  extern __shared__ __align__(16) unsigned char fr_smem[];
+  __shared__ double s_ref[2][4];  // reflector (alpha, v0, v1, v2) of steps of each parity
+  __shared__ double s_norm[kFrancisWarps];
+  __shared__ int s_lo;
+  int* off = reinterpret_cast<int*>(fr_smem);
+  double* a = reinterpret_cast<double*>(fr_smem + (((size_t)(n + 1) * sizeof(int) + 15) & ~(size_t)15));
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int ftid = tid - 32, nft = kFrancisThreads - 32;  // far threads
+  const unsigned full = 0xffffffffu;
+  if (tid == 0) {
     int o = 0;
-    for (int i = 0; i < n; ++i) { off[i] = o; o += n - max(0, i - 3); }
+    for (int j = 0; j < n; ++j) { off[j] = o; o += francis_col_len(j, n); }
     off[n] = o;
   }
   __syncthreads();
-  Band A{sm, off};
-  // copy the Hessenberg part (subdiagonal from tau[n+k]); zeros below it
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    for (int j = max(0, i - 3); j < n; ++j) {
+  const PackedH H{a, off};
+  // the Hessenberg matrix (subdiagonal from tau[n + j]), zero below it
+  double nrm_part = 0;
+  for (int j = tid; j < n; j += kFrancisThreads) {
+    const int len = francis_col_len(j, n);
+    for (int i = 0; i < len; ++i) {
       double v = 0;
-      if (j >= i) v = Hg[i + (int64_t)j * n];
-      else if (j == i - 1) v = (j + 2 < n) ? tau[n + j] : Hg[i + (int64_t)j * n];
-      A.at(i, j) = v;
+      if (i <= j) v = Hg[i + (int64_t)j * n];
+      else if (i == j + 1) v = (j + 2 < n) ? tau[n + j] : Hg[i + (int64_t)j * n];
+      H.at(i, j) = v;
+      nrm_part += fabs(v);
     }
   }
+  nrm_part = warp_sum(nrm_part);
+  if (lane == 0) s_norm[warp] = nrm_part;
   __syncthreads();
-  double anorm_part = 0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x)
-    for (int j = max(0, i - 1); j < n; ++j) anorm_part += fabs(A.at(i, j));
-  const double anorm = block_sum_d(anorm_part, sh);
-  int nn = n - 1;
-  double tsum = 0;  // accumulated exceptional shifts
-  int fail = 0;
-  while (nn >= 0) {
-    int its = 0;
-    int l;
-    for (;;) {
-      // look for a single small subdiagonal element
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        int ll;
-        for (ll = nn; ll >= 1; --ll) {
-          double s = fabs(A.at(ll - 1, ll - 1)) + fabs(A.at(ll, ll));
-          if (s == 0.0) s = anorm;
-          if (fabs(A.at(ll, ll - 1)) + s == s) { A.at(ll, ll - 1) = 0.0; break; }
+  double hnorm = 0;
+  for (int w = 0; w < kFrancisWarps; ++w) hnorm += s_norm[w];
+  const double eps = 2.220446049250313e-16;
+  int hi = n - 1, its = 0, total = 0, fail = 0;
+  const int max_total = 40 * n;
+  while (hi >= 0) {
+    // lo: the largest l <= hi whose subdiagonal entry is negligible (0 if none)
+    if (warp == 0) {
+      int lo = 0;
+      for (int base = hi; base >= 1; base -= 32) {
+        const int l = base - lane;
+        bool small = false;
+        if (l >= 1) {
+          double sz = fabs(H.at(l, l)) + fabs(H.at(l - 1, l - 1));
+          if (sz == 0.0) sz = hnorm;
+          small = fabs(H.at(l, l - 1)) <= eps * sz;
         }
-        s_l = ll;
-      }
-      __syncthreads();
-      l = s_l;
-      const double x = A.at(nn, nn);
-      if (l == nn) {  // one eigenvalue
-        if (threadIdx.x == 0) { wr[nn] = x + tsum; wi[nn] = 0.0; }
-        nn -= 1;
-        break;
-      }
-      const double y = A.at(nn - 1, nn - 1);
-      const double w = A.at(nn, nn - 1) * A.at(nn - 1, nn);
-      if (l == nn - 1) {  // a 2x2 block: two eigenvalues
-        if (threadIdx.x == 0) {
-          const double p = 0.5 * (y - x);
-          const double q = p * p + w;
-          const double z = sqrt(fabs(q));
-          const double xs = x + tsum;
-          if (q >= 0.0) {
-            const double zz = p + copysign(z, p);
-            wr[nn - 1] = wr[nn] = xs + zz;
-            if (zz != 0.0) wr[nn] = xs - w / zz;
-            wi[nn - 1] = wi[nn] = 0.0;
-          } else {
-            wr[nn - 1] = wr[nn] = xs + p;
-            wi[nn - 1] = z;
-            wi[nn] = -z;
-          }
-        }
-        nn -= 2;
-        break;
-      }
-      if (its == 60) { fail = 1; nn = -1; break; }
-      // shifts: the eigenvalues of the trailing 2x2 block, or exceptional
-      if (threadIdx.x == 0) {
-        double xs = x, ys = y, ws = w;
-        if (its == 10 || its == 20 || its == 30 || its == 40 || its == 50) {
-          tsum += x;  // thread 0's copy; broadcast below
-          for (int i = 0; i <= nn; ++i) A.at(i, i) -= x;
-          const double s = fabs(A.at(nn, nn - 1)) + fabs(A.at(nn - 1, nn - 2));
-          xs = ys = 0.75 * s;
-          ws = -0.4375 * s * s;
-        }
-        s_shift[0] = xs; s_shift[1] = ys; s_shift[2] = ws;
-        sh[31] = tsum;
-        // find m: the first double-shift vector that is negligibly coupled above
-        int m;
-        for (m = nn - 2; m >= l; --m) {
-          const double zm = A.at(m, m);
-          const double r = xs - zm, s = ys - zm;
-          double p = (r * s - ws) / A.at(m + 1, m) + A.at(m, m + 1);
-          double q = A.at(m + 1, m + 1) - zm - r - s;
-          double rr = A.at(m + 2, m + 1);
-          const double sc = fabs(p) + fabs(q) + fabs(rr);
-          p /= sc; q /= sc; rr /= sc;
-          if (m == l) break;
-          const double u = fabs(A.at(m, m - 1)) * (fabs(q) + fabs(rr));
-          const double v = fabs(p) * (fabs(A.at(m - 1, m - 1)) + fabs(zm) + fabs(A.at(m + 1, m + 1)));
-          if (u + v == v) break;
-        }
-        s_m = m;
-        for (int i = m + 2; i <= nn; ++i) {
-          A.at(i, i - 2) = 0.0;
-          if (i != m + 2) A.at(i, i - 3) = 0.0;
+        const unsigned m = __ballot_sync(full, small);
+        if (m) {
+          lo = base - (__ffs(m) - 1);
+          break;
         }
       }
-      __syncthreads();
-      tsum = sh[31];
-      const int m = s_m;
-      ++its;
-      const double xs = s_shift[0], ys = s_shift[1], ws = s_shift[2];
-      // double-shift QR step on rows l..nn, columns m..nn (bulge chase).  Thread
-      // 0 forms each 3x3 reflector once and broadcasts it (FP64 divide and sqrt
-      // take ~600 cycles each here; every thread computing them would also
-      // saturate the FP64 pipe).
-      for (int k = m; k <= nn - 1; ++k) {
-        if (threadIdx.x == 0) {
-          double p, q, r = 0.0, xk = 0.0;
-          if (k == m) {
-            const double zm = A.at(m, m);
-            const double rr0 = xs - zm, ss0 = ys - zm;
-            p = (rr0 * ss0 - ws) / A.at(m + 1, m) + A.at(m, m + 1);
-            q = A.at(m + 1, m + 1) - zm - rr0 - ss0;
-            r = A.at(m + 2, m + 1);
-            xk = fabs(p) + fabs(q) + fabs(r);
-            const double ix = 1.0 / xk;
-            p *= ix; q *= ix; r *= ix;
-          } else {
-            p = A.at(k, k - 1);
-            q = A.at(k + 1, k - 1);
-            if (k != nn - 1) r = A.at(k + 2, k - 1);
-            xk = fabs(p) + fabs(q) + fabs(r);
-            if (xk != 0.0) {
-              const double ix = 1.0 / xk;
-              p *= ix; q *= ix; r *= ix;
-            }
-          }
-          const double sg = copysign(sqrt(p * p + q * q + r * r), p);
-          s_ref[5] = (sg == 0.0) ? 0.0 : 1.0;
-          if (sg != 0.0) {
-            if (k == m) {
-              if (l != m) A.at(k, k - 1) = -A.at(k, k - 1);
-            } else {
-              A.at(k, k - 1) = -sg * xk;
-              A.at(k + 1, k - 1) = 0.0;
-              if (k != nn - 1) A.at(k + 2, k - 1) = 0.0;
-            }
-            const double pp = p + sg;
-            const double is = 1.0 / sg, ip = 1.0 / pp;
-            s_ref[0] = pp * is;  // vx
-            s_ref[1] = q * is;   // vy
-            s_ref[2] = r * is;   // vz
-            s_ref[3] = q * ip;   // q2
-            s_ref[4] = r * ip;   // r2
-          }
-        }
-        __syncthreads();
-        if (s_ref[5] == 0.0) {
-          __syncthreads();  // all threads have read the flag before thread 0 forms the next reflector
-          continue;
-        }
-        const double vx = s_ref[0], vy = s_ref[1], vz = s_ref[2], q2 = s_ref[3], r2 = s_ref[4];
-        // rows k..k+2, columns k..nn
-        for (int j = k + threadIdx.x; j <= nn; j += blockDim.x) {
-          double t = A.at(k, j) + q2 * A.at(k + 1, j);
-          if (k != nn - 1) {
-            t += r2 * A.at(k + 2, j);
-            A.at(k + 2, j) -= t * vz;
-          }
-          A.at(k + 1, j) -= t * vy;
-          A.at(k, j) -= t * vx;
-        }
-        __syncthreads();
-        // columns k..k+2, rows l..min(nn, k+3)
-        const int mmin = nn < k + 3 ? nn : k + 3;
-        for (int i = l + threadIdx.x; i <= mmin; i += blockDim.x) {
-          double t = vx * A.at(i, k) + vy * A.at(i, k + 1);
-          if (k != nn - 1) {
-            t += vz * A.at(i, k + 2);
-            A.at(i, k + 2) -= t * r2;
-          }
-          A.at(i, k + 1) -= t * q2;
-          A.at(i, k) -= t;
-        }
-        __syncthreads();
+      if (lane == 0) {
+        if (lo > 0) H.at(lo, lo - 1) = 0.0;
+        s_lo = lo;
       }
     }
+    __syncthreads();
+    const int lo = s_lo;
+    if (lo == hi) {
+      if (tid == 0) { wr[hi] = H.at(hi, hi); wi[hi] = 0.0; }
+      hi -= 1;
+      its = 0;
+      __syncthreads();
+      continue;
+    }
+    if (lo == hi - 1) {
+      // eigenvalues of the 2 x 2 block [[p, q], [r, u]]: mean +- sqrt(disc)
+      if (tid == 0) {
+        const double p = H.at(lo, lo), q = H.at(lo, hi), r = H.at(hi, lo), u = H.at(hi, hi);
+        const double mean = 0.5 * (p + u), half = 0.5 * (p - u);
+        const double disc = half * half + q * r;
+        if (disc >= 0.0) {
+          const double rt = sqrt(disc);
+          const double big = mean + (mean >= 0.0 ? rt : -rt);  // no cancellation
+          const double det = p * u - q * r;
+          wr[lo] = big;
+          wr[hi] = (big != 0.0) ? det / big : mean - rt;
+          wi[lo] = wi[hi] = 0.0;
+        } else {
+          const double im = sqrt(-disc);
+          wr[lo] = wr[hi] = mean;
+          wi[lo] = im;
+          wi[hi] = -im;
+        }
+      }
+      hi -= 2;
+      its = 0;
+      __syncthreads();
+      continue;
+    }
+    if (total >= max_total) {
+      fail = 1;
+      break;
+    }
+    ++its;
+    ++total;
+    if (warp == 0) {
+      // shifts: the trailing 2 x 2 block of the window (s = trace, t = det);
+      // every 10th iteration without a deflation, a double shift at
+      // h_hi,hi + 1.5 |h_hi,hi-1| instead (breaks cycles of the standard shift)
+      double s, t;
+      const int m = hi - 1;
+      if (its % 10 == 0) {
+        const double mu = H.at(hi, hi) + 1.5 * fabs(H.at(hi, m));
+        s = 2.0 * mu;
+        t = mu * mu;
+      } else {
+        s = H.at(m, m) + H.at(hi, hi);
+        t = H.at(m, m) * H.at(hi, hi) - H.at(m, hi) * H.at(hi, m);
+      }
+      // first column of H^2 - s H + t I on the window
+      const double x0 = H.at(lo, lo) * H.at(lo, lo) + H.at(lo, lo + 1) * H.at(lo + 1, lo) - s * H.at(lo, lo) + t;
+      const double y0 = H.at(lo + 1, lo) * (H.at(lo, lo) + H.at(lo + 1, lo + 1) - s);
+      const double z0 = H.at(lo + 1, lo) * H.at(lo + 2, lo + 1);
+      double al, u0, u1, u2;
+      house3(x0, y0, z0, al, u0, u1, u2);
+      if (lane == 0) {
+        s_ref[lo & 1][0] = al;
+        s_ref[lo & 1][1] = u0;
+        s_ref[lo & 1][2] = u1;
+        s_ref[lo & 1][3] = u2;
+      }
+    }
+    for (int k = lo; k <= hi - 2; ++k) {
+      __syncthreads();  // reflector k published; far(k - 1) done
+      const double alpha = s_ref[k & 1][0], v0 = s_ref[k & 1][1], v1 = s_ref[k & 1][2], v2 = s_ref[k & 1][3];
+      if (warp == 0) {
+        if (k > lo && lane == 0) {
+          H.at(k, k - 1) = alpha;  // column k-1, rows k..k+2 -> (alpha, 0, 0)
+          H.at(k + 1, k - 1) = 0.0;
+          H.at(k + 2, k - 1) = 0.0;
+        }
+        const int c = ((k > lo) ? k : lo) + lane;
+        if (lane < 4 && c <= min(k + 3, hi)) {
+          const double h0 = H.at(k, c), h1 = H.at(k + 1, c), h2 = H.at(k + 2, c);
+          const double w = v0 * h0 + v1 * h1 + v2 * h2;
+          H.at(k, c) = h0 - w * v0;
+          H.at(k + 1, c) = h1 - w * v1;
+          H.at(k + 2, c) = h2 - w * v2;
+        }
+        __syncwarp();
+        const int r = k + lane;
+        if (lane < 4 && r <= min(k + 3, hi)) {
+          const double h0 = H.at(r, k), h1 = H.at(r, k + 1), h2 = H.at(r, k + 2);
+          const double w = h0 * v0 + h1 * v1 + h2 * v2;
+          H.at(r, k) = h0 - w * v0;
+          H.at(r, k + 1) = h1 - w * v1;
+          H.at(r, k + 2) = h2 - w * v2;
+        }
+        __syncwarp();
+        // the next reflector (the last one of the sweep has two entries)
+        const double xn = H.at(k + 1, k), yn = H.at(k + 2, k), zn = (k < hi - 2) ? H.at(k + 3, k) : 0.0;
+        double an, u0, u1, u2;
+        house3(xn, yn, zn, an, u0, u1, u2);
+        if (lane == 0) {
+          s_ref[(k + 1) & 1][0] = an;
+          s_ref[(k + 1) & 1][1] = u0;
+          s_ref[(k + 1) & 1][2] = u1;
+          s_ref[(k + 1) & 1][3] = u2;
+        }
+      } else {
+        for (int c = k + 4 + ftid; c <= hi; c += nft) {
+          const double h0 = H.at(k, c), h1 = H.at(k + 1, c), h2 = H.at(k + 2, c);
+          const double w = v0 * h0 + v1 * h1 + v2 * h2;
+          H.at(k, c) = h0 - w * v0;
+          H.at(k + 1, c) = h1 - w * v1;
+          H.at(k + 2, c) = h2 - w * v2;
+        }
+        for (int r = lo + ftid; r <= k - 1; r += nft) {
+          const double h0 = H.at(r, k), h1 = H.at(r, k + 1), h2 = H.at(r, k + 2);
+          const double w = h0 * v0 + h1 * v1 + h2 * v2;
+          H.at(r, k) = h0 - w * v0;
+          H.at(r, k + 1) = h1 - w * v1;
+          H.at(r, k + 2) = h2 - w * v2;
+        }
+      }
+    }
+    __syncthreads();
+    // the last reflector (two entries, v2 = 0) acts on rows hi-1, hi
+    {
+      const int k = hi - 1;
+      const double alpha = s_ref[k & 1][0], v0 = s_ref[k & 1][1], v1 = s_ref[k & 1][2];
+      if (k > lo && tid == 0) {
+        H.at(k, k - 1) = alpha;
+        H.at(k + 1, k - 1) = 0.0;
+      }
+      const int c0 = (k > lo) ? k : lo;
+      for (int c = c0 + tid; c <= hi; c += kFrancisThreads) {
+        const double h0 = H.at(k, c), h1 = H.at(k + 1, c);
+        const double w = v0 * h0 + v1 * h1;
+        H.at(k, c) = h0 - w * v0;
+        H.at(k + 1, c) = h1 - w * v1;
+      }
+      __syncthreads();
+      for (int r = lo + tid; r <= hi; r += kFrancisThreads) {
+        const double h0 = H.at(r, k), h1 = H.at(r, k + 1);
+        const double w = h0 * v0 + h1 * v1;
+        H.at(r, k) = h0 - w * v0;
+        H.at(r, k + 1) = h1 - w * v1;
+      }
+      __syncthreads();
+    }
   }
-  if (threadIdx.x == 0) *status = fail;
+  if (tid == 0) *status = fail;
 }
+
 
 // ---- selection: nev eigenvalues of largest real part (ties: larger imaginary
 // part, then index) ----------------------------------------------------------------------
@@ -398,7 +479,14 @@ invit_kernel(const double* __restrict__ Hg, const double* __restrict__ tau, int 
     const int64_t d0 = (n - 1) + (int64_t)(n - 1) * n;
     if (Ur[d0] * Ur[d0] + Ui[d0] * Ui[d0] == 0.0) Ur[d0] = eps_u;
   }
-  for (int i = threadIdx.x; i < n; i += blockDim.x) { yr[i] = 1.0; yi[i] = 0.0; }
+  // start vector: entries in [0.5, 1.5) from the counter hash of (t, i), so
+  // that copies of a repeated eigenvalue start from different vectors and
+  // return independent vectors of its eigenspace
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const uint64_t h = mix64(0x5851F42D4C957F2Dull * (uint64_t)(t + 1) + (uint64_t)i);
+    yr[i] = 0.5 + (double)(h >> 11) * (1.0 / 9007199254740992.0);
+    yi[i] = 0.0;
+  }
   __syncthreads();
   for (int iter = 0; iter < 3; ++iter) {
     // forward: apply the row swaps and multipliers
@@ -455,23 +543,17 @@ invit_kernel(const double* __restrict__ Hg, const double* __restrict__ tau, int 
   }
 }
 
-size_t eig_smem_bytes(int n) {
-  size_t o = 0;
-  for (int i = 0; i < n; ++i) o += (size_t)(n - (i > 3 ? i - 3 : 0));
-  return o * sizeof(double);
-}
-
 // M (n x n, col-major, overwritten), outputs: wr, wi (n), sel (nev), Yre/Yim
 // (n x nev col-major), status (device int; 1 = QR iteration did not converge).
 sk_status enqueue_eig(double* M, int n, int nev, double* tau, double* wr, double* wi, int* sel, double* Wre,
                       double* Wim, double* Yre, double* Yim, int* status, cudaStream_t st) {
-  if (n > kEigMaxN || n < 3) { set_error("eigensolver supports 3 <= d <= %d", kEigMaxN); return SK_EINVAL; }
+  if (n > kFrancisMaxN || n < 3) { set_error("eigensolver supports 3 <= d <= %d", kFrancisMaxN); return SK_EINVAL; }
   hessenberg_kernel<<<1, kEigThreads, 0, st>>>(M, n, tau);
   SK_CUDA(cudaGetLastError());
-  const size_t smem = eig_smem_bytes(n);
-  if (smem > (size_t)kDynSmemLimit) { set_error("eigensolver: d too large for shared memory"); return SK_EINVAL; }
-  SK_CUDA(cudaFuncSetAttribute(hqr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kDynSmemLimit));
-  hqr_kernel<<<1, kEigThreads, smem, st>>>(M, tau, n, wr, wi, status);
+  // one attribute value for every launch (graph capture keeps launch sizes)
+  SK_CUDA(cudaFuncSetAttribute(francis_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)francis_smem_bytes(kFrancisMaxN) + 16));
+  francis_kernel<<<1, kFrancisThreads, francis_smem_bytes(n) + 16, st>>>(M, tau, n, wr, wi, status);
   SK_CUDA(cudaGetLastError());
   select_kernel<<<1, 1, 0, st>>>(wr, wi, n, nev, sel);
   SK_CUDA(cudaGetLastError());

@@ -23,12 +23,11 @@
 #include "basis.cuh"
 #include "common.cuh"
 #include "dense.cuh"
+#include "srr.cuh"
 
 namespace sk {
 
 static constexpr int kVecThreads = 256;
-static constexpr int kMaxSrrD = 256;
-static constexpr int kMaxNev = 32;
 
 // G consecutive entries of one column, converted to the compute type.
 template <int G, typename T, typename C>
@@ -202,35 +201,7 @@ static sk_status enqueue_update(double* x, const void* B, int64_t ldb, int64_t n
              : launch_update<__nv_bfloat16, 1>(x, (const __nv_bfloat16*)B, ldb, n, d, y, diag, st);
 }
 
-// ----------------------------------------------------------------------------
-// Sketch of either kind behind one interface (plans built once per solve).
-// ----------------------------------------------------------------------------
-struct Sketcher {
-  sk_sketch_kind kind = SK_SPARSE_SIGN;
-  SketchPlan sp;
-  SrhtPlan hp;
-  int s = 0, zeta = 0;
-  sk_status create(const sk_sketch& S, Scratch& sc, cudaStream_t st) {
-    kind = S.kind;
-    s = S.s;
-    if (kind == SK_SRHT) return srht_plan_create(&hp, &S, sc, st);
-    SK_TRY(plan_create(&sp, &S, sc, st));
-    zeta = sp.zeta;
-    return check_plan_status(sp, st);
-  }
-  // block = basis columns (a fixed summation order per column, whether the
-  // basis is sketched whole or in blocks); false for the residual
-  size_t ws(int ncols, sk_dtype dt, bool block) const {
-    return kind == SK_SRHT ? srht_ws_doubles(hp, ncols, block) : plan_ws_doubles(sp, ncols, dt, block);
-  }
-  sk_status apply(const void* B, int64_t ldb, int ncols, sk_dtype dt, double* out, double* ws, cudaStream_t st,
-                  bool block) const {
-    if (kind == SK_SRHT) return srht_apply_ws(hp, B, ldb, ncols, dt, out, ws, st, block);
-    return plan_apply_ws(sp, B, ldb, ncols, dt, out, ws, st, block);
-  }
-};
-
-static void resolve_opts(const sk_opts* in, sk_opts* o, int d) {
+void resolve_opts(const sk_opts* in, sk_opts* o, int d) {
   if (in) *o = *in;
   else sk_opts_default(o);
   if (o->zeta <= 0) o->zeta = default_zeta_for(d);
@@ -243,7 +214,7 @@ static void resolve_opts(const sk_opts* in, sk_opts* o, int d) {
 // A single classical Gram-Schmidt pass takes nu_j from ||m||^2 - ||h||^2,
 // which needs the window orthonormal to the working precision: fine with an
 // FP64 basis, unstable with FP32/BF16 (columns blow up after ~20 steps).
-static sk_status check_passes(const sk_opts& o) {
+sk_status check_passes(const sk_opts& o) {
   if (o.basis_kind == SK_BASIS_CHEBYSHEV) {
     const double rho = o.cheb_dx > o.cheb_dy ? o.cheb_dx : o.cheb_dy;
     if (!(rho > 0) || !std::isfinite(rho) || !std::isfinite(o.cheb_c) || o.cheb_dx < 0 || o.cheb_dy < 0) {
@@ -1032,150 +1003,11 @@ extern "C" sk_status sgmres_solve_batched(int nsys, const sk_op* const* A, int n
   return first_err;
 }
 
-// ----------------------------------------------------------------------------
-// Sketched Rayleigh-Ritz (Algorithm 2, §6.3-§6.4).
-// ----------------------------------------------------------------------------
-namespace sk {
-
-// M-hat = T^{-1} (U^T D): column c of the D block (rows 0..d-1 after the QR)
-// solved against the triangle (one CTA per column, column sweep).
-__global__ void __launch_bounds__(256)
-mhat_kernel(const double* __restrict__ Aug, const double* __restrict__ rdiag, int s, int d,
-            double* __restrict__ Mhat) {
-  __shared__ double z[kMaxSrrD];
-  __shared__ double s_y;
-  const int c = blockIdx.x;
-  const double* Dc = Aug + (int64_t)(d + c) * s;
-  for (int i = threadIdx.x; i < d; i += blockDim.x) z[i] = Dc[i];
-  __syncthreads();
-  for (int i = d - 1; i >= 0; --i) {
-    if (threadIdx.x == 0) { s_y = z[i] / rdiag[i]; z[i] = s_y; }
-    __syncthreads();
-    const double yi = s_y;
-    const double* Ri = Aug + (int64_t)i * s;
-    for (int t = threadIdx.x; t < i; t += blockDim.x) z[t] -= yi * Ri[t];
-    __syncthreads();
-  }
-  for (int i = threadIdx.x; i < d; i += blockDim.x) Mhat[i + (int64_t)c * d] = z[i];
-}
-
-// Residual estimate (eq. (srr-resid-est)) of selected pair t, computed in the
-// rotated basis after the QR: ||Q^T D y - lambda [T y; 0]|| / ||T y||.
-__global__ void __launch_bounds__(256)
-srr_resid_kernel(const double* __restrict__ Aug, const double* __restrict__ rdiag, int s, int d,
-                 const double* __restrict__ wr, const double* __restrict__ wi, const int* __restrict__ sel,
-                 const double* __restrict__ Yre, const double* __restrict__ Yim, int symmetric,
-                 double* __restrict__ out /* nev x 3: lam_re, lam_im, rhat */) {
-  __shared__ double yr[kMaxSrrD], yi[kMaxSrrD];
-  __shared__ double sh[32];
-  const int t = blockIdx.x;
-  const int e = sel[t];
-  const double lr = wr[e], li = symmetric ? 0.0 : wi[e];
-  for (int j = threadIdx.x; j < d; j += blockDim.x) {
-    yr[j] = Yre[(int64_t)t * d + j];
-    yi[j] = symmetric ? 0.0 : Yim[(int64_t)t * d + j];
-  }
-  __syncthreads();
-  double num = 0, den = 0;
-  for (int r = threadIdx.x; r < s; r += blockDim.x) {
-    double vr = 0, vi = 0, ur = 0, ui = 0;
-    for (int j = 0; j < d; ++j) {
-      const double dq = Aug[(int64_t)(d + j) * s + r];
-      vr += dq * yr[j];
-      vi += dq * yi[j];
-      if (r < d && j >= r) {
-        const double tq = (j == r) ? rdiag[r] : Aug[(int64_t)j * s + r];
-        ur += tq * yr[j];
-        ui += tq * yi[j];
-      }
-    }
-    const double rr = vr - (lr * ur - li * ui);
-    const double ri = vi - (lr * ui + li * ur);
-    num += rr * rr + ri * ri;
-    den += ur * ur + ui * ui;
-  }
-  num = warp_sum(num);
-  den = warp_sum(den);
-  __shared__ double s2[32];
-  if ((threadIdx.x & 31) == 0) { sh[threadIdx.x >> 5] = num; s2[threadIdx.x >> 5] = den; }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double a = 0, b = 0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { a += sh[w]; b += s2[w]; }
-    out[t * 3 + 0] = lr;
-    out[t * 3 + 1] = li;
-    out[t * 3 + 2] = sqrt(a) / sqrt(b);
-  }
-}
-
-// X = B Y for the selected pairs (complex), one pass over B; per-CTA partial
-// squared norms of each column for the normalisation.
-template <typename T>
-__global__ void __launch_bounds__(256)
-ritz_kernel(const T* __restrict__ B, int64_t ldb, int64_t n, int d, int nev, const double* __restrict__ Yre,
-            const double* __restrict__ Yim, int symmetric, double* __restrict__ Xre, double* __restrict__ Xim,
-            double* __restrict__ part) {
-  extern __shared__ double ys[];  // 2 * nev * d
-  __shared__ double sh[kMaxNev * 2 * 8];
-  for (int q = threadIdx.x; q < nev * d; q += blockDim.x) {
-    ys[q] = Yre[q];
-    ys[nev * d + q] = symmetric ? 0.0 : Yim[q];
-  }
-  __syncthreads();
-  double nrm[kMaxNev];
-  for (int t = 0; t < nev; ++t) nrm[t] = 0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    double ar[kMaxNev], ai[kMaxNev];
-    for (int t = 0; t < nev; ++t) { ar[t] = 0; ai[t] = 0; }
-    for (int j = 0; j < d; ++j) {
-      const double b = to_c(B[i + (int64_t)j * ldb]);
-      for (int t = 0; t < nev; ++t) {
-        ar[t] += b * ys[t * d + j];
-        ai[t] += b * ys[nev * d + t * d + j];
-      }
-    }
-    for (int t = 0; t < nev; ++t) {
-      Xre[i + (int64_t)t * n] = ar[t];
-      if (Xim) Xim[i + (int64_t)t * n] = ai[t];
-      nrm[t] += ar[t] * ar[t] + ai[t] * ai[t];
-    }
-  }
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (int t = 0; t < nev; ++t) {
-    const double v = warp_sum(nrm[t]);
-    if (lane == 0) sh[t * 8 + wid] = v;
-  }
-  __syncthreads();
-  if (threadIdx.x < nev) {
-    double a = 0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) a += sh[threadIdx.x * 8 + w];
-    part[blockIdx.x * nev + threadIdx.x] = a;
-  }
-}
-
-__global__ void ritz_normalize_kernel(double* __restrict__ Xre, double* __restrict__ Xim, int64_t n, int nev,
-                                      const double* __restrict__ part, int nblk) {
-  __shared__ double inv[kMaxNev];
-  if (threadIdx.x < nev) {
-    double a = 0;
-    for (int b = 0; b < nblk; ++b) a += part[b * nev + threadIdx.x];
-    inv[threadIdx.x] = a > 0 ? 1.0 / sqrt(a) : 0.0;
-  }
-  __syncthreads();
-  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n * nev; q += (int64_t)gridDim.x * blockDim.x) {
-    const int t = (int)(q / n);
-    Xre[q] *= inv[t];
-    if (Xim) Xim[q] *= inv[t];
-  }
-}
-
-}  // namespace sk
-
 extern "C" sk_status srr_eigs(const sk_op* A, const double* w1, int nev, int d, int k, int s, const sk_opts* opts,
                               double* lam_re, double* lam_im, double* X_re, double* X_im, double* rhat, int* nconv,
                               sk_info* info, void* stream) {
   SK_CHECK_ARG(A != nullptr && w1 != nullptr && lam_re != nullptr && X_re != nullptr, "NULL argument");
-  SK_CHECK_ARG(d >= 3 && d <= kMaxSrrD, "sRR needs 3 <= d <= 256");
+  SK_CHECK_ARG(d >= 3 && d <= kMaxSrrD, "sRR needs 3 <= d <= 232");
   SK_CHECK_ARG(nev >= 1 && nev <= d && nev <= kMaxNev, "need 1 <= nev <= min(d, 32)");
   SK_CHECK_ARG(k >= 1 && k <= d && k <= kMaxK, "need 1 <= k <= min(d, 16)");
   SK_CHECK_ARG(s >= d, "need s >= d");
@@ -1214,82 +1046,32 @@ extern "C" sk_status srr_eigs(const sk_op* A, const double* w1, int nev, int d, 
   sks.zeta = o.zeta;
   sks.seed = o.seed;
   SK_TRY(skt.create(sks, sc, st));
-  double *SB, *ws, *Aug, *rdiag, *tau, *Tws, *Mhat, *etau, *wr, *wi, *Wre, *Wim, *Yre, *Yim, *res, *part;
-  int *sel, *estat;
+  double *SB, *ws, *Aug;
   SK_TRY(sc.alloc(&SB, (size_t)s * (d + 1)));
   SK_TRY(sc.alloc(&ws, skt.ws(d + 1, o.basis, true)));
   SK_TRY(sc.alloc(&Aug, (size_t)s * 2 * d));
-  SK_TRY(sc.alloc(&rdiag, d));
-  SK_TRY(sc.alloc(&tau, d));
-  SK_TRY(sc.alloc(&Tws, (size_t)((d + kQrNb - 1) / kQrNb) * kQrNb * kQrNb));
-  SK_TRY(sc.alloc(&Mhat, (size_t)d * d));
-  SK_TRY(sc.alloc(&etau, 2 * (size_t)d));
-  SK_TRY(sc.alloc(&wr, d));
-  SK_TRY(sc.alloc(&wi, d));
-  SK_TRY(sc.alloc(&Wre, (size_t)nev * d * d));
-  SK_TRY(sc.alloc(&Wim, (size_t)nev * d * d));
-  SK_TRY(sc.alloc(&Yre, (size_t)nev * d));
-  SK_TRY(sc.alloc(&Yim, (size_t)nev * d));
-  SK_TRY(sc.alloc(&res, (size_t)nev * 3));
-  SK_TRY(sc.alloc(&sel, nev));
-  SK_TRY(sc.alloc(&estat, 1));
-  SK_CUDA(cudaMemsetAsync(estat, 0, sizeof(int), st));
-  // C = S B (columns 0..d-1), D = S A B = (S B_{d+1}) Hbar; QR of C, Q^T applied to D
+  // C = S B (columns 0..d-1), D = S A B = (S B_{d+1}) Hbar
   SK_TRY(skt.apply(bb.bp.B, bb.bp.ldb, d + 1, o.basis, SB, ws, st, true));
   SK_TRY(enqueue_copy_sb(SB, s, d, bb.bp.stop, Aug, st));
   SK_TRY(enqueue_hbar_product(SB, bb.bp.Hbar, s, d, k, bb.bp.stop, Aug + (size_t)s * d, st));
-  SK_TRY(enqueue_qr(Aug, s, d, 2 * d, rdiag, tau, Tws, st));
-  mhat_kernel<<<d, 256, 0, st>>>(Aug, rdiag, s, d, Mhat);
-  SK_CUDA(cudaGetLastError());
-  SK_TRY(enqueue_eig(Mhat, d, nev, etau, wr, wi, sel, Wre, Wim, Yre, Yim, estat, st));
-  srr_resid_kernel<<<nev, 256, 0, st>>>(Aug, rdiag, s, d, wr, wi, sel, Yre, Yim, o.symmetric, res);
-  SK_CUDA(cudaGetLastError());
-  const int nblk = vec_grid(n);
-  SK_TRY(sc.alloc(&part, (size_t)nblk * nev));
-  const size_t smem = (size_t)2 * nev * d * sizeof(double);
-  double* Xi = (X_im && !o.symmetric) ? X_im : nullptr;
-  if (o.basis == SK_F64) {
-    SK_CUDA(cudaFuncSetAttribute(ritz_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, kDynSmemLimit));
-    ritz_kernel<double><<<nblk, 256, smem, st>>>((const double*)bb.bp.B, bb.bp.ldb, n, d, nev, Yre, Yim, o.symmetric,
-                                                 X_re, Xi, part);
-  } else if (o.basis == SK_F32) {
-    SK_CUDA(cudaFuncSetAttribute(ritz_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, kDynSmemLimit));
-    ritz_kernel<float><<<nblk, 256, smem, st>>>((const float*)bb.bp.B, bb.bp.ldb, n, d, nev, Yre, Yim, o.symmetric,
-                                                X_re, Xi, part);
-  } else {
-    SK_CUDA(cudaFuncSetAttribute(ritz_kernel<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 kDynSmemLimit));
-    ritz_kernel<__nv_bfloat16><<<nblk, 256, smem, st>>>((const __nv_bfloat16*)bb.bp.B, bb.bp.ldb, n, d, nev, Yre,
-                                                        Yim, o.symmetric, X_re, Xi, part);
-  }
-  SK_CUDA(cudaGetLastError());
-  ritz_normalize_kernel<<<vec_grid(n * nev), kVecThreads, 0, st>>>(X_re, Xi, n, nev, part, nblk);
-  SK_CUDA(cudaGetLastError());
-  if (X_im && o.symmetric) SK_CUDA(cudaMemsetAsync(X_im, 0, sizeof(double) * (size_t)n * nev, st));
-  SK_CUDA(cudaEventRecord(e1, st));
-  double hres[3 * kMaxNev];
-  int hstat[3] = {0, 0, 0};
-  SK_CUDA(cudaMemcpyAsync(hres, res, sizeof(double) * 3 * nev, cudaMemcpyDeviceToHost, st));
-  SK_CUDA(cudaMemcpyAsync(hstat, estat, sizeof(int), cudaMemcpyDeviceToHost, st));
-  SK_CUDA(cudaMemcpyAsync(hstat + 1, bb.bp.stop, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+  int hstat[2] = {0, 0};
+  SK_CUDA(cudaMemcpyAsync(hstat, bb.bp.stop, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
   SK_CUDA(cudaStreamSynchronize(st));
-  int conv = 0;
-  for (int t = 0; t < nev; ++t) {
-    lam_re[t] = hres[3 * t];
-    if (lam_im) lam_im[t] = hres[3 * t + 1];
-    if (rhat) rhat[t] = hres[3 * t + 2];
-    if (hres[3 * t + 2] <= o.tau) ++conv;
-  }
-  if (nconv) *nconv = conv;
+  if (hstat[1]) { set_error("NaN/Inf in the basis recurrence"); return SK_ENAN; }
+  if (hstat[0] < d) { set_error("basis breakdown at %d < d columns; sRR on a partial basis is not supported", hstat[0]); return SK_EILLCOND; }
+  SrrOut out{lam_re, lam_im, X_re, X_im, rhat, nconv, nullptr};
+  int eig_fail = 0;
+  SK_TRY(srr_tail(Aug, s, d, bb.bp.B, bb.bp.ldb, n, o.basis, nullptr, nev, o.symmetric, o.tau, o.srr_trunc_tol, out,
+                  sc, st, &eig_fail));
+  SK_CUDA(cudaEventRecord(e1, st));
+  SK_CUDA(cudaEventSynchronize(e1));
   if (info) {
     float ms = 0;
     cudaEventElapsedTime(&ms, e0, e1);
     info->ms[5] = ms;
     info->cycles = 1;
-    info->d_used = hstat[1] < d ? hstat[1] : d;
+    info->d_used = d;
   }
-  if (hstat[2]) { set_error("NaN/Inf in the basis recurrence"); return SK_ENAN; }
-  if (hstat[0]) { set_error("eigensolver: QR iteration did not converge"); return SK_ENOCONV; }
-  if (hstat[1] < d) { set_error("basis breakdown at %d < d columns; sRR on a partial basis is not supported", hstat[1]); return SK_EILLCOND; }
+  if (eig_fail) { set_error("eigensolver: QR iteration did not converge"); return SK_ENOCONV; }
   return SK_OK;
 }

@@ -1,0 +1,174 @@
+"""GPU sketched Rayleigh-Ritz on a given basis, its stabilized form (§6.5),
+and restarted sRR on block Chebyshev bases (§7.2, §7.5), against the CPU
+oracle (oracle/eigs.py), closed-form spectra and ARPACK."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import eigs, hashing, krylov, operators, sketch
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def skg():
+    import torch
+    assert torch.cuda.is_available(), "GPU test needs CUDA"
+    import paper_2111_00113_gb300 as m
+    return m
+
+
+def _t(a):
+    import torch
+    return torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+def _diag_op(skg, lam):
+    return skg.Op.stencil5(len(lam), 1, (0.0, 0.0, 0.0, 0.0, 0.0), _t(lam))
+
+
+def _true_res(A, lam, X):
+    return np.array([eigs.eig_residual(A, lam[i], X[:, i]) for i in range(len(lam))])
+
+
+def _monomial_basis(A, w, d):
+    B = np.zeros((w.shape[0], d))
+    v = w / np.linalg.norm(w)
+    for j in range(d):
+        B[:, j] = v
+        v = A @ v
+        v = v / np.linalg.norm(v)
+    return B
+
+
+def test_basis_algorithm_2_matches_oracle(skg):
+    # Algorithm 2's reduction on a given (truncated Arnoldi) basis: the same
+    # arithmetic as the oracle's srr_from_basis up to summation order
+    N, d, k, nev = 20, 40, 4, 6
+    shift = synth.uniform(1, N * N)
+    coef = synth.conv_diff_coef(N, 10.0)
+    A = operators.stencil5_matrix(N, N, coef, shift)
+    B, M, _, _ = krylov.trunc_arnoldi(A, synth.randn(9, N * N), d, k)
+    s, zeta = 2 * d, hashing.default_zeta(d)
+    op = skg.Op.stencil5(N, N, coef, _t(shift))
+    out = skg.srr_basis(op, _t(B), nev, s, zeta=zeta, seed=7)
+    ref = eigs.srr_from_basis(B, M, lambda X: sketch.sparse_sign_apply(7, s, zeta, X), nev)
+    lam = out["lam"].numpy()
+    assert np.allclose(lam, ref["lam"], rtol=1e-8, atol=1e-10)
+    assert np.allclose(out["rhat"].numpy(), ref["rhat"], rtol=1e-5, atol=1e-12)
+    assert out["rank"] == d
+    tr = _true_res(A, lam, out["X"].cpu().numpy())
+    assert np.allclose(tr, _true_res(A, ref["lam"], ref["X"]), rtol=1e-4, atol=1e-10)
+
+
+@pytest.mark.parametrize("seed", [1, 3])
+def test_stabilized_recovers_spectrum_past_unit_roundoff(skg, seed):
+    # diagonal A with six separated top eigenvalues above a bulk in [0, 1];
+    # monomial bases of depth 40..80 with kappa_2 ~ 1e17.  The GPU's
+    # stabilized sRR (column-pivoted QR + Jacobi SVD, truncation at 1e13)
+    # finds the top six to 5e-4, as the oracle does (its pin), agrees with
+    # the oracle's values to 1e-3 and keeps a rank within 2 of the oracle's
+    # (the truncated SVD of a kappa ~ 1e17 matrix is determined only up to
+    # rounding amplified by 1e13 near the cut)
+    n = 2000
+    top = np.array([3.0, 2.6, 2.2, 2.0, 1.7, 1.5])
+    lam = np.concatenate([top, np.linspace(1.0, 0.0, n - 6)])
+    A = np.diag(lam)
+    op = _diag_op(skg, lam)
+    w = synth.randn(seed, n)
+    for d in (40, 60, 80):
+        B = _monomial_basis(A, w, d)
+        s, zeta = 4 * d, hashing.default_zeta(d)
+        out = skg.srr_basis(op, _t(B), 6, s, zeta=zeta, seed=5, trunc_tol=1e13, symmetric=True)
+        ref = eigs.srr_stabilized_from_basis(B, A @ B, lambda X: sketch.sparse_sign_apply(5, s, zeta, X), 6,
+                                             trunc_tol=1e13, symmetric=True)
+        got = out["lam"].real.numpy()
+        assert np.abs(got - top).max() <= 5e-4, (d, got)
+        assert np.abs(got - ref["lam"].real).max() <= 1e-3
+        assert abs(out["rank"] - ref["rank"]) <= 2 and out["rank"] < d, (out["rank"], ref["rank"])
+
+
+def test_stabilized_equals_algorithm_2_on_a_good_basis(skg):
+    # no truncation on a well-conditioned basis (full orthogonalisation):
+    # the stabilized form's Ritz values equal Algorithm 2's
+    N, d = 16, 30
+    coef = synth.conv_diff_coef(N, 20.0)
+    A = operators.stencil5_matrix(N, N, coef)
+    B, _, _, _ = krylov.trunc_arnoldi(A, synth.randn(4, N * N), d, d)
+    op = skg.Op.stencil5(N, N, coef)
+    kw = dict(zeta=hashing.default_zeta(d), seed=9)
+    a = skg.srr_basis(op, _t(B), 8, 2 * d, **kw)
+    b = skg.srr_basis(op, _t(B), 8, 2 * d, trunc_tol=1e300, **kw)
+    assert b["rank"] == d
+    la, lb = a["lam"].numpy(), b["lam"].numpy()
+    assert np.abs(la[:, None] - lb[None, :]).min(axis=1).max() <= 1e-9
+    ia = np.argsort(np.round(la.real, 6) + 1e-3 * np.round(la.imag, 6))
+    ib = np.argsort(np.round(lb.real, 6) + 1e-3 * np.round(lb.imag, 6))
+    assert np.allclose(a["rhat"].numpy()[ia], b["rhat"].numpy()[ib], rtol=1e-6, atol=1e-12)
+
+
+def test_stabilized_closed_forms(skg):
+    # exact spectra at d = n: a diagonal matrix and the 1-D Laplacian's
+    # 2 - 2 cos(j pi / (n+1)), with residual estimates <= 1e-8
+    n = 64
+    lam = np.concatenate([np.linspace(-1, -0.1, 10), np.linspace(0, 1, n - 10)])
+    A = np.diag(lam)
+    B, _, _, _ = krylov.trunc_arnoldi(A, synth.randn(1, n), n, n)
+    out = skg.srr_basis(_diag_op(skg, lam), _t(B), 10, 2 * n, zeta=hashing.default_zeta(n), trunc_tol=1e13,
+                        symmetric=True)
+    assert np.allclose(out["lam"].real.numpy(), np.sort(lam)[::-1][:10], atol=1e-8)
+    L = operators.stencil5_matrix(n, 1, (2.0, -1.0, -1.0, 0.0, 0.0))
+    B, _, _, _ = krylov.trunc_arnoldi(L, synth.randn(2, n), n, n)
+    out = skg.srr_basis(skg.Op.stencil5(n, 1, (2.0, -1.0, -1.0, 0.0, 0.0)), _t(B), 10, 2 * n,
+                        zeta=hashing.default_zeta(n), trunc_tol=1e13, symmetric=True)
+    exact = np.sort(2 - 2 * np.cos(np.arange(1, n + 1) * np.pi / (n + 1)))[::-1]
+    assert np.allclose(out["lam"].real.numpy(), exact[:10], atol=1e-8)
+    assert np.all(out["rhat"].numpy() <= 1e-8)
+    assert np.allclose(np.linalg.norm(out["X"].cpu().numpy(), axis=0), 1, atol=1e-12)
+
+
+def test_restarted_laplacian_2d_double_eigenvalue(skg):
+    # Dirichlet 5-point Laplacian on 24 x 24: the top five eigenvalues
+    # 4 - 2 cos(i pi/25) - 2 cos(j pi/25) include a double one, found twice
+    # with independent Ritz vectors, true residuals <= 1e-8
+    import torch
+    N, b, p, nev = 24, 8, 12, 5
+    coef = (4.0, -1.0, -1.0, -1.0, -1.0)
+    A = operators.stencil5_matrix(N, N, coef)
+    h = np.pi / (N + 1)
+    ev = np.sort([4 - 2 * np.cos(i * h) - 2 * np.cos(j * h) for i in range(1, N + 1) for j in range(1, N + 1)])[::-1]
+    Om = np.column_stack([synth.randn(400 + i, N * N) for i in range(b)])
+    out = skg.srr_restarted(skg.Op.stencil5(N, N, coef), _t(Om), p, nev, -0.1, 7.0, 40, tau=8e-9, seed=13)
+    assert out["status"] == 0 and out["restarts"] < 40, out["history"]
+    lam = out["lam"].real.numpy()
+    assert np.allclose(np.sort(lam)[::-1], ev[:nev], atol=1e-9)
+    X = out["X"].real.cpu().numpy()
+    assert np.all(_true_res(A, lam, X) <= 1e-8)
+    dbl = [i for i in range(nev) if abs(lam[i] - ev[1]) < 1e-8]
+    assert len(dbl) == 2 and np.linalg.svd(X[:, dbl], compute_uv=False)[-1] >= 0.1
+    assert torch.is_tensor(out["X"])
+
+
+def test_restarted_matches_arpack_and_oracle_on_clustered_spectrum(skg):
+    # the eig workload's operator at 48 x 48 (clustered top eigenvalues):
+    # true residuals <= 1e-8 ||A||, eigenvalues within 1e-7 of ARPACK's and
+    # of the oracle's restarted sRR (same restart rule, same sketches)
+    import scipy.sparse.linalg as spla
+    N, b, p, nev = 48, 12, 16, 6
+    shift = synth.uniform(1, N * N)
+    coef = synth.conv_diff_coef(N, 10.0)
+    A = operators.stencil5_matrix(N, N, coef, shift)
+    An = 8 + shift.max()
+    ref = np.sort(spla.eigs(A, k=nev + 4, which="LR", return_eigenvectors=False, tol=1e-13).real)[::-1]
+    Om = np.column_stack([synth.randn(200 + i, N * N) for i in range(b)])
+    out = skg.srr_restarted(skg.Op.stencil5(N, N, coef, _t(shift)), _t(Om), p, nev, -0.5, 8.0, 30, tau=1e-8 * An,
+                            seed=7)
+    assert out["status"] == 0 and out["restarts"] < 30, out["history"]
+    lam = out["lam"].numpy()
+    tr = _true_res(A, lam, out["X"].cpu().numpy()) / An
+    assert tr.max() <= 1e-8
+    assert np.abs(np.sort(lam.real)[::-1] - ref[:nev]).max() <= 1e-7
+    d = b * p
+    skf = lambda t: (lambda M: sketch.sparse_sign_apply(7 + t, 2 * d, hashing.default_zeta(d), M))
+    ora = eigs.srr_restarted(A, Om, p, nev, -0.5, 8.0, 30, skf, tau=1e-8 * An)
+    assert np.abs(np.sort(lam.real)[::-1] - np.sort(ora["lam"][:nev].real)[::-1]).max() <= 1e-7
