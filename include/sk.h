@@ -246,6 +246,17 @@ sk_status trunc_arnoldi_basis(const sk_op* A, const double* r0, int d, int k, sk
 sk_status sgmres_solve(const sk_op* A, const double* b, double* x, int d, int k, int s, double tol,
                        const sk_opts* opts, sk_info* info, void* stream);
 
+/* Device workspace in bytes that sgmres_solve(A, ., ., d, k, s, ., opts)
+ * allocates (stream-ordered, released before it returns), for callers that
+ * budget memory: the basis n x (d+1) in the basis precision, the Arnoldi
+ * coefficients, the sketch's index tables and partial sums, the s x (d+1)
+ * sketches and the n-vectors of the residual; each buffer rounded up to
+ * 256 bytes (the allocator may reserve more).  Depends on the current
+ * device's SM count.  0 for invalid arguments.  Not counted: the FP32 copies
+ * of an operator's arrays that FP32/BF16 solves make once and the operator
+ * keeps (4 bytes per shift/theta/value entry). */
+size_t sk_workspace_bytes(const sk_op* A, int d, int k, int s, const sk_opts* opts);
+
 /* ------------------------------------------------------------------------
  * Batched restarted sGMRES: nsys independent systems A[i] with nrhs
  * right-hand sides each (not in the paper: many small problems at once).
@@ -297,7 +308,10 @@ sk_status srr_basis(const sk_op* A, const void* B, int64_t ldb, int d, sk_dtype 
  * the restart strategy open; this library restarts from the Krylov space of
  * the current Ritz vectors, built by the block Chebyshev recurrence for the
  * unwanted part of the real spectrum, as follows.  X_0 = Omega (device,
- * n x b FP64).  Restart t: Q = orth(X_t); B_0 = Q, B_1 = (A - c) B_0 / (2 rho),
+ * n x b FP64).  Restart t: Q = orth(X_t) (shifted CholeskyQR3); with
+ * filter_degree = m > 0, Q = orth(T_m((A - c)/rho) Q), a degree-m
+ * Chebyshev filter for the same interval (Q stays a block of the Krylov
+ * space of X_t); B_0 = Q, B_1 = (A - c) B_0 / (2 rho),
  * B_j = ((A - c) B_{j-1} - (rho/4) B_{j-2}) / rho for the interval [lo, cut_t]
  * (c its centre, rho its half-width; cut_0 = hi, then the real part of the
  * b-th Ritz value of restart t-1); the d = b p columns of B_0..B_{p-1}
@@ -313,8 +327,8 @@ sk_status srr_basis(const sk_op* A, const void* B, int64_t ldb, int d, sk_dtype 
  *   Returns SK_OK when all nev estimates are <= tau, else SK_ENOCONV.
  * ------------------------------------------------------------------------ */
 sk_status srr_restarted(const sk_op* A, const double* Omega, int b, int p, int nev, double lo, double hi,
-                        int max_restarts, const sk_opts* opts, double* lam_re, double* lam_im, double* X_re,
-                        double* X_im, double* rhat, int* nconv, int* restarts, double* history, void* stream);
+                        int max_restarts, int filter_degree, const sk_opts* opts, double* lam_re, double* lam_im,
+                        double* X_re, double* X_im, double* rhat, int* nconv, int* restarts, double* history, void* stream);
 
 const char* sk_last_error(void);
 const char* sk_status_string(sk_status st);

@@ -101,11 +101,32 @@ def srr_stabilized(A, w1, d, k, sketch, nev, trunc_tol=1e14, tau=1e-8, symmetric
     return srr_stabilized_from_basis(B, M, sketch, nev, trunc_tol, tau, symmetric)
 
 
-def srr_restarted(A, Omega, p, nev, lo, hi, restarts, sketch_for, tau=1e-8, trunc_tol=1e13, stabilized=True):
+def chebyshev_filter(A, Q, m, c, dx):
+    """T_m((A - c I)/dx) Q by the three-term recurrence Y_0 = Q,
+    Y_1 = (A - c I) Q / dx, Y_{j+1} = 2 (A - c I) Y_j / dx - Y_{j-1}
+    (§4.3 with dy = 0, unscaled Chebyshev polynomials), both carried columns
+    divided by the norms of the newest one after every 10th step (a column
+    scaling, which leaves the span of each column's sequence unchanged)."""
+    Y0 = np.array(Q, dtype=np.float64, copy=True)
+    Y1 = (A @ Y0 - c * Y0) / dx
+    for j in range(2, m + 1):
+        Y0, Y1 = Y1, 2.0 * (A @ Y1 - c * Y1) / dx - Y0
+        if j % 10 == 0:
+            sc = np.linalg.norm(Y1, axis=0)
+            Y0 = Y0 / sc
+            Y1 = Y1 / sc
+    return Y1
+
+
+def srr_restarted(A, Omega, p, nev, lo, hi, restarts, sketch_for, tau=1e-8, trunc_tol=1e13, stabilized=True,
+                  filter_degree=0):
     """Restarted sRR (§7.2) on block Chebyshev bases (§7.5).
 
     X_0 = Omega (n x b).  Restart t: Q = orth(X_t) (Householder QR of the
-    start block); B = [B_1..B_p] from block_chebyshev_basis(A, Q, p, c, dx)
+    start block); with filter_degree = m > 0, Q = orth(T_m((A - c)/dx) Q)
+    (chebyshev_filter: a degree-m Chebyshev filter for the same interval,
+    still a block of K_{m+1}(A; X_t)); B = [B_1..B_p] from
+    block_chebyshev_basis(A, Q, p, c, dx)
     for the interval [lo, cut_t] that holds the unwanted part of the real
     spectrum (c, dx its centre and half-width; cut_0 = hi, then the real part
     of the b-th Ritz value of restart t-1), each column scaled to unit norm;
@@ -126,6 +147,8 @@ def srr_restarted(A, Omega, p, nev, lo, hi, restarts, sketch_for, tau=1e-8, trun
     for t in range(restarts):
         Q, _ = np.linalg.qr(X)
         c, dx = 0.5 * (lo + cut), 0.5 * (cut - lo)
+        if filter_degree > 0:
+            Q, _ = np.linalg.qr(chebyshev_filter(A, Q, filter_degree, c, dx))
         B = krylov.block_chebyshev_basis(A, Q, p, c, dx, 0.0)
         B = B / np.linalg.norm(B, axis=0)
         M = A @ B

@@ -206,6 +206,12 @@ def make_opts(basis=torch.float64, sketch="sparse", zeta=0, seed=7, stab_tol=0.0
     return o
 
 
+def workspace_bytes(A, d, k, s, **opts):
+    """Device bytes sgmres_solve allocates for this operator and shape."""
+    o = make_opts(**opts)
+    return int(N.lib.sk_workspace_bytes(A._h, d, k, s, C.byref(o)))
+
+
 def trunc_arnoldi_basis(A, r0, d, k, dtype=torch.float64, s=None, zeta=0, seed=7, kind="sparse", cgs_passes=2,
                         persistent=False, cheb=None, barrier_spins=0):
     """k-truncated Arnoldi basis (§1.2.2 eq. (partorth)).
@@ -339,9 +345,11 @@ def srr_basis(A, B, nev, s, **opts):
     return dict(lam=lam, X=torch.complex(Xr, Xi), rhat=torch.tensor(list(rh)), nconv=nconv.value, rank=rank.value)
 
 
-def srr_restarted(A, Omega, p, nev, lo, hi, max_restarts, **opts):
+def srr_restarted(A, Omega, p, nev, lo, hi, max_restarts, filter_degree=0, **opts):
     """Restarted sRR (§7.2) on block Chebyshev bases (§7.5) from the start
-    block Omega (n x b, float64); [lo, hi] brackets the real spectrum.
+    block Omega (n x b, float64); [lo, hi] brackets the real spectrum;
+    filter_degree > 0 filters each start block by a Chebyshev polynomial of
+    that degree first.
     Returns dict(lam, X, rhat, nconv, restarts, history, status)."""
     Om = colmajor(_dev_f64(Omega) if Omega.dim() == 1 else Omega.to(torch.float64))
     n, b = Om.shape
@@ -354,7 +362,8 @@ def srr_restarted(A, Omega, p, nev, lo, hi, max_restarts, **opts):
     Xi = empty_colmajor(n, nev, torch.float64, Om.device)
     nconv = C.c_int(0)
     nres = C.c_int(0)
-    st = N.check(N.lib.srr_restarted(A._h, _ptr(Om), b, p, nev, float(lo), float(hi), max_restarts, C.byref(o), lre,
+    st = N.check(N.lib.srr_restarted(A._h, _ptr(Om), b, p, nev, float(lo), float(hi), max_restarts,
+                                     int(filter_degree), C.byref(o), lre,
                                      lim, _ptr(Xr), _ptr(Xi), rh, C.byref(nconv), C.byref(nres), hist, _stream()),
                  allow=(N.SK_OK, N.SK_ENOCONV))
     lam = torch.tensor([complex(a, b) for a, b in zip(lre, lim)], dtype=torch.complex128)

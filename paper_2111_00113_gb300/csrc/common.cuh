@@ -266,6 +266,10 @@ size_t plan_ws_doubles(const SketchPlan& p, int ncols, sk_dtype dtype, bool bloc
 sk_status plan_apply_ws(const SketchPlan& p, const void* B, int64_t ldb, int ncols, sk_dtype dtype, double* SB,
                         double* partial, cudaStream_t st, bool block = false);
 sk_status check_plan_status(const SketchPlan& p, cudaStream_t st);
+struct SrhtPlan;
+// The device bytes of the plan for S and the shape fields that the
+// workspace queries (plan_ws_doubles, srht_ws_doubles) read; allocates nothing.
+size_t sketch_plan_shape(const sk_sketch& S, SketchPlan* sp, SrhtPlan* hp);
 int default_zeta_for(int d);
 
 struct SrhtPlan {

@@ -720,6 +720,26 @@ sk_status plan_apply(const SketchPlan& p, const void* B, int64_t ldb, int ncols,
   return plan_apply_ws(p, B, ldb, ncols, dtype, SB, partial, st);
 }
 
+size_t sketch_plan_shape(const sk_sketch& S, SketchPlan* sp, SrhtPlan* hp) {
+  auto r256 = [](size_t b) { return (b + 255) & ~(size_t)255; };
+  if (S.kind == SK_SRHT) {
+    hp->n = S.n;
+    hp->s = S.s;
+    hp->logn = 0;
+    while ((1ll << hp->logn) < hp->n) ++hp->logn;
+    hp->n_p = 1ll << hp->logn;
+    hp->b = hp->logn < 12 ? hp->logn : 12;
+    return r256((size_t)S.s * sizeof(int32_t)) + r256((size_t)((S.n + 31) / 32) * sizeof(uint32_t));
+  }
+  sp->n = S.n;
+  sp->s = S.s;
+  sp->zeta = S.zeta > 0 ? S.zeta : default_zeta_for(S.s / 2);
+  sp->L = kChunk;
+  sp->nchunks = (int)((S.n + kChunk - 1) / kChunk);
+  return r256((size_t)sp->nchunks * rp_stride(sp->s) * sizeof(uint32_t)) +
+         r256((size_t)sp->nchunks * kChunk * sp->zeta * sizeof(uint16_t)) + r256(sizeof(int));
+}
+
 sk_status check_plan_status(const SketchPlan& p, cudaStream_t st) {
   int h = 0;
   SK_CUDA(cudaMemcpyAsync(&h, p.d_status, sizeof(int), cudaMemcpyDeviceToHost, st));

@@ -879,6 +879,49 @@ static sk_status sgmres_impl(const sk_op* A, const double* b, double* x, int d, 
   return result;
 }
 
+// Device workspace of one sgmres_solve call: the buffers sgmres_impl
+// allocates, in the same order, each rounded up to 256 bytes.
+extern "C" size_t sk_workspace_bytes(const sk_op* A, int d, int k, int s, const sk_opts* opts) {
+  if (!A || d < 1 || k < 1 || k > d || k > kMaxK || s < d + 1 || d > 768) return 0;
+  sk_opts o;
+  resolve_opts(opts, &o, d);
+  if (!(o.basis == SK_F64 || o.basis == SK_F32 || o.basis == SK_BF16)) return 0;
+  auto r = [](size_t b) { return (b + 255) & ~(size_t)255; };
+  const int64_t n = A->n;
+  const size_t esz = dtype_size(o.basis);
+  const bool iter = o.iter_chunk != 0;
+  const bool cheb = o.basis_kind == SK_BASIS_CHEBYSHEV;
+  size_t t = 0;
+  // basis buffers
+  t += r((size_t)((n + 7) / 8) * 8 * (d + 1) * esz);
+  if (o.basis == SK_F64) t += r((size_t)n * 8);
+  int pg = 0, pe = 0;
+  size_t psm = 0;
+  if (o.persistent && !iter && !cheb && persist_shape(A, o.basis, k, &pg, &pe, &psm))
+    t += r(2 * sizeof(unsigned)) + r(sizeof(int)) + r((size_t)3 * pg * (kMaxK + 1) * 8);
+  const int nblk_cap = basis_grid(n, 1);
+  t += r(((size_t)2 * d * k + 2 * (size_t)d + (size_t)(d + 1) * d + (size_t)nblk_cap * (kMaxK + 1) + 2 +
+          (size_t)d * (kMaxK + 1)) * 8);
+  t += r(8 * sizeof(unsigned)) + r(2 * sizeof(int));
+  if (cheb) t += r((size_t)(d + 1) * 8) + r((size_t)(d + 1) * nblk_cap * 8);
+  // the sketch plan and its workspaces
+  sk_sketch sks{o.sketch, n, s, o.zeta, o.seed};
+  SketchPlan sp;
+  SrhtPlan hp;
+  t += sketch_plan_shape(sks, &sp, &hp);
+  auto ws = [&](int c, sk_dtype dt, bool blk) {
+    return sks.kind == SK_SRHT ? srht_ws_doubles(hp, c, blk) : plan_ws_doubles(sp, c, dt, blk);
+  };
+  t += r((size_t)n * 8) + r((size_t)s * 8) + 2 * r((size_t)s * (d + 1) * 8) + 2 * r((size_t)d * 8) +
+       r((size_t)((d + kQrNb - 1) / kQrNb) * kQrNb * kQrNb * 8) + r((size_t)d * 8) + r(ws(1, SK_F64, false) * 8);
+  size_t wsb = ws(d + 1, o.basis, true);
+  for (int c = 1; iter && c <= o.iter_chunk + 1 && c <= d + 1; ++c) wsb = std::max(wsb, ws(c, o.basis, true));
+  t += r(wsb * 8);
+  if (iter) t += r(2 * sizeof(int));
+  t += r((size_t)vec_grid(n) * 8) + r(2 * sizeof(unsigned)) + r(4 * 8) + r(8);
+  return t;
+}
+
 extern "C" sk_status sgmres_solve(const sk_op* A, const double* b, double* x, int d, int k, int s, double tol,
                                   const sk_opts* opts, sk_info* info, void* stream) {
   SK_CHECK_ARG(A != nullptr && b != nullptr && x != nullptr, "NULL argument");

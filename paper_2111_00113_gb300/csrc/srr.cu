@@ -670,11 +670,15 @@ gram_kernel(const double* __restrict__ X, int64_t n, int b, double* __restrict__
   if (threadIdx.x == 0) { G[i + j * b] = p; G[j + i * b] = p; }
 }
 
-// Cholesky G = R^T R (upper R, in place), one thread; *fail on a non-positive pivot
-__global__ void chol_kernel(double* G, int b, int* fail) {
+// Cholesky G + sigma I = R^T R (upper R, in place), one thread, with
+// sigma = shift * trace(G) (0 for shift = 0); *fail on a non-positive pivot
+__global__ void chol_kernel(double* G, int b, double shift, int* fail) {
   if (threadIdx.x != 0) return;
+  double tr = 0;
+  for (int j = 0; j < b; ++j) tr += G[j + j * b];
+  const double sigma = shift * tr;
   for (int j = 0; j < b; ++j) {
-    double a = G[j + j * b];
+    double a = G[j + j * b] + sigma;
     for (int k = 0; k < j; ++k) a -= G[k + j * b] * G[k + j * b];
     if (!(a > 0)) { *fail = 1; return; }
     const double rjj = sqrt(a);
@@ -723,11 +727,29 @@ colnorm_kernel(const double* __restrict__ X, int64_t n, double* __restrict__ nrm
   if (threadIdx.x == 0) nrm[blockIdx.x] = sqrt(p);
 }
 
-// Q with orthonormal columns spanning X (CholeskyQR, twice), in place
+// X[:, c] *= f[c] and Y[:, c] *= f[c], f = 1 / nrm
+__global__ void scale_two_kernel(double* __restrict__ X, double* __restrict__ Y, int64_t n, int b,
+                                 const double* __restrict__ nrm) {
+  const int64_t total = n * b;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
+    const double f = 1.0 / nrm[q / n];
+    X[q] *= f;
+    Y[q] *= f;
+  }
+}
+
+// Q with orthonormal columns spanning X, in place: shifted CholeskyQR3
+// (Fukaya, Kannan, Nakatsukasa, Yamamoto, Yanagisawa, "Shifted Cholesky QR
+// for computing the QR factorization of ill-conditioned matrices", SIAM J.
+// Sci. Comput. 2020): a first pass on X^T X + sigma I with sigma =
+// 11 (n b + b (b + 1)) u ||X||_F^2 makes the factor well enough conditioned
+// for two plain CholeskyQR passes (condition numbers up to about 1/u).
 static sk_status orthonormalize(double* X, int64_t n, int b, double* G, int* fail, cudaStream_t st) {
-  for (int pass = 0; pass < 2; ++pass) {
+  const double u = 1.1102230246251565e-16;
+  for (int pass = 0; pass < 3; ++pass) {
     gram_kernel<<<b * b, kSrrThreads, 0, st>>>(X, n, b, G);
-    chol_kernel<<<1, 32, 0, st>>>(G, b, fail);
+    const double shift = pass == 0 ? 11.0 * ((double)n * b + (double)b * (b + 1)) * u : 0.0;
+    chol_kernel<<<1, 32, 0, st>>>(G, b, shift, fail);
     right_trsm_kernel<<<grid_for(n, 256, 8 * num_sms()), 256, 0, st>>>(X, n, b, G);
   }
   SK_CUDA(cudaGetLastError());
@@ -779,7 +801,7 @@ extern "C" sk_status srr_basis(const sk_op* A, const void* B, int64_t ldb, int d
 }
 
 extern "C" sk_status srr_restarted(const sk_op* A, const double* Omega, int b, int p, int nev, double lo, double hi,
-                                   int max_restarts, const sk_opts* opts, double* lam_re, double* lam_im,
+                                   int max_restarts, int filter_degree, const sk_opts* opts, double* lam_re, double* lam_im,
                                    double* X_re, double* X_im, double* rhat, int* nconv, int* restarts,
                                    double* history, void* stream) {
   SK_CHECK_ARG(A != nullptr && Omega != nullptr && lam_re != nullptr && X_re != nullptr, "NULL argument");
@@ -788,6 +810,7 @@ extern "C" sk_status srr_restarted(const sk_op* A, const double* Omega, int b, i
   SK_CHECK_ARG(nev >= 1 && nev <= b, "need 1 <= nev <= b");
   SK_CHECK_ARG(hi > lo && std::isfinite(lo) && std::isfinite(hi), "need finite lo < hi");
   SK_CHECK_ARG(max_restarts >= 1, "max_restarts >= 1");
+  SK_CHECK_ARG(filter_degree >= 0 && filter_degree <= 100000, "0 <= filter_degree <= 100000");
   cudaStream_t st = (cudaStream_t)stream;
   const int d = b * p;
   sk_opts o;
@@ -808,6 +831,8 @@ extern "C" sk_status srr_restarted(const sk_op* A, const double* Omega, int b, i
   Xim = Xre + (size_t)n * b;
   SK_TRY(sc.alloc(&nrm, 2 * b));
   SK_TRY(sc.alloc(&fail, 1));
+  double* Yf = nullptr;
+  if (filter_degree > 0) SK_TRY(sc.alloc(&Yf, (size_t)3 * n * b));
   SK_TRY(sc.alloc(&src, b));
   SK_CUDA(cudaMemsetAsync(fail, 0, sizeof(int), st));
   SK_CUDA(cudaMemcpyAsync(X, Omega, sizeof(double) * (size_t)n * b, cudaMemcpyDeviceToDevice, st));
@@ -817,11 +842,34 @@ extern "C" sk_status srr_restarted(const sk_op* A, const double* Omega, int b, i
   double cut = hi;
   int t = 0, conv = 0;
   for (; t < max_restarts; ++t) {
-    // B_0 = orth(X); the block Chebyshev basis for [lo, cut]
+    // B_0 = orth(X), optionally orth(T_m((A - c)/rho) orth(X)); the block
+    // Chebyshev basis for [lo, cut]
     SK_TRY(orthonormalize(X, n, b, G, fail, st));
-    SK_CUDA(cudaMemcpyAsync(Bk, X, sizeof(double) * (size_t)n * b, cudaMemcpyDeviceToDevice, st));
     const double c = 0.5 * (lo + cut), rho = 0.5 * (cut - lo), gamma = rho / 4.0;
     const int g = grid_for(n * b, 256, 16 * num_sms());
+    if (filter_degree > 0) {
+      // Y_1 = (A - c) Y_0 / rho, Y_{j+1} = 2 (A - c) Y_j / rho - Y_{j-1}; after
+      // every 10th step both carried blocks divided by the newest one's
+      // column norms
+      double* Y[3] = {Yf, Yf + (size_t)n * b, Yf + (size_t)2 * n * b};
+      SK_CUDA(cudaMemcpyAsync(Y[0], X, sizeof(double) * (size_t)n * b, cudaMemcpyDeviceToDevice, st));
+      block_cheb_kernel<<<g, 256, 0, st>>>(Av, Y[0], nullptr, Y[1], b, c, 1.0 / rho, 0.0);
+      int i0 = 0, i1 = 1;
+      for (int j = 2; j <= filter_degree; ++j) {
+        const int i2 = 3 - i0 - i1;
+        block_cheb_kernel<<<g, 256, 0, st>>>(Av, Y[i1], Y[i0], Y[i2], b, c, 2.0 / rho, 0.5 * rho);
+        i0 = i1;
+        i1 = i2;
+        if (j % 10 == 0) {
+          colnorm_kernel<<<b, kSrrThreads, 0, st>>>(Y[i1], n, nrm);
+          scale_two_kernel<<<g, 256, 0, st>>>(Y[i0], Y[i1], n, b, nrm);
+        }
+      }
+      SK_CUDA(cudaGetLastError());
+      SK_CUDA(cudaMemcpyAsync(X, Y[i1], sizeof(double) * (size_t)n * b, cudaMemcpyDeviceToDevice, st));
+      SK_TRY(orthonormalize(X, n, b, G, fail, st));
+    }
+    SK_CUDA(cudaMemcpyAsync(Bk, X, sizeof(double) * (size_t)n * b, cudaMemcpyDeviceToDevice, st));
     for (int j = 0; j <= p - 1; ++j) {
       const double* Bj = Bk + (size_t)j * n * b;
       const double* Bm = j >= 1 ? Bk + (size_t)(j - 1) * n * b : nullptr;

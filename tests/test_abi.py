@@ -92,3 +92,25 @@ def test_invalid_arguments_rejected_on_host(native):
     assert b"truncated-Arnoldi" in lib.sk_last_error()
     lib.sk_op_destroy(hT)
     lib.sk_op_destroy(h)
+
+
+def test_workspace_bytes_accounts_for_the_basis(native):
+    # sk_workspace_bytes on the bench workload (1024^2, d = 300, s = 600):
+    # the basis n x (d+1) dominates; the FP64 form adds the FP64 basis and
+    # the stored A b_j; invalid shapes give 0.  Host-only (no device needed).
+    lib = native.lib
+    h = C.c_void_p()
+    coef = (C.c_double * 5)(4, -0.9, -1.1, -0.9, -1.1)
+    assert lib.sk_op_stencil5(C.byref(h), 1024, 1024, coef, None) == native.SK_OK
+    o = native.SkOpts()
+    lib.sk_opts_default(C.byref(o))
+    n, d, s = 1 << 20, 300, 600
+    o.basis = native.SK_F32
+    b32 = lib.sk_workspace_bytes(h, d, 2, s, C.byref(o))
+    assert n * (d + 1) * 4 < b32 < 1.15 * n * (d + 1) * 4
+    o.basis = native.SK_F64
+    b64 = lib.sk_workspace_bytes(h, d, 2, s, C.byref(o))
+    assert b64 - b32 >= n * (d + 1) * 4 + n * 8
+    assert lib.sk_workspace_bytes(h, d, 2, d, C.byref(o)) == 0  # s < d + 1
+    assert lib.sk_workspace_bytes(h, 0, 1, s, C.byref(o)) == 0
+    lib.sk_op_destroy(h)

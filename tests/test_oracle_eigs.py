@@ -257,3 +257,43 @@ def test_restarted_srr_matches_arpack_on_clustered_spectrum():
     tr = np.array([eigs.eig_residual(A, lam[i], out["X"][:, i]) for i in range(nev)]) / An
     assert tr.max() <= 1e-8
     assert np.abs(np.sort(lam.real)[::-1] - ref[:nev]).max() <= 1e-7
+
+
+def test_chebyshev_filter_is_chebyshev_polynomial_on_a_diagonal():
+    # on a diagonal matrix column q of the filtered block is, up to a
+    # positive scale, T_m((lam - c)/dx) * Q[:, q] (numpy's chebval)
+    n, m, c, dx = 300, 37, 0.6, 0.55
+    lam = np.linspace(-0.2, 1.3, n)
+    A = np.diag(lam)
+    Q = np.column_stack([synth.randn(60 + i, n) for i in range(3)])
+    Y = eigs.chebyshev_filter(A, Q, m, c, dx)
+    coef = np.zeros(m + 1)
+    coef[m] = 1.0
+    T = np.polynomial.chebyshev.chebval((lam - c) / dx, coef)
+    for q in range(3):
+        ref = T * Q[:, q]
+        scale = (Y[:, q] @ ref) / (ref @ ref)
+        assert scale > 0
+        assert np.linalg.norm(Y[:, q] - scale * ref) <= 1e-10 * np.linalg.norm(Y[:, q])
+
+
+def test_filtered_restarted_srr_matches_arpack_in_few_restarts():
+    # the 48 x 48 clustered case of the test above with a degree-60 filter of
+    # the start block: ARPACK's eigenvalues within 1e-7 and true residuals
+    # <= 1e-8 ||A|| in fewer restarts than without the filter
+    import scipy.sparse.linalg as spla
+    N, b, p, nev = 48, 12, 16, 6
+    shift = synth.uniform(1, N * N)
+    A = operators.stencil5_matrix(N, N, synth.conv_diff_coef(N, 10.0), shift)
+    An = 8 + shift.max()
+    ref = np.sort(spla.eigs(A, k=nev + 4, which="LR", return_eigenvectors=False, tol=1e-13).real)[::-1]
+    Om = np.column_stack([synth.randn(200 + i, N * N) for i in range(b)])
+    d = b * p
+    skf = lambda t: (lambda M: sketch.sparse_sign_apply(7 + t, 2 * d, hashing.default_zeta(d), M))
+    plain = eigs.srr_restarted(A, Om, p, nev, -0.5, 8.0, 30, skf, tau=1e-8 * An)
+    out = eigs.srr_restarted(A, Om, p, nev, -0.5, 8.0, 30, skf, tau=1e-8 * An, filter_degree=60)
+    assert out["restarts"] < plain["restarts"]
+    lam = out["lam"][:nev]
+    tr = np.array([eigs.eig_residual(A, lam[i], out["X"][:, i]) for i in range(nev)]) / An
+    assert tr.max() <= 1e-8
+    assert np.abs(np.sort(lam.real)[::-1] - ref[:nev]).max() <= 1e-7
