@@ -136,34 +136,46 @@ def test_chebyshev_argument_errors(skg):
 
 def test_laplace_workload_full_size(skg):
     # 1024^2 Neumann Laplacian, f = A GRF(seed 5, 64 cells), d = 300, s = 600,
-    # Chebyshev c = 4, dx = 4.  FP64 basis: the residual after each of the
-    # first 10 cycles within 1.5x of the oracle's stored history
-    # (tests/golden/laplace_oracle.json, written by make_laplace_reference.py),
-    # and 1e-6 reached within 1.3x the oracle's cycle count: each cycle gains
-    # only 10-20% here and kappa_2(T) ~ 3e9, so rounding differences compound
-    # over 30+ cycles (changing only the summation order of g = S r moved the
-    # GPU's count from 30 to 39; the oracle takes 34).  FP32 basis: reaches
-    # the tolerance.
+    # Chebyshev c = 4, dx = 4, FP64 basis.  Each cycle gains only 10-20 %
+    # here, so rounding differences compound: the oracle itself, with its
+    # sketches perturbed at the 1e-15 level, takes 27 to 34 cycles
+    # (tests/golden/laplace_spread.json, written by make_laplace_spread.py;
+    # unperturbed: 34, laplace_oracle.json).  Every cycle's residual (cycle by
+    # cycle: a restart from the returned x is the next cycle) must lie within
+    # 3x of the envelope of those runs (measured: within 1.02x through cycle
+    # 8, then up to 2.05x above it at cycle 24, when the GPU takes 27 cycles),
+    # and the cycle count within their range +-2.  FP32 basis: reaches the
+    # tolerance.
     import json
     import os
     import torch
     W = synth.WORKLOADS["laplace"]
     N = W["N"]
-    with open(os.path.join(os.path.dirname(__file__), "golden", "laplace_oracle.json")) as fh:
-        ref = json.load(fh)
+    gold = os.path.join(os.path.dirname(__file__), "golden")
+    with open(os.path.join(gold, "laplace_oracle.json")) as fh:
+        runs = [json.load(fh)["relres"]]
+    with open(os.path.join(gold, "laplace_spread.json")) as fh:
+        runs += list(json.load(fh)["runs"].values())
+    counts = [len(h) for h in runs]
     A = operators.neumann_laplacian_matrix(N, N)
     f = A @ synth.grf(W["x_seed"], N, W["ell"])
     op, _ = _neumann(N, N, skg)
     b = torch.tensor(f, device="cuda")
     kw = dict(zeta=W["zeta"], seed=7, cheb=W["cheb"])
     x = torch.zeros_like(b)
-    for c in range(10):
+    cycles = 0
+    for c in range(max(counts) + 3):
         x, info = skg.sgmres_solve(op, b, W["d"], W["k"], W["s"], 1e-300, x0=x, maxit=1, **kw)
         rel = np.linalg.norm(f - A @ x.cpu().numpy()) / np.linalg.norm(f)
-        assert rel <= 1.5 * ref["relres"][c] and ref["relres"][c] <= 1.5 * rel, (c, rel, ref["relres"][c])
+        live = [h[c] for h in runs if c < len(h)]
+        if live:
+            assert min(live) / 3.0 <= rel <= 3.0 * max(live), (c, rel, min(live), max(live))
+        cycles = c + 1
+        if rel <= W["tol"]:
+            break
+    assert min(counts) - 2 <= cycles <= max(counts) + 2, (cycles, counts)
     x, info = skg.sgmres_solve(op, b, W["d"], W["k"], W["s"], W["tol"], maxit=100, **kw)
-    assert info["status"] == 0
-    assert info["cycles"] <= int(np.ceil(1.3 * ref["cycles"])), (info["cycles"], ref["cycles"])
+    assert info["status"] == 0 and info["cycles"] == cycles
     assert np.linalg.norm(f - A @ x.cpu().numpy()) <= W["tol"] * np.linalg.norm(f)
     x, info = skg.sgmres_solve(op, b, W["d"], W["k"], W["s"], W["tol"], maxit=100, basis=torch.float32, **kw)
     assert info["status"] == 0, info
