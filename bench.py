@@ -200,7 +200,9 @@ def run_reference(args):
 
 
 def _bench_sketch(skg, dev, peak):
-    """Standalone sketch_apply on the basis shape (2^20 x 301, s = 600)."""
+    """Standalone sketch on the basis shape (2^20 x 301, s = 600): a reusable
+    plan (tables built once, outside the timing) applied to the block, and
+    the one-shot sketch_apply (plan built inside every call) beside it."""
     import torch
     n, c, s = 1 << 20, 301, 600
     g = torch.Generator(device=dev).manual_seed(0)
@@ -208,20 +210,25 @@ def _bench_sketch(skg, dev, peak):
     for name, dt, kind in (("sparse_f32", torch.float32, "sparse"), ("sparse_f64", torch.float64, "sparse"),
                            ("srht_f32", torch.float32, "srht")):
         B = torch.randn((c, n), generator=g, device=dev, dtype=dt).t()
-        skg.sketch_apply(B, s, 12, 7, kind=kind)
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record()
-        reps = 3
-        for _ in range(reps):
-            skg.sketch_apply(B, s, 12, 7, kind=kind)
-        e1.record()
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / reps
-        gbs = B.element_size() * n * c / (ms / 1000) / 1e9
-        out[name] = {"ms": round(ms, 3), "GB/s": round(gbs, 1), "frac_hbm": round(gbs / peak, 4)}
-        del B
+        plan = skg.SketchPlan(n, s, 12, 7, kind=kind)
+        res = empty = None
+        for mode in ("plan", "one_shot"):
+            f = (lambda: plan(B, out=res)) if mode == "plan" else (lambda: skg.sketch_apply(B, s, 12, 7, kind=kind))
+            res = f() if res is None else res
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            reps = 5
+            for _ in range(reps):
+                f()
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            gbs = B.element_size() * n * c / (ms / 1000) / 1e9
+            out[name + ("" if mode == "plan" else "_one_shot")] = {"ms": round(ms, 3), "GB/s": round(gbs, 1),
+                                                                  "frac_hbm": round(gbs / peak, 4)}
+        del B, plan, empty
     return out
 
 
@@ -247,6 +254,29 @@ def _bench_srr(skg, dev):
         ms = (time.perf_counter() - t) * 1000 / reps
         res[name] = {"ms": round(ms, 2), "nconv_1e-8": r["nconv"], "max_rhat": float(r["rhat"].max()),
                      "lam_top": float(r["lam"].real[0])}
+    # restarted sRR (block Chebyshev bases, b = 16, p = 12, degree-150
+    # filter of each start block, stabilized sRR), FP64, to 1e-8 ||A||
+    anorm = 8.589148193315218  # ||A||_2 of this operator (tests/golden/eig_oracle.json)
+    Om = torch.tensor(np.column_stack([synth.randn(500 + i, N * N) for i in range(16)]), device=dev)
+    kw = dict(tau=1e-8 * anorm, seed=7)
+    skg.srr_restarted(op, Om, 12, W["nev"], -0.5, 9.0, 40, 150, **kw)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    r = skg.srr_restarted(op, Om, 12, W["nev"], -0.5, 9.0, 40, 150, **kw)
+    torch.cuda.synchronize()
+    ms = (time.perf_counter() - t) * 1000
+    X = r["X"]
+    tr = []
+    for i in range(W["nev"]):
+        xr, xi = X[:, i].real.contiguous(), X[:, i].imag.contiguous()
+        lam = r["lam"][i]
+        rr = op.apply(xr) - lam.real * xr + lam.imag * xi
+        ri = op.apply(xi) - lam.real * xi - lam.imag * xr
+        tr.append(float(torch.sqrt((rr * rr).sum() + (ri * ri).sum()) / anorm))
+    res["restarted_f64_basis"] = {"ms": round(ms, 2), "restarts": r["restarts"], "nconv_1e-8": r["nconv"],
+                                  "max_true_residual_over_normA": max(tr), "lam_top": float(r["lam"].real[0]),
+                                  "config": "b=16, p=12 (d=192, s=384), Chebyshev filter degree 150, "
+                                            "stabilized sRR (trunc 1e13), tau 1e-8 ||A||"}
     return res
 
 
@@ -439,6 +469,22 @@ def run_ours(args):
         "gpu_launches": int(sum(i["launches"] for i in infos)),
     }
     if not args.no_extras:
+        # the other forms of the same workload: SRHT sketch (FP32 basis) and BF16 basis
+        forms = {}
+        for fname, fkw in (("srht_f32", dict(kw, basis=torch.float32, sketch="srht")),
+                           ("bf16", dict(kw, basis=torch.bfloat16, sketch="sparse", maxit=400))):
+            x.zero_()
+            skg.sgmres_solve(A, b, W["d"], W["k"], W["s"], W["tol"], x0=x, **fkw)
+            barrier()
+            e0.record(stream)
+            x.zero_()
+            _, finfo = skg.sgmres_solve(A, b, W["d"], W["k"], W["s"], W["tol"], x0=x, **fkw)
+            e1.record(stream)
+            barrier()
+            fms = e0.elapsed_time(e1)
+            forms[fname] = {"solves_per_s": round(1000.0 / fms, 3), "ms": round(fms, 2), "cycles": finfo["cycles"],
+                            "relres": finfo["relres"], "status": finfo["status"]}
+        out["forms"] = forms
         out["sketch_apply"] = _bench_sketch(skg, dev, peak)
         out["srr"] = _bench_srr(skg, dev)
         out["batched"] = _bench_batched(skg, dev)

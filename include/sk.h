@@ -116,6 +116,23 @@ typedef struct {
 sk_status sketch_apply(const sk_sketch* S, const void* B, int64_t ldb, int ncols,
                        sk_dtype dtype, double* SB, void* stream);
 
+/* A reusable plan for one sketch (sparse sign: the row-sorted index tables;
+ * SRHT: the signs and sampled rows), built once on the device by
+ * sk_sketch_plan_create (allocates the tables; synchronises `stream`, and
+ * returns SK_EHASH as sketch_apply does) and applied by sk_sketch_plan_apply
+ * to any number of column blocks with the same n: SB = S * B with the
+ * arguments, layout and accuracy of sketch_apply.  An apply allocates only
+ * when it needs more partial-sum workspace than every earlier apply on the
+ * plan (then it synchronises `stream` first).  Applies on one plan share
+ * that workspace: issue them on one stream, or serialise them.
+ * sk_sketch_plan_destroy frees the plan (synchronous; the plan's work must
+ * be finished or ordered before it). */
+typedef struct sk_sketch_plan sk_sketch_plan;
+sk_status sk_sketch_plan_create(const sk_sketch* S, sk_sketch_plan** plan, void* stream);
+sk_status sk_sketch_plan_apply(sk_sketch_plan* plan, const void* B, int64_t ldb, int ncols, sk_dtype dtype,
+                               double* SB, void* stream);
+void sk_sketch_plan_destroy(sk_sketch_plan* plan);
+
 /* sketch_apply for the sparse sign sketch without any device allocation.
  * The paper has no counterpart: this is a deployment variant for callers
  * that cannot call cudaMalloc on their hot path (plugins inside another

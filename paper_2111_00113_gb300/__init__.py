@@ -152,6 +152,40 @@ def sketch_apply(B, s, zeta=0, seed=7, kind="sparse"):
     return out[:, 0] if vec else out
 
 
+class SketchPlan:
+    """A sketch whose index tables (sparse sign) or signs and rows (SRHT) are
+    built once on the device and reused: plan(B) = S @ B as sketch_apply."""
+
+    def __init__(self, n, s, zeta=0, seed=7, kind="sparse"):
+        self.n, self.s = int(n), int(s)
+        self._h = C.c_void_p()
+        sk = _sketch_struct(kind, n, s, zeta, seed)
+        N.check(N.lib.sk_sketch_plan_create(C.byref(sk), C.byref(self._h), _stream()))
+
+    def __call__(self, B, out=None):
+        vec = B.dim() == 1
+        Bc = colmajor(B)
+        if Bc.dtype not in _DT:
+            raise ValueError("dtype must be float64, float32 or bfloat16")
+        n, c = Bc.shape
+        if n != self.n:
+            raise ValueError("B has %d rows, the plan %d" % (n, self.n))
+        ldb = Bc.stride(1) if c > 1 else n
+        if out is None:
+            out = empty_colmajor(self.s, c, torch.float64, Bc.device)
+        N.check(N.lib.sk_sketch_plan_apply(self._h, _ptr(Bc), ldb, c, _DT[Bc.dtype], _ptr(out), _stream()))
+        return out[:, 0] if vec else out
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            try:
+                N.lib.sk_sketch_plan_destroy(h)
+            except Exception:
+                pass
+            self._h = None
+
+
 def sketch_apply_noalloc(B, s, zeta=0, seed=7):
     """sketch_apply (sparse sign) that allocates no device memory.
 

@@ -18,7 +18,7 @@ EXPORTED = [
     "sk_op_stencil5", "sk_op_diffusion_var", "sk_op_csr", "sk_op_transpose", "sk_op_apply", "sk_op_n",
     "sk_op_destroy", "sketch_apply", "sketch_apply_noalloc", "sk_opts_default", "trunc_arnoldi_basis", "sgmres_solve", "srr_eigs",
     "sk_last_error", "sk_status_string", "sk_op_param_grad", "sgmres_solve_batched", "srr_basis", "srr_restarted",
-    "sk_workspace_bytes",
+    "sk_workspace_bytes", "sk_sketch_plan_create", "sk_sketch_plan_apply", "sk_sketch_plan_destroy",
 ]
 
 
@@ -83,6 +83,9 @@ def _load():
         "srr_restarted": (st, [P, P, I, I, I, D, D, I, I, C.POINTER(SkOpts), C.POINTER(D), C.POINTER(D), P, P,
                                C.POINTER(D), C.POINTER(I), C.POINTER(I), C.POINTER(D), P]),
         "sk_workspace_bytes": (C.c_size_t, [P, I, I, I, C.POINTER(SkOpts)]),
+        "sk_sketch_plan_create": (st, [C.POINTER(SkSketch), C.POINTER(P), P]),
+        "sk_sketch_plan_apply": (st, [P, P, I64, I, I, P, P]),
+        "sk_sketch_plan_destroy": (None, [P]),
         "sk_last_error": (C.c_char_p, []),
         "sk_status_string": (C.c_char_p, [I]),
     }

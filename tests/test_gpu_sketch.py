@@ -134,3 +134,23 @@ def test_sparse_sign_single_column_unaligned(skg):
     got = skg.sketch_apply(Xt, s, zeta, 4).cpu().numpy()
     ref = sketch.sparse_sign_apply(4, s, zeta, X[1:, None])[:, 0]
     assert _relf(got, ref) <= 1e-12
+
+
+@pytest.mark.parametrize("kind", ["sparse", "srht"])
+def test_sketch_plan_reused_across_calls(skg, kind):
+    # one plan applied to blocks of different widths and types (its
+    # workspace grows on the wider ones): each result is the oracle's sketch
+    # of the values the GPU holds, as sketch_apply gives it
+    import torch
+    n, s, zeta, seed = 1024 * 6 + 77, 300, 10, 4
+    plan = skg.SketchPlan(n, s, zeta, seed, kind=kind)
+    rng = np.random.default_rng(3)
+    for c, dt, tol in ((3, torch.float64, 1e-12), (40, torch.float32, 1e-5), (1, torch.float64, 1e-12),
+                       (17, torch.bfloat16, 1e-5), (3, torch.float64, 1e-12)):
+        X = rng.standard_normal((n, c))
+        Xt = _tensor(X, dt)
+        held = Xt.to(torch.float64).cpu().numpy()
+        got = plan(Xt).cpu().numpy()
+        ref = sketch.apply(kind, seed, s, zeta, held)
+        assert _relf(got, ref) <= tol, (c, dt)
+        assert _relf(got, skg.sketch_apply(Xt, s, zeta, seed, kind=kind).cpu().numpy()) <= tol
