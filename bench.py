@@ -130,11 +130,12 @@ def _problem(dev):
     return W, N, coef, f, torch.tensor(f, device=dev)
 
 
-def _oracle_cycle_seconds(d_sample=None):
+def _oracle_cycle_seconds(d_sample=None, threads=1):
     """Time one oracle restart cycle of the scale workload in a child process.
 
-    The child pins numpy/BLAS to one thread.  d_sample < d runs the first
-    d_sample Arnoldi steps only (the caller scales the time by d/d_sample).
+    The child pins numpy/BLAS to `threads` threads (1 = the reference
+    number).  d_sample < d runs the first d_sample Arnoldi steps only (the
+    caller scales the time by d/d_sample).
     """
     code = r"""
 import json, sys, time
@@ -153,7 +154,8 @@ x, info = krylov.sgmres_cycle(A, f, np.zeros(N * N), d, W["k"], lambda M: S @ M)
 t2 = time.time()
 print(json.dumps({"plan_s": t1 - t0, "cycle_s": t2 - t1, "d": d}))
 """ % (ROOT, repr(d_sample))
-    env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    t = str(int(threads))
+    env = dict(os.environ, OPENBLAS_NUM_THREADS=t, OMP_NUM_THREADS=t, MKL_NUM_THREADS=t)
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=900)
     if r.returncode != 0:
         raise RuntimeError("oracle sample failed: " + r.stderr[-2000:])
@@ -497,6 +499,12 @@ def run_ours(args):
             out["cpu_baseline"] = {"value": v, "unit": "solves/s", "cores": 1, "kind": "oracle",
                                    "sample": "one full FP64 oracle restart cycle of this workload (%.1f s, one "
                                              "thread) x %d oracle cycles per solve" % (r["cycle_s"], ncyc)}
+            nproc = os.cpu_count() or 1
+            rm = _oracle_cycle_seconds(None, threads=nproc)
+            out["cpu_baseline"]["all_cores"] = {
+                "value": 1.0 / (ncyc * rm["cycle_s"]), "unit": "solves/s", "cores": nproc,
+                "sample": "the same cycle with numpy/BLAS on %d threads (%.1f s); the sparse products stay "
+                          "single-threaded" % (nproc, rm["cycle_s"])}
         except Exception as e:  # report, do not hide
             out["cpu_baseline"] = {"value": None, "error": str(e)[:300]}
     if rank == 0:
