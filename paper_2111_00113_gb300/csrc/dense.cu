@@ -6,10 +6,10 @@
 // The QR works in place on an augmented s x ncols matrix: the first nq
 // columns are factored, the remaining columns (the sketched right-hand side
 // g for sGMRES, S A B for sRR) receive Q^T through the trailing updates.
-// Panel p is factored by one CTA (reflectors stored below the diagonal,
-// v_0 on the diagonal, R's diagonal in rdiag, tau = 2 / v^T v) together with
-// its compact-WY factor T_p (Q_p = I - V T_p V^T); the trailing update
-// A <- A - V T_p^T (V^T A) runs one CTA per column.
+// Panel p is factored (reflectors stored below the diagonal, v_0 on the
+// diagonal, R's diagonal in rdiag, tau = 2 / v^T v) together with its
+// compact-WY factor T_p (Q_p = I - V T_p V^T); the trailing update
+// A <- A - V T_p^T (V^T A) runs one 8-CTA cluster per column.
 #include <cmath>
 #include <cooperative_groups.h>
 
@@ -373,78 +373,106 @@ qr_panel_cluster_kernel(double* __restrict__ Aug, int s, int p0, int nbc, double
   }
 }
 
-// One column a (rows p0..s-1 used) gets Q_p^T of panel p: a <- a - V T^T
-// (V^T a), V = the panel's reflectors (columns p0.., rows from their
-// diagonal), T its compact-WY factor.  The whole CTA takes part; `red`, `u`
-// and `w` are its shared scratch.  Ends with every thread's writes to a
-// pending (the caller synchronises before re-reading a).
-__device__ __forceinline__ void wy_apply_column(double* __restrict__ a, const double* __restrict__ V, int s, int p0,
-                                                int nbc, const double* __restrict__ Tp,
-                                                double (*red)[kQrNb], double* u, double* w) {
+// Q_p^T of panels p_first .. p_last - 1, in order, applied to column
+// c = c0 + blockIdx.x / kWyCluster by a cluster of kWyCluster CTAs: CTA q
+// always owns rows [q per, (q+1) per) of the column (per = ceil(s / 8)), so a
+// row is only ever read and written by its owner.  For each panel the CTAs'
+// partial sums of u = V^T a (over their rows at or below the panel's
+// diagonal) are pushed into every CTA's shared memory, one cluster barrier
+// publishes them, every CTA sums them in rank order (identical u
+// everywhere), forms w = T^T u and updates its rows: a <- a - V w.  The same
+// kernel serves the right-looking trailing update (one panel, many columns)
+// and the left-looking one (all earlier panels, the new columns), so the
+// sequential and the pipelined QR give identical columns.  The FP64 work of
+// one column is spread over 8 SMs (one SM's FP64 rate made the one-CTA
+// left-looking update, 16 columns x up to 18 panels, take ~240 us).
+static constexpr int kWyCluster = 8;
+static constexpr int kWyThreads = 128;
+
+__global__ void __launch_bounds__(kWyThreads)
+qr_apply_cluster_kernel(double* __restrict__ Aug, int s, int p_first, int p_last, int last_nbc, int c0,
+                        const double* __restrict__ Tws) {
+  cg::cluster_group cluster = cg::this_cluster();
+  __shared__ double slot[2][kWyCluster][kQrNb];
+  __shared__ double red[kWyThreads / 32][kQrNb];
+  __shared__ double uu[kQrNb];
+  __shared__ double w[kQrNb];
+  const int q = (int)cluster.block_rank();
+  const int c = c0 + (int)(blockIdx.x / kWyCluster);
+  double* a = Aug + (int64_t)c * s;
+  const int per = (s + kWyCluster - 1) / kWyCluster;
+  const int r_lo = q * per, r_hi = min(s, r_lo + per);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  double acc[kQrNb];
+  cluster.sync();  // every CTA of the cluster has started before the first remote store
+  for (int p = p_first; p < p_last; ++p) {
+    const int buf = (p - p_first) & 1;
+    const int p0 = p * kQrNb;
+    const int nbc = (p == p_last - 1) ? last_nbc : kQrNb;
+    const double* V = Aug + (int64_t)p0 * s;
+    const double* T = Tws + (int64_t)p * kQrNb * kQrNb;
+    __syncthreads();  // the previous panel's row updates (by other threads of this CTA) are visible
+    double acc[kQrNb];
 #pragma unroll
-  for (int i = 0; i < kQrNb; ++i) acc[i] = 0;
-  for (int r = p0 + threadIdx.x; r < s; r += blockDim.x) {
-    const double ar = a[r];
+    for (int i = 0; i < kQrNb; ++i) acc[i] = 0;
+    for (int r = max(r_lo, p0) + threadIdx.x; r < r_hi; r += blockDim.x) {
+      const double ar = a[r];
 #pragma unroll
-    for (int i = 0; i < kQrNb; ++i) {
-      if (i < nbc && r >= p0 + i) acc[i] += V[(int64_t)i * s + r] * ar;
+      for (int i = 0; i < kQrNb; ++i)
+        if (i < nbc && r >= p0 + i) acc[i] += V[(int64_t)i * s + r] * ar;
     }
-  }
-  const double part = warp_reduce_scatter16(acc);
-  if ((lane & 1) == 0) red[wid][lane >> 1] = part;
-  __syncthreads();
-  if (wid == 0) {
-    // u = V^T a, then w = T^T u (lane i: w_i = sum_{l <= i} T[l, i] u_l)
-    if (lane < kQrNb) {
+    const double part = warp_reduce_scatter16(acc);
+    if ((lane & 1) == 0) red[wid][lane >> 1] = part;
+    __syncthreads();
+    if (wid == 0 && lane < kQrNb) {
       double t = 0;
-      for (int q = 0; q < nw; ++q) t += red[q][lane];
-      u[lane] = t;
+      for (int k = 0; k < nw; ++k) t += red[k][lane];
+      for (int k = 0; k < kWyCluster; ++k) cluster.map_shared_rank(&slot[buf][q][0], k)[lane] = t;
     }
-    __syncwarp();
-    if (lane < kQrNb) {
-      double t = 0;
-      for (int l = 0; l <= lane && l < nbc; ++l) t += Tp[l * kQrNb + lane] * u[l];
-      w[lane] = (lane < nbc) ? t : 0.0;
+    cluster.sync();
+    if (wid == 0) {
+      if (lane < kQrNb) {
+        double t = 0;
+        for (int k = 0; k < kWyCluster; ++k) t += slot[buf][k][lane];
+        uu[lane] = t;
+      }
+      __syncwarp();
+      if (lane < kQrNb) {
+        double t = 0;
+        for (int l = 0; l <= lane && l < nbc; ++l) t += T[l * kQrNb + lane] * uu[l];
+        w[lane] = (lane < nbc) ? t : 0.0;
+      }
     }
-  }
-  __syncthreads();
-  for (int r = p0 + threadIdx.x; r < s; r += blockDim.x) {
-    double d = 0;
+    __syncthreads();
+    for (int r = max(r_lo, p0) + threadIdx.x; r < r_hi; r += blockDim.x) {
+      double d = 0;
 #pragma unroll
-    for (int i = 0; i < kQrNb; ++i) {
-      if (i < nbc && r >= p0 + i) d += V[(int64_t)i * s + r] * w[i];
+      for (int i = 0; i < kQrNb; ++i)
+        if (i < nbc && r >= p0 + i) d += V[(int64_t)i * s + r] * w[i];
+      a[r] -= d;
     }
-    a[r] -= d;
   }
+  cluster.sync();  // no CTA leaves while another may still store into its shared memory
 }
 
-// Column c = c0 + blockIdx.x of Aug gets Q_p^T: a <- a - V T^T (V^T a).
-__global__ void __launch_bounds__(kQrTrailThreads)
-qr_trailing_kernel(double* __restrict__ Aug, int s, int p0, int nbc, int c0, const double* __restrict__ Tws) {
-  __shared__ double red[kQrTrailThreads / 32][kQrNb];
-  __shared__ double u[kQrNb];
-  __shared__ double w[kQrNb];
-  const int c = c0 + blockIdx.x;
-  wy_apply_column(Aug + (int64_t)c * s, Aug + (int64_t)p0 * s, s, p0, nbc, Tws, red, u, w);
-}
-
-// Left-looking form of the trailing updates: column c = c0 + blockIdx.x
-// gets Q_{np-1}^T ... Q_0^T, the full panels 0..np-1 applied in order (the
-// per-panel arithmetic of qr_trailing_kernel, so a column ends bit-identical
-// to the right-looking factorisation).
-__global__ void __launch_bounds__(kQrTrailThreads)
-qr_left_kernel(double* __restrict__ Aug, int s, int np, int c0, const double* __restrict__ Tws) {
-  __shared__ double red[kQrTrailThreads / 32][kQrNb];
-  __shared__ double u[kQrNb];
-  __shared__ double w[kQrNb];
-  double* a = Aug + (int64_t)(c0 + blockIdx.x) * s;
-  for (int p = 0; p < np; ++p) {
-    __syncthreads();  // the previous panel's writes to a are visible to every thread
-    wy_apply_column(a, Aug + (int64_t)p * kQrNb * s, s, p * kQrNb, kQrNb, Tws + (int64_t)p * kQrNb * kQrNb, red, u,
-                    w);
-  }
+// Panels p_first .. p_last - 1 (the last with last_nbc columns) applied to
+// columns [c0, c0 + ncols).
+static sk_status launch_wy_apply(double* Aug, int s, int p_first, int p_last, int last_nbc, int c0, int ncols,
+                                 const double* Tws, cudaStream_t st) {
+  if (ncols <= 0 || p_last <= p_first) return SK_OK;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)ncols * kWyCluster);
+  cfg.blockDim = dim3(kWyThreads);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = kWyCluster;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  SK_CUDA(cudaLaunchKernelEx(&cfg, qr_apply_cluster_kernel, Aug, s, p_first, p_last, last_nbc, c0, Tws));
+  return SK_OK;
 }
 
 // Factor panel [p0, p0+nbc) of Aug in place: the 8-CTA cluster kernel when
@@ -490,7 +518,7 @@ sk_status enqueue_qr(double* Aug, int s, int nq, int ncols, double* rdiag, doubl
     double* T = Tws + (int64_t)(p0 / kQrNb) * kQrNb * kQrNb;
     SK_TRY(factor_panel(Aug, s, p0, nbc, rdiag, tau, T, st));
     const int c0 = p0 + nbc;
-    if (ncols > c0) qr_trailing_kernel<<<ncols - c0, kQrTrailThreads, 0, st>>>(Aug, s, p0, nbc, c0, T);
+    SK_TRY(launch_wy_apply(Aug, s, p0 / kQrNb, p0 / kQrNb + 1, nbc, c0, ncols - c0, Tws, st));
   }
   SK_CUDA(cudaGetLastError());
   return SK_OK;
@@ -512,7 +540,7 @@ sk_status enqueue_qr_append(double* Aug, int s, int c0, int c1, int zc, double* 
   }
   long long nl = 0;
   if (c0 > 0) {
-    qr_left_kernel<<<c1 - c0, kQrTrailThreads, 0, st>>>(Aug, s, c0 / kQrNb, c0, Tws);
+    SK_TRY(launch_wy_apply(Aug, s, 0, c0 / kQrNb, kQrNb, c0, c1 - c0, Tws, st));
     ++nl;
   }
   for (int p0 = c0; p0 < c1; p0 += kQrNb) {
@@ -521,10 +549,10 @@ sk_status enqueue_qr_append(double* Aug, int s, int c0, int c1, int zc, double* 
     SK_TRY(factor_panel(Aug, s, p0, nbc, rdiag, tau, T, st));
     const int cn = p0 + nbc;
     if (c1 > cn) {
-      qr_trailing_kernel<<<c1 - cn, kQrTrailThreads, 0, st>>>(Aug, s, p0, nbc, cn, T);
+      SK_TRY(launch_wy_apply(Aug, s, p0 / kQrNb, p0 / kQrNb + 1, nbc, cn, c1 - cn, Tws, st));
       ++nl;
     }
-    qr_trailing_kernel<<<1, kQrTrailThreads, 0, st>>>(Aug, s, p0, nbc, zc, T);
+    SK_TRY(launch_wy_apply(Aug, s, p0 / kQrNb, p0 / kQrNb + 1, nbc, zc, 1, Tws, st));
     nl += 2;
   }
   SK_CUDA(cudaGetLastError());

@@ -6,7 +6,6 @@ namespace sk {
 
 static constexpr int kQrNb = 16;            // panel width of the blocked Householder QR
 static constexpr int kQrPanelThreads = 512;
-static constexpr int kQrTrailThreads = 256;
 
 sk_status enqueue_hbar_product(const double* SB, const double* Hbar, int s, int d, int k, const int* stop,
                                double* Aug, cudaStream_t st);
