@@ -108,6 +108,31 @@ def max_over_ranks(ms, dev):
     return float(t.item())
 
 
+def sum_over_ranks(v, dev):
+    """Sum of a per-rank count over all ranks; identity on one process."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(v)
+    t = torch.tensor([float(v)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def partition_jobs(sizes, ws):
+    """Independent jobs of the given sizes split over ws ranks: largest first,
+    each to the rank with the least total size so far (ties: lower rank).
+    Returns one list of job indices per rank (disjoint, covering all jobs)."""
+    order = sorted(range(len(sizes)), key=lambda i: (-sizes[i], i))
+    load = [0] * ws
+    parts = [[] for _ in range(ws)]
+    for i in order:
+        r = min(range(ws), key=lambda q: (load[q], q))
+        parts[r].append(i)
+        load[r] += sizes[i]
+    return [sorted(p) for p in parts]
+
+
 def job_rate(ws, units_per_rank, ms):
     """Whole-job throughput: the units all ranks processed / the job's time."""
     return ws * units_per_rank / (ms / 1000.0)
@@ -311,13 +336,18 @@ def _bench_laplace(skg, dev):
 
 
 def _bench_batched(skg, dev):
-    """256 convection-diffusion systems (side U{128..512}, Pe U(1,100)), 4 RHS each."""
+    """256 convection-diffusion systems (side U{128..512}, Pe U(1,100)), 4 RHS
+    each; with several ranks the systems are partitioned over them
+    (partition_jobs, balanced by size) and the job's rate is all ranks'
+    converged solves over the slowest rank's time."""
     import torch
     import synth
+    ws, rank, _ = _dist()
     W = synth.WORKLOADS["batched"]
     sides, pes = synth.batch_systems(W["seed"], W["nsys"])
+    mine = partition_jobs([int(v) ** 2 for v in sides], ws)[rank]
     ops, bs = [], []
-    for i in range(W["nsys"]):
+    for i in mine:
         N = int(sides[i])
         ops.append(skg.Op.stencil5(N, N, synth.conv_diff_coef(N, pes[i])))
         g = torch.Generator(device=dev).manual_seed(synth.batch_rhs_seed(i, 0))
@@ -329,9 +359,10 @@ def _bench_batched(skg, dev):
     t = time.perf_counter()
     xs, stat, info = skg.sgmres_solve_batched(ops, bs, W["d"], W["k"], W["s"], W["tol"], batch_workers=best, **kw)
     torch.cuda.synchronize()
-    wall = time.perf_counter() - t
-    conv = sum(1 for st in stat if st == 0)
-    return {"jobs": len(stat), "converged_1e-6": conv, "wall_s": round(wall, 3),
+    wall = max_over_ranks(time.perf_counter() - t, dev)
+    conv = int(sum_over_ranks(sum(1 for st in stat if st == 0), dev))
+    jobs = int(sum_over_ranks(len(stat), dev))
+    return {"jobs": jobs, "converged_1e-6": conv, "wall_s": round(wall, 3), "ranks": ws,
             "solves_per_s": round(conv / wall, 2), "workers": best,
             "autotune_s": {str(k): round(v, 3) for k, v in tun.items()}, "form": "FP32 basis, FP64 refinement",
             "maxit": 500}
@@ -342,6 +373,10 @@ def run_ours(args):
     import torch.distributed as dist
 
     ws, rank, local = _dist()
+    if ws != args.gpus:
+        print("bench.py: --gpus %d but %d process(es) (WORLD_SIZE); launch N > 1 with torch.distributed.run "
+              "--nproc-per-node N" % (args.gpus, ws), file=sys.stderr)
+        return 2
     if ws > 1:
         torch.cuda.set_device(local)
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))

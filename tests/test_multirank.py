@@ -97,3 +97,53 @@ def test_reference_arm_json_line_contract():
     assert d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
     assert "workload" in d["config"]
+
+
+def _sum_main(rank, ws, port, q):
+    import torch
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    import bench
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(ws),
+                      LOCAL_RANK=str(rank))
+    dist.init_process_group("gloo", rank=rank, world_size=ws)
+    try:
+        import synth
+        W = synth.WORKLOADS["batched"]
+        sides, _ = synth.batch_systems(W["seed"], W["nsys"])
+        mine = bench.partition_jobs([int(v) ** 2 for v in sides], ws)[rank]
+        # each rank counts its own jobs; the job totals come from the sum over ranks
+        q.put((rank, sorted(mine), bench.sum_over_ranks(len(mine), torch.device("cpu"))))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_batched_partition_over_two_gloo_ranks():
+    # the batched workload's 256 systems split over two ranks: disjoint,
+    # complete, balanced by size (loads differ by at most the largest
+    # system), and the per-rank counts sum to the job total on every rank
+    import synth
+    sys.path.insert(0, ROOT)
+    import bench
+    W = synth.WORKLOADS["batched"]
+    sides, _ = synth.batch_systems(W["seed"], W["nsys"])
+    sizes = [int(v) ** 2 for v in sides]
+    for ws in (1, 2, 3, 8):
+        parts = bench.partition_jobs(sizes, ws)
+        flat = sorted(i for p in parts for i in p)
+        assert flat == list(range(len(sizes)))
+        loads = [sum(sizes[i] for i in p) for p in parts]
+        assert max(loads) - min(loads) <= max(sizes)
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_sum_main, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    got = sorted(q.get(timeout=10) for _ in range(2))
+    assert set(got[0][1]).isdisjoint(got[1][1])
+    assert sorted(got[0][1] + got[1][1]) == list(range(len(sizes)))
+    assert got[0][2] == got[1][2] == len(sizes)
