@@ -63,12 +63,20 @@ sk_status sk_op_stencil5(sk_op** op, int nx, int ny, const double* coef, const d
  * theta: device, nx*ny doubles (> 0). Symmetric positive definite. */
 sk_status sk_op_diffusion_var(sk_op** op, int nx, int ny, const double* theta);
 
-/* General sparse A in CSR (0-based, int32 indices), FP64 values, device. */
+/* General sparse A in CSR (0-based, int32 indices), FP64 values, device
+ * (borrowed).  The op also builds, on the device, a SELL-32 copy that the
+ * kernels read (rows in slices of 32, each slice's entries stored
+ * column-major and padded with zeros to its longest row, so that a warp of
+ * consecutive rows reads consecutive words); it owns that copy.  Allocates
+ * and synchronises the device. */
 sk_status sk_op_csr(sk_op** op, int64_t n, int64_t nnz, const int32_t* rowptr,
                     const int32_t* colind, const double* val);
 
-/* A^T as a new op (stencil: E<->W and N<->S swapped; diffusion: itself).
- * CSR ops return SK_EINVAL. The new op borrows the same arrays. */
+/* A^T as a new op (stencil: E<->W and N<->S swapped; diffusion: itself; both
+ * borrow the same arrays).  CSR: the transpose is built on the device (rows
+ * sorted by column; owned by the new op, with its own SELL-32 copy;
+ * allocates and synchronises the device); the new op's parameter gradient
+ * (sk_op_param_grad) is with respect to its own entries. */
 sk_status sk_op_transpose(const sk_op* op, sk_op** opT);
 
 /* y = A x in FP64 (x, y: device, n doubles; must not alias). */

@@ -43,3 +43,15 @@ def stencil_loss_and_grad(nx, ny, coef, shift, b, x_t):
         e[q] = 1.0
         gc[q] = -lam @ (operators.stencil5_matrix(nx, ny, e) @ x)
     return float(np.sum((x - x_t) ** 2)), gc, -lam * x, lam, x
+
+
+def csr_loss_and_grad(A, b, x_t):
+    """The same loss for a general sparse A (scipy CSR, the given pattern):
+      lam = A^{-T} 2(x - x_t),  dL/db = lam,  dL/dval_e = -lam_row(e) x_col(e).
+    Returns (L, dL/dval (nnz, CSR order), lam, x)."""
+    A = A.tocsr()
+    lu = spla.splu(A.tocsc())
+    x = lu.solve(np.asarray(b, dtype=np.float64))
+    lam = lu.solve(2.0 * (x - x_t), trans="T")
+    rows = np.repeat(np.arange(A.shape[0]), np.diff(A.indptr))
+    return float(np.sum((x - x_t) ** 2)), -lam[rows] * x[A.indices], lam, x

@@ -490,3 +490,32 @@ def stencil_solve(coef, b, nx, ny, shift=None, d=100, k=2, s=200, tol=1e-10, **o
     """Differentiable x = A(coef, shift)^{-1} b (see StencilSolve); coef is a
     tensor of the five coefficients (centre, E, W, N, S)."""
     return StencilSolve.apply(coef, shift, b, nx, ny, d, k, s, tol, opts)
+
+
+class CsrSolve(torch.autograd.Function):
+    """x = A(val)^{-1} b by sGMRES for a general sparse operator (Op.csr with a
+    fixed pattern rowptr/colind), differentiable in the stored values and b.
+    Backward: the adjoint solve with the library's CSR transpose, then
+    dL/dval = -lam_row x_col (sk_op_param_grad, alpha = -1, on A's entries)."""
+
+    @staticmethod
+    def forward(ctx, val, b, rowptr, colind, d, k, s, tol, opts):
+        op = Op.csr(rowptr, colind, val.detach())
+        x, info = _forward(op, b, d, k, s, tol, opts)
+        ctx.save_for_backward(val.detach(), x)
+        ctx.cfg = (rowptr, colind, d, k, s, tol, opts)
+        ctx.info = info
+        return x
+
+    @staticmethod
+    def backward(ctx, gx):
+        val, x = ctx.saved_tensors
+        rowptr, colind, d, k, s, tol, opts = ctx.cfg
+        lam, gval = _adjoint(Op.csr(rowptr, colind, val), x, gx, d, k, s, tol, opts)
+        return gval, lam, None, None, None, None, None, None, None
+
+
+def csr_solve(val, b, rowptr, colind, d=100, k=2, s=200, tol=1e-10, **opts):
+    """Differentiable x = A(val)^{-1} b for a CSR pattern (see CsrSolve)."""
+    return CsrSolve.apply(val, b, rowptr, colind, d, k, s, tol, opts)
+

@@ -1,5 +1,6 @@
 // C ABI plumbing: errors, options, operator objects, operator apply and the
 // sketch_apply entry point.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -38,6 +39,9 @@ sk_status make_view(const sk_op* op, OpView<double>* v) {
   v->rowptr = op->rowptr;
   v->colind = op->colind;
   v->val = op->val;
+  v->sell_ptr = op->sell_ptr;
+  v->sell_col = op->sell_col;
+  v->sell_val = op->sell_val;
   return SK_OK;
 }
 
@@ -70,6 +74,16 @@ sk_status make_view(const sk_op* cop, OpView<float>* v, cudaStream_t st) {
   if (op->shift) { SK_TRY(f32_copy(op->shift, op->n, &op->shift32, st)); v->shift = op->shift32; }
   if (op->theta) { SK_TRY(f32_copy(op->theta, op->n, &op->theta32, st)); v->theta = op->theta32; }
   if (op->val) { SK_TRY(f32_copy(op->val, op->nnz, &op->val32, st)); v->val = op->val32; }
+  v->sell_ptr = op->sell_ptr;
+  v->sell_col = op->sell_col;
+  v->sell_val = nullptr;
+  if (op->sell_ptr && !op->sell_val32) {  // first FP32 use (solvers make it before any capture)
+    int64_t total = 0;
+    SK_CUDA(cudaMemcpyAsync(&total, op->sell_ptr + (op->n + 31) / 32, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    SK_CUDA(cudaStreamSynchronize(st));
+    SK_TRY(f32_copy(op->sell_val, total, &op->sell_val32, st));
+  }
+  v->sell_val = op->sell_val32;
   return SK_OK;
 }
 
@@ -134,6 +148,135 @@ __global__ void csr_grad_kernel(int64_t n, const int32_t* __restrict__ rowptr, c
     const double l = alpha * lam[i];
     for (int32_t e = rowptr[i]; e < rowptr[i + 1]; ++e) g[e] = l * x[col[e]];
   }
+}
+
+// ---- CSR: SELL-32 copy and transpose ---------------------------------------------------
+__global__ void sell_width_kernel(const int32_t* __restrict__ rowptr, int64_t n, int64_t* __restrict__ w) {
+  const int64_t ns = (n + 31) / 32;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < ns; q += (int64_t)gridDim.x * blockDim.x) {
+    int32_t m = 0;
+    for (int64_t i = 32 * q; i < 32 * q + 32 && i < n; ++i) m = max(m, rowptr[i + 1] - rowptr[i]);
+    w[q] = (int64_t)m * 32;
+  }
+}
+
+__global__ void sell_fill_kernel(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                                 const double* __restrict__ val, int64_t n, const int64_t* __restrict__ sptr,
+                                 int32_t* __restrict__ scol, double* __restrict__ sval) {
+  const int64_t ns = (n + 31) / 32;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < ns * 32; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t q = t >> 5, i = t;
+    const int w = (int)((sptr[q + 1] - sptr[q]) >> 5);
+    const int32_t e0 = i < n ? rowptr[i] : 0, len = i < n ? rowptr[i + 1] - e0 : 0;
+    for (int e = 0; e < w; ++e) {
+      const int64_t idx = sptr[q] + 32 * (int64_t)e + (i & 31);
+      scol[idx] = e < len ? col[e0 + e] : (int32_t)(i < n ? i : 0);
+      sval[idx] = e < len ? val[e0 + e] : 0.0;
+    }
+  }
+}
+
+// the SELL-32 copy of op's CSR arrays (synchronous, legacy default stream)
+static sk_status build_sell(sk_op* op) {
+  const int64_t n = op->n, ns = (n + 31) / 32;
+  int64_t* w = nullptr;
+  SK_CUDA(cudaMalloc((void**)&op->sell_ptr, sizeof(int64_t) * (ns + 1)));
+  SK_CUDA(cudaMalloc((void**)&w, sizeof(int64_t) * ns));
+  const int g = (int)std::min<int64_t>((ns + 255) / 256, 8 * num_sms());
+  sell_width_kernel<<<g > 0 ? g : 1, 256>>>(op->rowptr, n, w);
+  SK_CUDA(cudaGetLastError());
+  int64_t* hw = new (std::nothrow) int64_t[ns + 1];
+  if (!hw) { cudaFree(w); set_error("out of host memory"); return SK_ENOMEM; }
+  cudaError_t e = cudaMemcpy(hw, w, sizeof(int64_t) * ns, cudaMemcpyDeviceToHost);
+  cudaFree(w);
+  if (e != cudaSuccess) { delete[] hw; return cuda_fail(e, "cudaMemcpy(SELL widths)"); }
+  int64_t run = 0;
+  for (int64_t q = 0; q < ns; ++q) { const int64_t v = hw[q]; hw[q] = run; run += v; }
+  hw[ns] = run;
+  e = cudaMemcpy(op->sell_ptr, hw, sizeof(int64_t) * (ns + 1), cudaMemcpyHostToDevice);
+  delete[] hw;
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy(SELL offsets)");
+  SK_CUDA(cudaMalloc((void**)&op->sell_col, sizeof(int32_t) * (run > 0 ? run : 1)));
+  SK_CUDA(cudaMalloc((void**)&op->sell_val, sizeof(double) * (run > 0 ? run : 1)));
+  const int g2 = (int)std::min<int64_t>((ns * 32 + 255) / 256, 16 * num_sms());
+  sell_fill_kernel<<<g2 > 0 ? g2 : 1, 256>>>(op->rowptr, op->colind, op->val, n, op->sell_ptr, op->sell_col,
+                                            op->sell_val);
+  SK_CUDA(cudaGetLastError());
+  SK_CUDA(cudaDeviceSynchronize());
+  return SK_OK;
+}
+
+__global__ void csr_count_kernel(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col, int64_t n,
+                                 int32_t* __restrict__ cnt) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    for (int32_t e = rowptr[i]; e < rowptr[i + 1]; ++e) atomicAdd(&cnt[col[e]], 1);
+}
+
+// entry (i, j, v) of A lands in row j of A^T at a slot claimed atomically;
+// the rows are sorted afterwards, so the result does not depend on the order
+__global__ void csr_scatter_kernel(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                                   const double* __restrict__ val, int64_t n, const int32_t* __restrict__ tptr,
+                                   int32_t* __restrict__ fill, int32_t* __restrict__ tcol, double* __restrict__ tval) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    for (int32_t e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+      const int32_t j = col[e];
+      const int32_t pos = tptr[j] + atomicAdd(&fill[j], 1);
+      tcol[pos] = (int32_t)i;
+      tval[pos] = val[e];
+    }
+}
+
+// each row of A^T sorted by column (insertion sort; rows are short)
+__global__ void csr_sort_rows_kernel(const int32_t* __restrict__ tptr, int64_t n, int32_t* __restrict__ tcol,
+                                     double* __restrict__ tval) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t b = tptr[j], e = tptr[j + 1];
+    for (int32_t q = b + 1; q < e; ++q) {
+      const int32_t c = tcol[q];
+      const double v = tval[q];
+      int32_t p = q - 1;
+      while (p >= b && tcol[p] > c) { tcol[p + 1] = tcol[p]; tval[p + 1] = tval[p]; --p; }
+      tcol[p + 1] = c;
+      tval[p + 1] = v;
+    }
+  }
+}
+
+// A^T of a CSR op into t's own arrays (synchronous)
+static sk_status build_csr_transpose(const sk_op* op, sk_op* t) {
+  const int64_t n = op->n, nnz = op->nnz;
+  int32_t *cnt = nullptr, *fill = nullptr;
+  SK_CUDA(cudaMalloc((void**)&t->own_rowptr, sizeof(int32_t) * (n + 1)));
+  SK_CUDA(cudaMalloc((void**)&t->own_colind, sizeof(int32_t) * (nnz > 0 ? nnz : 1)));
+  SK_CUDA(cudaMalloc((void**)&t->own_val, sizeof(double) * (nnz > 0 ? nnz : 1)));
+  SK_CUDA(cudaMalloc((void**)&cnt, sizeof(int32_t) * n));
+  SK_CUDA(cudaMalloc((void**)&fill, sizeof(int32_t) * n));
+  SK_CUDA(cudaMemset(cnt, 0, sizeof(int32_t) * n));
+  SK_CUDA(cudaMemset(fill, 0, sizeof(int32_t) * n));
+  const int g = (int)std::min<int64_t>((n + 255) / 256, 16 * num_sms());
+  csr_count_kernel<<<g > 0 ? g : 1, 256>>>(op->rowptr, op->colind, n, cnt);
+  SK_CUDA(cudaGetLastError());
+  int32_t* h = new (std::nothrow) int32_t[n + 1];
+  if (!h) { cudaFree(cnt); cudaFree(fill); set_error("out of host memory"); return SK_ENOMEM; }
+  cudaError_t e = cudaMemcpy(h + 1, cnt, sizeof(int32_t) * n, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) {
+    h[0] = 0;
+    for (int64_t j = 0; j < n; ++j) h[j + 1] += h[j];
+    e = cudaMemcpy(t->own_rowptr, h, sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice);
+  }
+  delete[] h;
+  cudaFree(cnt);
+  if (e != cudaSuccess) { cudaFree(fill); return cuda_fail(e, "cudaMemcpy(transpose counts)"); }
+  csr_scatter_kernel<<<g > 0 ? g : 1, 256>>>(op->rowptr, op->colind, op->val, n, t->own_rowptr, fill, t->own_colind,
+                                             t->own_val);
+  csr_sort_rows_kernel<<<g > 0 ? g : 1, 256>>>(t->own_rowptr, n, t->own_colind, t->own_val);
+  SK_CUDA(cudaGetLastError());
+  SK_CUDA(cudaDeviceSynchronize());
+  cudaFree(fill);
+  t->rowptr = t->own_rowptr;
+  t->colind = t->own_colind;
+  t->val = t->own_val;
+  return SK_OK;
 }
 
 }  // namespace sk
@@ -232,15 +375,28 @@ sk_status sk_op_csr(sk_op** out, int64_t n, int64_t nnz, const int32_t* rowptr, 
   op->rowptr = rowptr;
   op->colind = colind;
   op->val = val;
+  const sk_status r = build_sell(op);
+  if (r != SK_OK) { sk_op_destroy(op); return r; }
   *out = op;
   return SK_OK;
 }
 
 sk_status sk_op_transpose(const sk_op* op, sk_op** opT) {
   SK_CHECK_ARG(op != nullptr && opT != nullptr, "NULL op");
-  SK_CHECK_ARG(op->kind != OP_CSR, "transpose of a CSR op is not supported");
   sk_op* t = new_op();
   if (!t) { set_error("out of host memory"); return SK_ENOMEM; }
+  if (op->kind == OP_CSR) {
+    t->kind = OP_CSR;
+    t->n = op->n;
+    t->nx = op->nx;
+    t->ny = 1;
+    t->nnz = op->nnz;
+    sk_status r = build_csr_transpose(op, t);
+    if (r == SK_OK) r = build_sell(t);
+    if (r != SK_OK) { sk_op_destroy(t); return r; }
+    *opT = t;
+    return SK_OK;
+  }
   t->kind = op->kind;
   t->nx = op->nx;
   t->ny = op->ny;
@@ -286,6 +442,13 @@ void sk_op_destroy(sk_op* op) {
   if (op->shift32) cudaFree(op->shift32);
   if (op->theta32) cudaFree(op->theta32);
   if (op->val32) cudaFree(op->val32);
+  if (op->sell_ptr) cudaFree(op->sell_ptr);
+  if (op->sell_col) cudaFree(op->sell_col);
+  if (op->sell_val) cudaFree(op->sell_val);
+  if (op->sell_val32) cudaFree(op->sell_val32);
+  if (op->own_rowptr) cudaFree(op->own_rowptr);
+  if (op->own_colind) cudaFree(op->own_colind);
+  if (op->own_val) cudaFree(op->own_val);
   delete op;
 }
 

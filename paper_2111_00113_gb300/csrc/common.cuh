@@ -189,6 +189,18 @@ struct sk_op {
   float* theta32;
   float* val32;
   bool owns_nothing_else;
+  // CSR: the SELL-32 copy the kernels read (owned; built by sk_op_csr and
+  // sk_op_transpose): slice q (rows 32q .. 32q+31) has width w_q and its
+  // entries column-major at sell_ptr[q] + e*32 + (row % 32), e < w_q, padded
+  // with zero values; so a warp of consecutive rows reads consecutive words.
+  int64_t* sell_ptr;      // nslices + 1
+  int32_t* sell_col;
+  double* sell_val;
+  float* sell_val32;
+  // a transposed CSR op owns its CSR arrays (rowptr, colind, val above)
+  int32_t* own_rowptr;
+  int32_t* own_colind;
+  double* own_val;
 };
 
 namespace sk {
@@ -204,6 +216,9 @@ struct OpView {
   const int32_t* rowptr;
   const int32_t* colind;
   const C* val;
+  const int64_t* sell_ptr;  // SELL-32 (see sk_op); NULL: plain CSR rows
+  const int32_t* sell_col;
+  const C* sell_val;
 
   // (A x)_i, x of storage type T (converted to C on load).
   template <typename T>
@@ -229,6 +244,13 @@ struct OpView {
       acc += (ix > 0) ? (C)0.5 * (tP + theta[i - 1]) * (xP - to_c(x[i - 1])) : tP * xP;
       acc += (iy + 1 < ny) ? (C)0.5 * (tP + theta[i + nx]) * (xP - to_c(x[i + nx])) : tP * xP;
       acc += (iy > 0) ? (C)0.5 * (tP + theta[i - nx]) * (xP - to_c(x[i - nx])) : tP * xP;
+      return acc;
+    } else if (sell_ptr) {
+      // row i = lane (i % 32) of slice i / 32: consecutive rows, consecutive words
+      C acc = 0;
+      const int64_t q = i >> 5, base = sell_ptr[q] + (i & 31);
+      const int w = (int)((sell_ptr[q + 1] - sell_ptr[q]) >> 5);
+      for (int e = 0; e < w; ++e) acc += sell_val[base + 32 * (int64_t)e] * to_c(x[sell_col[base + 32 * (int64_t)e]]);
       return acc;
     } else {
       C acc = 0;

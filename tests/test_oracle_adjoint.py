@@ -90,3 +90,25 @@ def test_stencil_adjoint_gradient_matches_central_differences():
         assert abs(fd - gs[p]) <= 1e-6 * max(1.0, abs(gs[p]))
         fd = (loss(coef, shift, b + e) - loss(coef, shift, b - e)) / 2e-6
         assert abs(fd - lam[p]) <= 1e-6 * max(1.0, abs(lam[p]))
+
+
+def test_csr_adjoint_gradient_matches_central_differences():
+    # gradient with respect to the stored values of a general sparse matrix
+    import scipy.sparse as sp
+    n = 30
+    A = (sp.random(n, n, density=0.15, random_state=5, format="csr") + 4.0 * sp.eye(n)).tocsr()
+    b = synth.randn(12, n)
+    xt = synth.randn(13, n) * 0.1
+
+    def loss(vals):
+        M = sp.csr_matrix((vals, A.indices, A.indptr), shape=A.shape).toarray()
+        x = np.linalg.solve(M, b)
+        return np.sum((x - xt) ** 2)
+
+    L, gv, lam, x = adjoint.csr_loss_and_grad(A, b, xt)
+    assert abs(L - loss(A.data)) <= 1e-12 * L
+    for e in range(0, A.nnz, 7):
+        d = np.zeros(A.nnz)
+        d[e] = 1e-6
+        fd = (loss(A.data + d) - loss(A.data - d)) / 2e-6
+        assert abs(fd - gv[e]) <= 1e-6 * max(1.0, abs(gv[e])), (e, fd, gv[e])
