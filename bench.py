@@ -549,6 +549,36 @@ def run_ours(args):
     return 0
 
 
+def run_case(args):
+    """One small piece of the path for ncu captures (prints one status line,
+    not the bench JSON line):
+      cycle   one warm-up restart cycle, then one more, of the scale workload
+              (FP32 basis; --no-pipeline for the sequential cycle);
+      sketch  a reusable sparse-sign plan applied twice to a --n x --cols
+              FP32 block (s = 600, zeta = 12)."""
+    import torch
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    import paper_2111_00113_gb300 as skg
+    if args.case == "cycle":
+        W, N, coef, f, b = _problem(dev)
+        A = skg.Op.stencil5(N, N, coef)
+        kw = dict(zeta=W["zeta"], seed=7, basis=torch.float32, pipeline=not args.no_pipeline)
+        for _ in range(2):
+            x, info = skg.sgmres_solve(A, b, W["d"], W["k"], W["s"], 1e-300, maxit=1, **kw)
+        torch.cuda.synchronize()
+        print("case cycle ms %.3f launches %d" % (info["ms"], info["launches"]))
+    else:
+        g = torch.Generator(device=dev).manual_seed(0)
+        B = torch.randn((args.cols, args.n), generator=g, device=dev, dtype=torch.float32).t()
+        plan = skg.SketchPlan(args.n, 600, 12, 7)
+        out = plan(B)
+        plan(B, out=out)
+        torch.cuda.synchronize()
+        print("case sketch n %d cols %d ok" % (args.n, args.cols))
+    return 0
+
+
 def build_parser():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -565,11 +595,17 @@ def build_parser():
                     help="run each cycle's phases one after another (no sketch/QR overlap with the basis)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the sketch, sRR, batched and Laplacian measurements")
+    ap.add_argument("--case", choices=["cycle", "sketch"],
+                    help="run one small piece of the path for a profiler capture and exit")
+    ap.add_argument("--n", type=int, default=1 << 18, help="rows of the --case sketch block")
+    ap.add_argument("--cols", type=int, default=301, help="columns of the --case sketch block")
     return ap
 
 
 def main():
     args = build_parser().parse_args()
+    if args.case:
+        return run_case(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)
