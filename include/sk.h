@@ -218,6 +218,14 @@ typedef struct {
                               block of 16 basis columns and add the panels it completes to the QR
                               of S A B on a second, lower-priority stream while the basis passes
                               continue (same arithmetic, overlapped); 0 = one phase after another */
+  int batch_mode;          /* sgmres_solve_batched: 0 (default) = grouped where supported, else
+                              worker threads; 1 = grouped (SK_EINVAL where unsupported); 2 = worker
+                              threads.  Grouped: every launch advances one phase of all resident
+                              jobs (sparse sign sketch, truncated-Arnoldi basis, FP32 or FP64
+                              storage, s <= 640, iter_chunk = 0) */
+  long long batch_elems;   /* grouped batches: jobs are admitted, largest first, while the resident
+                              systems' sizes n sum to at most this (at least one job is resident);
+                              0 = 2^23 */
 } sk_opts;
 
 void sk_opts_default(sk_opts* o);
@@ -290,13 +298,31 @@ size_t sk_workspace_bytes(const sk_op* A, int d, int k, int s, const sk_opts* op
  *   initial guess in, the solution out.  per_job: host array of nsys*nrhs
  *   statuses (or NULL).  job_info: host array of nsys*nrhs sk_info, each the
  *   job's own diagnostics as sgmres_solve reports them (or NULL).  info:
- *   aggregate (cycles and matvecs summed, relres the worst job, ms summed
- *   over jobs except ms[5] = wall time).
- * Jobs run on opts->batch_workers host threads with one stream each, largest
- * systems first; `stream` is joined before and after.  Blocks until done.
- * Jobs launch their kernels directly on their streams (opts->use_graph is
- * ignored: capturing a graph per small job costs more than it saves).
- * Returns SK_OK if every job converged, else the first failing job's status.
+ *   aggregate (cycles and matvecs summed, relres the worst job, ms[5] =
+ *   wall time).
+ * Grouped batches (opts->batch_mode 0 where supported, or 1): jobs are
+ *   admitted largest first while the resident systems' n sum to at most
+ *   opts->batch_elems; every kernel launch runs one phase of the restart
+ *   cycle for all resident jobs (a flat map of each job's blocks for the
+ *   n-sized kernels, one grid row per job for the small dense problems),
+ *   and the host reads one row of scalars per job and cycle, then retires
+ *   and admits jobs.  Each job computes what sgmres_solve computes on its
+ *   inputs, bit for bit.  info->ms[0..4] and launches: device time and
+ *   kernel launches of the grouped phases; a job's ms[0..4] and launches
+ *   are those of the grouped cycles it took part in (shared with the jobs
+ *   resident beside it), its ms[5] the wall time from admission to exit.
+ *   Workspace: one slab of the s x (d+1) problem per slot plus each
+ *   resident job's n-sized buffers (the basis n x (d+1) dominates), so
+ *   about batch_elems x (d+1) x (basis bytes + 1) bytes at the budget.
+ *   `stream` carries all launches.  opts->persistent and opts->use_graph
+ *   are ignored.
+ * Worker threads (opts->batch_mode 2, or 0 where grouped is unsupported):
+ *   jobs run on opts->batch_workers host threads with one stream each,
+ *   largest systems first, each as sgmres_solve with eager launches
+ *   (opts->use_graph ignored); `stream` is joined before and after; ms[0..4]
+ *   summed over jobs.
+ * Blocks until done.  Returns SK_OK if every job converged, else the first
+ * failing job's status.
  * ------------------------------------------------------------------------ */
 sk_status sgmres_solve_batched(int nsys, const sk_op* const* A, int nrhs, const double* const* b,
                                double* const* x, int d, int k, int s, double tol, const sk_opts* opts,

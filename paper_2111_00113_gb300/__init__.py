@@ -207,14 +207,17 @@ def sketch_apply_noalloc(B, s, zeta=0, seed=7):
 
 def make_opts(basis=torch.float64, sketch="sparse", zeta=0, seed=7, stab_tol=0.0, maxit=10000, cgs_passes=2,
               tau=1e-8, symmetric=False, breakdown=0.0, use_graph=True, persistent=False, batch_workers=0,
-              cheb=None, barrier_spins=0, iter_chunk=0, pipeline=True, trunc_tol=0.0):
+              cheb=None, barrier_spins=0, iter_chunk=0, pipeline=True, trunc_tol=0.0, batch_mode="auto",
+              batch_elems=0):
     """Solver options.  cheb=(c, dx, dy) selects the Chebyshev basis (§4.3)
     for a spectrum inside [c - dx, c + dx] x [-dy, dy].  iter_chunk > 0
     selects iterative sGMRES (§5.2): the cycle grows the basis iter_chunk
     columns at a time and stops at the first prefix whose residual estimate
     meets the target.  pipeline=False runs the cycle's phases one after
     another instead of overlapping the sketch and QR of finished basis
-    blocks with the basis passes."""
+    blocks with the basis passes.  batch_mode ("auto", "grouped",
+    "workers") and batch_elems (resident elements of a grouped batch, 0 =
+    2^23) shape sgmres_solve_batched."""
     o = N.SkOpts()
     N.lib.sk_opts_default(C.byref(o))
     o.sketch = _KIND[sketch]
@@ -234,6 +237,8 @@ def make_opts(basis=torch.float64, sketch="sparse", zeta=0, seed=7, stab_tol=0.0
     o.iter_chunk = int(iter_chunk)
     o.pipeline = int(bool(pipeline))
     o.srr_trunc_tol = float(trunc_tol)
+    o.batch_mode = {"auto": 0, "grouped": 1, "workers": 2}[batch_mode]
+    o.batch_elems = int(batch_elems)
     if cheb is not None:
         o.basis_kind = 1
         o.cheb_c, o.cheb_dx, o.cheb_dy = (float(v) for v in cheb)
@@ -315,23 +320,41 @@ def sgmres_solve_batched(ops, bs, d, k, s, tol, x0s=None, **opts):
     return xs, list(stat), out
 
 
-def autotune_batch_workers(ops, bs, d, k, s, tol, candidates=(4, 8, 16, 32, 48), sample=48, **opts):
-    """Pick the number of concurrent batched jobs by timing a sample.
-
-    The sample takes jobs spread evenly over the size range (largest first
-    ordering is what the library uses).  Returns (best, {workers: seconds}).
-    """
-    import time
+def _batch_sample(ops, bs, sample):
     nsys = len(ops)
     order = sorted(range(nsys), key=lambda i: -ops[i].n)
     pick = sorted(set(order[int(q * (nsys - 1) / max(1, min(sample, nsys) - 1))] for q in range(min(sample, nsys))))
-    sops = [ops[i] for i in pick]
-    sbs = [bs[i][:1] for i in pick]
+    return [ops[i] for i in pick], [bs[i][:1] for i in pick]
+
+
+def autotune_batch(ops, bs, d, k, s, tol, candidates=(1 << 21, 1 << 22, 1 << 23), sample=96, **opts):
+    """Pick the grouped batch's resident-element budget (batch_elems) by
+    timing a sample of the jobs (spread evenly over the size range, one
+    right-hand side each).  Returns (best, {batch_elems: seconds})."""
+    import time
+    sops, sbs = _batch_sample(ops, bs, sample)
+    timings = {}
+    for e in candidates:
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        sgmres_solve_batched(sops, sbs, d, k, s, tol, batch_mode="grouped", batch_elems=e, **opts)
+        torch.cuda.synchronize()
+        timings[e] = time.perf_counter() - t
+    best = min(timings, key=timings.get)
+    return best, timings
+
+
+def autotune_batch_workers(ops, bs, d, k, s, tol, candidates=(4, 8, 16, 32, 48), sample=48, **opts):
+    """Pick the number of worker threads of batch_mode="workers" (one job
+    per thread and stream) by timing a sample of jobs spread evenly over
+    the size range.  Returns (best, {workers: seconds})."""
+    import time
+    sops, sbs = _batch_sample(ops, bs, sample)
     timings = {}
     for w in candidates:
         torch.cuda.synchronize()
         t = time.perf_counter()
-        sgmres_solve_batched(sops, sbs, d, k, s, tol, batch_workers=w, **opts)
+        sgmres_solve_batched(sops, sbs, d, k, s, tol, batch_mode="workers", batch_workers=w, **opts)
         torch.cuda.synchronize()
         timings[w] = time.perf_counter() - t
     best = min(timings, key=timings.get)

@@ -33,7 +33,7 @@ class SkOpts(C.Structure):
         ("symmetric", C.c_int), ("breakdown", C.c_double), ("use_graph", C.c_int), ("persistent", C.c_int),
         ("batch_workers", C.c_int), ("basis_kind", C.c_int), ("cheb_c", C.c_double), ("cheb_dx", C.c_double),
         ("cheb_dy", C.c_double), ("barrier_spins", C.c_int), ("iter_chunk", C.c_int), ("srr_trunc_tol", C.c_double),
-        ("pipeline", C.c_int),
+        ("pipeline", C.c_int), ("batch_mode", C.c_int), ("batch_elems", C.c_longlong),
     ]
 
 

@@ -42,6 +42,7 @@ sk_status make_view(const sk_op* op, OpView<double>* v) {
   v->sell_ptr = op->sell_ptr;
   v->sell_col = op->sell_col;
   v->sell_val = op->sell_val;
+  set_div_magic(op->nx, op->n, &v->nx_m, &v->nx_s);
   return SK_OK;
 }
 
@@ -84,6 +85,7 @@ sk_status make_view(const sk_op* cop, OpView<float>* v, cudaStream_t st) {
     SK_TRY(f32_copy(op->sell_val, total, &op->sell_val32, st));
   }
   v->sell_val = op->sell_val32;
+  set_div_magic(op->nx, op->n, &v->nx_m, &v->nx_s);
   return SK_OK;
 }
 
@@ -323,6 +325,8 @@ void sk_opts_default(sk_opts* o) {
   o->barrier_spins = 0;
   o->iter_chunk = 0;
   o->pipeline = 1;
+  o->batch_mode = 0;
+  o->batch_elems = 0;
 }
 
 static sk_op* new_op() {

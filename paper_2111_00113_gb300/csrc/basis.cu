@@ -23,6 +23,7 @@
 
 #include "basis.cuh"
 #include "common.cuh"
+#include "grouped.cuh"
 
 namespace sk {
 
@@ -81,9 +82,10 @@ __device__ __forceinline__ void gstore(T* p, int64_t i, const C (&v)[G]) {
 template <int G, typename T, typename C>
 __device__ __forceinline__ void op_apply(const OpView<C>& A, const T* __restrict__ x, int64_t i0, C (&m)[G]) {
   if constexpr (G == 4) {
-    const int ii = (int)i0;
-    const int iy = ii / A.nx;
-    const int ix0 = ii - iy * A.nx;
+    int ix0;
+    int64_t iy64;
+    A.grid_pos(i0, ix0, iy64);
+    const int iy = (int)iy64;
     C xc[4], up[4], dn[4];
     ld4(x + i0, xc);
     const C w = ix0 > 0 ? to_c(x[i0 - 1]) : (C)0;
@@ -92,15 +94,18 @@ __device__ __forceinline__ void op_apply(const OpView<C>& A, const T* __restrict
     else up[0] = up[1] = up[2] = up[3] = 0;
     if (iy > 0) ld4(x + i0 - A.nx, dn);
     else dn[0] = dn[1] = dn[2] = dn[3] = 0;
-    m[0] = A.cP * xc[0] + A.cE * xc[1] + A.cW * w + A.cN * up[0] + A.cS * dn[0];
-    m[1] = A.cP * xc[1] + A.cE * xc[2] + A.cW * xc[0] + A.cN * up[1] + A.cS * dn[1];
-    m[2] = A.cP * xc[2] + A.cE * xc[3] + A.cW * xc[1] + A.cN * up[2] + A.cS * dn[2];
-    m[3] = A.cP * xc[3] + A.cE * e + A.cW * xc[2] + A.cN * up[3] + A.cS * dn[3];
+    // explicit fused multiply-adds, left to right: the rounding does not
+    // depend on how the compiler contracts the sum in a given kernel
+    const C cP = A.cP, cE = A.cE, cW = A.cW, cN = A.cN, cS = A.cS;
+    m[0] = fma(cS, dn[0], fma(cN, up[0], fma(cW, w, fma(cE, xc[1], cP * xc[0]))));
+    m[1] = fma(cS, dn[1], fma(cN, up[1], fma(cW, xc[0], fma(cE, xc[2], cP * xc[1]))));
+    m[2] = fma(cS, dn[2], fma(cN, up[2], fma(cW, xc[1], fma(cE, xc[3], cP * xc[2]))));
+    m[3] = fma(cS, dn[3], fma(cN, up[3], fma(cW, xc[2], fma(cE, e, cP * xc[3]))));
     if (A.shift) {
       C sh[4];
       ld4(A.shift + i0, sh);
 #pragma unroll
-      for (int q = 0; q < 4; ++q) m[q] += sh[q] * xc[q];
+      for (int q = 0; q < 4; ++q) m[q] = fma(sh[q], xc[q], m[q]);
     }
   } else {
     m[0] = A.apply(x, i0);
@@ -129,14 +134,20 @@ __device__ __forceinline__ C* coef_row(const BasisParams& p, int j) {
 }
 
 // ---- kernels ------------------------------------------------------------------
-// Each thread handles kIter groups of G elements.  The passes are launched
+// Each thread handles IterOf<G> groups of G elements.  The passes are launched
 // with programmatic dependent launch: a kernel loads every operand that its
 // immediate predecessor does not write (b_j is written by form(j), the
 // predecessor of dots1(j); the older window vectors and, for dots2 and form,
 // b_j itself are older), then waits for the predecessor's results (h1, h2,
 // nu, stop; m for FP64) and only then lets its own successor launch, so a
 // successor's early loads only ever read what completed kernels wrote.
-static constexpr int kIter = 2;
+// kIter<G> groups per thread: 2 groups of 4 cells (vector path) or 8 single
+// cells, so every CTA covers 2048 unknowns on either path (fewer, longer
+// CTAs: each pass is latency bound, one block reduction per CTA).
+template <int G>
+struct IterOf {
+  static constexpr int value = G == 4 ? 2 : 8;
+};
 
 __device__ __forceinline__ void pdl_trigger() {
 #if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 900
@@ -149,14 +160,18 @@ __device__ __forceinline__ void pdl_wait() {
 #endif
 }
 
+// The passes' bodies take the block index `bid` of `nb` blocks that cover
+// the vector: the whole grid of a single-system launch, or one job's blocks
+// of a grouped launch.
 template <typename T, int KM, int G, bool STORE_M>
-__global__ void __launch_bounds__(kBasisThreads)
-form_kernel(BasisParams p, OpView<typename Compute<T>::type> A, int c) {
+__device__ __forceinline__ void form_body(const BasisParams& p, const OpView<typename Compute<T>::type>& A, int c,
+                                          int bid, int nb) {
+  constexpr int kIter = IterOf<G>::value;
   using C = typename Compute<T>::type;
   T* out = bcol<T>(p.B, p.ldb, c);
   const int64_t n = p.n;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x * G;
-  const int64_t i_begin = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * G;
+  const int64_t stride = (int64_t)nb * blockDim.x * G;
+  const int64_t i_begin = ((int64_t)bid * blockDim.x + threadIdx.x) * G;
   if (c == 0) {
     pdl_wait();
     pdl_trigger();
@@ -218,7 +233,7 @@ form_kernel(BasisParams p, OpView<typename Compute<T>::type> A, int c) {
       for (int q = 0; q < KM; ++q) {
         if (q < kw) {
 #pragma unroll
-          for (int e = 0; e < G; ++e) m[it][e] -= h[q] * bw[it][q][e];
+          for (int e = 0; e < G; ++e) m[it][e] = fma(-h[q], bw[it][q][e], m[it][e]);
         }
       }
 #pragma unroll
@@ -228,18 +243,25 @@ form_kernel(BasisParams p, OpView<typename Compute<T>::type> A, int c) {
   }
 }
 
+template <typename T, int KM, int G, bool STORE_M>
+__global__ void __launch_bounds__(kBasisThreads)
+form_kernel(BasisParams p, OpView<typename Compute<T>::type> A, int c) {
+  form_body<T, KM, G, STORE_M>(p, A, c, blockIdx.x, gridDim.x);
+}
+
 // PASS = 1: dots with m (and m stored if STORE_M);  PASS = 2: dots with
 // w = m - W h1.
 template <typename T, int KM, int G, bool STORE_M, int PASS>
-__global__ void __launch_bounds__(kBasisThreads)
-dots_kernel(BasisParams p, OpView<typename Compute<T>::type> A, int j) {
+__device__ __forceinline__ void dots_body(const BasisParams& p, const OpView<typename Compute<T>::type>& A, int j,
+                                          int bid, int nb) {
+  constexpr int kIter = IterOf<G>::value;
   using C = typename Compute<T>::type;
   __shared__ C red[(KM + 1) * (kBasisThreads / 32)];
   const int kw = min(p.k, j + 1);
   const int64_t n = p.n;
   const T* bj = bcol<T>(p.B, p.ldb, j);
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x * G;
-  const int64_t i_begin = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * G;
+  const int64_t stride = (int64_t)nb * blockDim.x * G;
+  const int64_t i_begin = ((int64_t)bid * blockDim.x + threadIdx.x) * G;
   C m[kIter][G];
   C bw[kIter][KM][G];
   // prologue: the window b_{j-1..} is old; b_j is old for pass 2 only
@@ -290,27 +312,27 @@ dots_kernel(BasisParams p, OpView<typename Compute<T>::type> A, int j) {
 #pragma unroll
         for (int q = 0; q < KM; ++q) {
 #pragma unroll
-          for (int e = 0; e < G; ++e) m[it][e] -= h[q] * bw[it][q][e];
+          for (int e = 0; e < G; ++e) m[it][e] = fma(-h[q], bw[it][q][e], m[it][e]);
         }
       }
 #pragma unroll
       for (int q = 0; q < KM; ++q) {
 #pragma unroll
-        for (int e = 0; e < G; ++e) acc[q] += bw[it][q][e] * m[it][e];
+        for (int e = 0; e < G; ++e) acc[q] = fma(bw[it][q][e], m[it][e], acc[q]);
       }
 #pragma unroll
-      for (int e = 0; e < G; ++e) acc[KM] += m[it][e] * m[it][e];
+      for (int e = 0; e < G; ++e) acc[KM] = fma(m[it][e], m[it][e], acc[KM]);
     }
   }
   block_sum_k<KM + 1>(acc, red);
   C* part = reinterpret_cast<C*>(p.partial);
   if (threadIdx.x == 0) {
 #pragma unroll
-    for (int q = 0; q <= KM; ++q) part[blockIdx.x * (KM + 1) + q] = acc[q];
+    for (int q = 0; q <= KM; ++q) part[bid * (KM + 1) + q] = acc[q];
   }
-  if (!last_block_arrived(p.counters + (PASS - 1))) return;
+  if (!last_block_arrived_n(p.counters + (PASS - 1), (unsigned)nb)) return;
   C tc[KM + 1];
-  reduce_partials<KM + 1>(part, (int)gridDim.x, tc, red);
+  reduce_partials<KM + 1>(part, nb, tc, red);
   if (threadIdx.x != 0) return;
   C* cf = coef_row<C>(p, j);
   double tot[KM + 1];
@@ -351,6 +373,41 @@ dots_kernel(BasisParams p, OpView<typename Compute<T>::type> A, int j) {
   cf[kMaxK] = brk ? (C)0 : (C)1 / nuc;
   if (p.Hbar) p.Hbar[(int64_t)j * (p.d + 1) + j + 1] = nu;
   if (brk) *p.stop = j + 1;
+}
+
+template <typename T, int KM, int G, bool STORE_M, int PASS>
+__global__ void __launch_bounds__(kBasisThreads)
+dots_kernel(BasisParams p, OpView<typename Compute<T>::type> A, int j) {
+  dots_body<T, KM, G, STORE_M, PASS>(p, A, j, blockIdx.x, gridDim.x);
+}
+
+// ---- grouped passes (batched solver) -------------------------------------------
+// map[blockIdx.x] = {slot, block of that job}; the job's vector path picks
+// the body instantiation (the branch is uniform over the CTA).  The map and
+// the job array are written before the cycle, so the prologue may read them
+// before the programmatic wait.
+template <typename T, int KM, bool STORE_M>
+__global__ void __launch_bounds__(kBasisThreads)
+g_form_kernel(const GJob* __restrict__ jobs, const int2* __restrict__ map, int c) {
+  using C = typename Compute<T>::type;
+  const int2 m = map[blockIdx.x];
+  const GJob& J = jobs[m.x];
+  const BasisParams& p = J.bp;
+  const OpView<C>& A = job_view<C>(J);
+  if (J.vec) form_body<T, KM, 4, STORE_M>(p, A, c, m.y, p.nblk);
+  else form_body<T, KM, 1, STORE_M>(p, A, c, m.y, p.nblk);
+}
+
+template <typename T, int KM, bool STORE_M, int PASS>
+__global__ void __launch_bounds__(kBasisThreads)
+g_dots_kernel(const GJob* __restrict__ jobs, const int2* __restrict__ map, int j) {
+  using C = typename Compute<T>::type;
+  const int2 m = map[blockIdx.x];
+  const GJob& J = jobs[m.x];
+  const BasisParams& p = J.bp;
+  const OpView<C>& A = job_view<C>(J);
+  if (J.vec) dots_body<T, KM, 4, STORE_M, PASS>(p, A, j, m.y, p.nblk);
+  else dots_body<T, KM, 1, STORE_M, PASS>(p, A, j, m.y, p.nblk);
 }
 
 // prio != 0 gives the launch that priority (the pipelined cycle raises the
@@ -394,6 +451,7 @@ static cudaError_t launch_pdl(K kernel, int grid, cudaStream_t st, bool pdl, int
 template <typename T, int G>
 __global__ void __launch_bounds__(kBasisThreads)
 cheb_kernel(BasisParams p, OpView<typename Compute<T>::type> A, int c) {
+  constexpr int kIter = IterOf<G>::value;
   using C = typename Compute<T>::type;
   __shared__ C red[2 * (kBasisThreads / 32)];
   const int64_t n = p.n;
@@ -543,12 +601,42 @@ bool basis_vector_path(const sk_op* op, int64_t ldb, const void* B) {
 }
 
 int basis_grid(int64_t n, int G) {
-  // every thread handles exactly kIter groups of G elements (registers hold
+  // every thread handles exactly IterOf<G> groups of G elements (registers hold
   // the prefetched operands); the grid grows with n
-  const int64_t per = (int64_t)kBasisThreads * G * kIter;
+  const int64_t per = (int64_t)kBasisThreads * G * (G == 4 ? IterOf<4>::value : IterOf<1>::value);
   int64_t g = (n + per - 1) / per;
   if (g < 1) g = 1;
   return (int)g;
+}
+
+template <typename T, int KM, bool SM>
+static sk_status enqueue_basis_grouped_t(const GJob* jobs, const int2* map, int nmap, int passes, int d,
+                                         cudaStream_t st) {
+  SK_CUDA(launch_pdl(g_form_kernel<T, KM, SM>, nmap, st, false, 0, jobs, map, 0));
+  for (int j = 0; j < d; ++j) {
+    SK_CUDA(launch_pdl(g_dots_kernel<T, KM, SM, 1>, nmap, st, true, 0, jobs, map, j));
+    if (passes == 2) SK_CUDA(launch_pdl(g_dots_kernel<T, KM, SM, 2>, nmap, st, true, 0, jobs, map, j));
+    SK_CUDA(launch_pdl(g_form_kernel<T, KM, SM>, nmap, st, true, 0, jobs, map, j + 1));
+  }
+  return SK_OK;
+}
+
+template <typename T, bool SM>
+static sk_status enqueue_basis_grouped_k(const GJob* jobs, const int2* map, int nmap, int k, int passes, int d,
+                                         cudaStream_t st) {
+  if (k <= 2) return enqueue_basis_grouped_t<T, 2, SM>(jobs, map, nmap, passes, d, st);
+  if (k <= 4) return enqueue_basis_grouped_t<T, 4, SM>(jobs, map, nmap, passes, d, st);
+  if (k <= 8) return enqueue_basis_grouped_t<T, 8, SM>(jobs, map, nmap, passes, d, st);
+  return enqueue_basis_grouped_t<T, 16, SM>(jobs, map, nmap, passes, d, st);
+}
+
+sk_status enqueue_basis_grouped(const GJob* jobs, const int2* map, int nmap, sk_dtype dt, int k, int passes, int d,
+                                cudaStream_t st) {
+  if (k > kMaxK) { set_error("k <= %d supported", kMaxK); return SK_EINVAL; }
+  if (nmap <= 0) return SK_OK;
+  if (dt == SK_F64) return enqueue_basis_grouped_k<double, true>(jobs, map, nmap, k, passes, d, st);
+  if (dt == SK_F32) return enqueue_basis_grouped_k<float, false>(jobs, map, nmap, k, passes, d, st);
+  return enqueue_basis_grouped_k<__nv_bfloat16, false>(jobs, map, nmap, k, passes, d, st);
 }
 
 sk_status enqueue_basis(const BasisParams& p, const sk_op* op, cudaStream_t st) {

@@ -132,17 +132,37 @@ __device__ __forceinline__ void block_sum_k(V (&v)[K], V* sh) {
 // in the last block the barrier after it orders every thread's reads of the
 // partials after thread 0's acquire.  The counter is reset by the last block
 // so that the launch can be replayed (CUDA graphs).
-__device__ __forceinline__ bool last_block_arrived(unsigned int* counter) {
+// `nblocks` blocks share the counter (the whole grid, or one job's blocks of
+// a grouped launch).
+__device__ __forceinline__ bool last_block_arrived_n(unsigned int* counter, unsigned nblocks) {
   __shared__ bool s_last;
   __syncthreads();
   if (threadIdx.x == 0) {
     cuda::atomic_ref<unsigned int, cuda::thread_scope_device> c(*counter);
     const unsigned prev = c.fetch_add(1u, cuda::memory_order_acq_rel);
-    s_last = (prev == gridDim.x * gridDim.y - 1);
+    s_last = (prev == nblocks - 1);
     if (s_last) c.store(0u, cuda::memory_order_relaxed);
   }
   __syncthreads();
   return s_last;
+}
+__device__ __forceinline__ bool last_block_arrived(unsigned int* counter) {
+  return last_block_arrived_n(counter, gridDim.x * gridDim.y);
+}
+
+// Grouped launches of the batched solver over its small dense problems:
+// blockIdx.y picks job slot ids[blockIdx.y] (ids NULL: slot blockIdx.y),
+// whose buffers lie `stride` bytes apart (one slab per slot, the same
+// layout in every slab).  stride = 0: a single problem (grid.y = 1).
+struct JobSlab {
+  const int* ids = nullptr;
+  int64_t stride = 0;
+};
+template <typename P>
+__device__ __forceinline__ P* at_job(P* p, const JobSlab& js) {
+  if (js.stride == 0) return p;
+  const int64_t j = js.ids ? js.ids[blockIdx.y] : blockIdx.y;
+  return reinterpret_cast<P*>(reinterpret_cast<uintptr_t>(p) + j * js.stride);
 }
 
 // ----------------------------------------------------------------------------
@@ -219,13 +239,30 @@ struct OpView {
   const int64_t* sell_ptr;  // SELL-32 (see sk_op); NULL: plain CSR rows
   const int32_t* sell_col;
   const C* sell_val;
+  // i / nx for 0 <= i < 2^31 as (i * nx_m) >> nx_s (nx_s = 0: plain division);
+  // set by make_view (set_div_magic)
+  uint64_t nx_m;
+  int nx_s;
+
+  // grid position of unknown i: column ix, row iy
+  __device__ __forceinline__ void grid_pos(int64_t i, int& ix, int64_t& iy) const {
+    if (nx_s) {
+      const int64_t q = (int64_t)(((uint64_t)i * nx_m) >> nx_s);
+      iy = q;
+      ix = (int)(i - q * nx);
+    } else {
+      iy = i / nx;
+      ix = (int)(i - iy * nx);
+    }
+  }
 
   // (A x)_i, x of storage type T (converted to C on load).
   template <typename T>
   __device__ __forceinline__ C apply(const T* __restrict__ x, int64_t i) const {
     if (kind == OP_STENCIL5) {
-      const int ix = (int)(i % nx);
-      const int64_t iy = i / nx;
+      int ix;
+      int64_t iy;
+      grid_pos(i, ix, iy);
       C acc = cP * to_c(x[i]);
       if (ix + 1 < nx) acc += cE * to_c(x[i + 1]);
       if (ix > 0) acc += cW * to_c(x[i - 1]);
@@ -234,8 +271,9 @@ struct OpView {
       if (shift) acc += shift[i] * to_c(x[i]);
       return acc;
     } else if (kind == OP_DIFFUSION) {
-      const int ix = (int)(i % nx);
-      const int64_t iy = i / nx;
+      int ix;
+      int64_t iy;
+      grid_pos(i, ix, iy);
       const C tP = theta[i];
       const C xP = to_c(x[i]);
       C acc = 0;
@@ -260,6 +298,22 @@ struct OpView {
     }
   }
 };
+
+// Division by the invariant nx (Granlund and Montgomery, "Division by
+// invariant integers using multiplication", 1994): with l = ceil(log2 nx) and
+// m = floor(2^(31+l) / nx) + 1, (i * m) >> (31 + l) = floor(i / nx) for every
+// 0 <= i < 2^31, because i * m / 2^(31+l) exceeds i / nx by less than
+// 2^-l <= 1/nx, too little to cross the next integer; i * m < 2^64.  Views of
+// operators with n > 2^31 keep plain division.
+inline void set_div_magic(int nx, int64_t n, uint64_t* m, int* s) {
+  *m = 0;
+  *s = 0;
+  if (nx < 1 || n > (1ll << 31)) return;
+  int l = 0;
+  while ((1ll << l) < nx) ++l;
+  *s = 31 + l;
+  *m = ((1ull << (31 + l)) / (uint64_t)nx) + 1;
+}
 
 // Build a view for compute type C (FP32 views use the op's FP32 copies).
 sk_status make_view(const sk_op* op, OpView<double>* v);

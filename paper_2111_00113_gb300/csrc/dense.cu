@@ -24,7 +24,12 @@ namespace sk {
 // for columns c0 <= j < c1 (0 <= c0 < c1 <= d): the product for j < du
 // (du = min(stop, d)), zero for du <= j.
 __global__ void hbar_product_kernel(const double* __restrict__ SB, const double* __restrict__ Hbar, int s, int d,
-                                    int k, const int* __restrict__ stop, int c0, int c1, double* __restrict__ Aug) {
+                                    int k, const int* __restrict__ stop, int c0, int c1, double* __restrict__ Aug,
+                                    JobSlab js) {
+  SB = at_job(SB, js);
+  Hbar = at_job(Hbar, js);
+  stop = at_job(stop, js);
+  Aug = at_job(Aug, js);
   const int du = min(*stop, d);
   const int64_t total = (int64_t)s * (c1 - c0);
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
@@ -67,7 +72,11 @@ __device__ __forceinline__ double block_sum1(double v, double* sh) {
 // in global memory (fallback for panels too tall for shared memory).
 __global__ void __launch_bounds__(kQrPanelThreads)
 qr_panel_global_kernel(double* __restrict__ Aug, int s, int p0, int nbc, double* __restrict__ rdiag,
-                double* __restrict__ tau, double* __restrict__ Tws) {
+                double* __restrict__ tau, double* __restrict__ Tws, JobSlab js) {
+  Aug = at_job(Aug, js);
+  rdiag = at_job(rdiag, js);
+  tau = at_job(tau, js);
+  Tws = at_job(Tws, js);
   __shared__ double sh[32];
   __shared__ double s_tau[kQrNb];
   __shared__ double s_T[kQrNb * kQrNb];
@@ -136,7 +145,11 @@ qr_panel_global_kernel(double* __restrict__ Aug, int s, int p0, int nbc, double*
 // whole block), and written back with the compact-WY factor T.
 __global__ void __launch_bounds__(kQrPanelThreads)
 qr_panel_kernel(double* __restrict__ Aug, int s, int p0, int nbc, double* __restrict__ rdiag,
-                double* __restrict__ tau, double* __restrict__ Tws) {
+                double* __restrict__ tau, double* __restrict__ Tws, JobSlab js) {
+  Aug = at_job(Aug, js);
+  rdiag = at_job(rdiag, js);
+  tau = at_job(tau, js);
+  Tws = at_job(Tws, js);
   extern __shared__ double P[];  // len x nbc, column-major, ld = len
   __shared__ double sh[32];
   __shared__ double s_tau[kQrNb];
@@ -253,7 +266,11 @@ static constexpr int kQrRowWarps = kQrClusterThreads / 32 - 1;
 
 __global__ void __launch_bounds__(kQrClusterThreads)
 qr_panel_cluster_kernel(double* __restrict__ Aug, int s, int p0, int nbc, double* __restrict__ rdiag,
-                        double* __restrict__ tau, double* __restrict__ Tws) {
+                        double* __restrict__ tau, double* __restrict__ Tws, JobSlab js) {
+  Aug = at_job(Aug, js);
+  rdiag = at_job(rdiag, js);
+  tau = at_job(tau, js);
+  Tws = at_job(Tws, js);
   cg::cluster_group cluster = cg::this_cluster();
   extern __shared__ double P[];                           // rows x kQrNb, column-major (ld = per)
   __shared__ double slot[2][kQrCluster][kQrNb];            // tot partials of every rank
@@ -391,7 +408,9 @@ static constexpr int kWyThreads = 128;
 
 __global__ void __launch_bounds__(kWyThreads)
 qr_apply_cluster_kernel(double* __restrict__ Aug, int s, int p_first, int p_last, int last_nbc, int c0,
-                        const double* __restrict__ Tws) {
+                        const double* __restrict__ Tws, JobSlab js) {
+  Aug = at_job(Aug, js);
+  Tws = at_job(Tws, js);
   cg::cluster_group cluster = cg::this_cluster();
   __shared__ double slot[2][kWyCluster][kQrNb];
   __shared__ double red[kWyThreads / 32][kQrNb];
@@ -457,10 +476,10 @@ qr_apply_cluster_kernel(double* __restrict__ Aug, int s, int p_first, int p_last
 // Panels p_first .. p_last - 1 (the last with last_nbc columns) applied to
 // columns [c0, c0 + ncols).
 static sk_status launch_wy_apply(double* Aug, int s, int p_first, int p_last, int last_nbc, int c0, int ncols,
-                                 const double* Tws, cudaStream_t st) {
+                                 const double* Tws, cudaStream_t st, const JobSlab& js = JobSlab(), int nj = 1) {
   if (ncols <= 0 || p_last <= p_first) return SK_OK;
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)ncols * kWyCluster);
+  cfg.gridDim = dim3((unsigned)ncols * kWyCluster, (unsigned)nj);
   cfg.blockDim = dim3(kWyThreads);
   cfg.dynamicSmemBytes = 0;
   cfg.stream = st;
@@ -471,7 +490,7 @@ static sk_status launch_wy_apply(double* Aug, int s, int p_first, int p_last, in
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  SK_CUDA(cudaLaunchKernelEx(&cfg, qr_apply_cluster_kernel, Aug, s, p_first, p_last, last_nbc, c0, Tws));
+  SK_CUDA(cudaLaunchKernelEx(&cfg, qr_apply_cluster_kernel, Aug, s, p_first, p_last, last_nbc, c0, Tws, js));
   return SK_OK;
 }
 
@@ -482,11 +501,11 @@ static sk_status launch_wy_apply(double* Aug, int s, int p_first, int p_last, in
 // instruction per 16 cycles and the per-column products and reductions of
 // the whole panel then queue on it.)
 static sk_status factor_panel(double* Aug, int s, int p0, int nbc, double* rdiag, double* tau, double* T,
-                              cudaStream_t st) {
+                              cudaStream_t st, const JobSlab& js = JobSlab(), int nj = 1) {
   const int per = (s - p0 + kQrCluster - 1) / kQrCluster;
   if (s - p0 >= 4 * kQrCluster && (size_t)per * kQrNb * sizeof(double) <= (size_t)kDynSmemLimit) {
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(kQrCluster);
+    cfg.gridDim = dim3(kQrCluster, (unsigned)nj);
     cfg.blockDim = dim3(kQrClusterThreads);
     cfg.dynamicSmemBytes = (size_t)per * kQrNb * sizeof(double);
     cfg.stream = st;
@@ -498,27 +517,27 @@ static sk_status factor_panel(double* Aug, int s, int p0, int nbc, double* rdiag
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     SK_CUDA(cudaFuncSetAttribute(qr_panel_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kDynSmemLimit));
-    SK_CUDA(cudaLaunchKernelEx(&cfg, qr_panel_cluster_kernel, Aug, s, p0, nbc, rdiag, tau, T));
+    SK_CUDA(cudaLaunchKernelEx(&cfg, qr_panel_cluster_kernel, Aug, s, p0, nbc, rdiag, tau, T, js));
     return SK_OK;
   }
   const size_t smem = (size_t)(s - p0) * nbc * sizeof(double);
   if (smem <= 200 * 1024) {
     SK_CUDA(cudaFuncSetAttribute(qr_panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kDynSmemLimit));
-    qr_panel_kernel<<<1, kQrPanelThreads, smem, st>>>(Aug, s, p0, nbc, rdiag, tau, T);
+    qr_panel_kernel<<<dim3(1, nj), kQrPanelThreads, smem, st>>>(Aug, s, p0, nbc, rdiag, tau, T, js);
   } else {
-    qr_panel_global_kernel<<<1, kQrPanelThreads, 0, st>>>(Aug, s, p0, nbc, rdiag, tau, T);
+    qr_panel_global_kernel<<<dim3(1, nj), kQrPanelThreads, 0, st>>>(Aug, s, p0, nbc, rdiag, tau, T, js);
   }
   return SK_OK;
 }
 
 sk_status enqueue_qr(double* Aug, int s, int nq, int ncols, double* rdiag, double* tau, double* Tws,
-                     cudaStream_t st) {
+                     cudaStream_t st, const JobSlab& js, int nj) {
   for (int p0 = 0; p0 < nq; p0 += kQrNb) {
     const int nbc = (nq - p0) < kQrNb ? (nq - p0) : kQrNb;
     double* T = Tws + (int64_t)(p0 / kQrNb) * kQrNb * kQrNb;
-    SK_TRY(factor_panel(Aug, s, p0, nbc, rdiag, tau, T, st));
+    SK_TRY(factor_panel(Aug, s, p0, nbc, rdiag, tau, T, st, js, nj));
     const int c0 = p0 + nbc;
-    SK_TRY(launch_wy_apply(Aug, s, p0 / kQrNb, p0 / kQrNb + 1, nbc, c0, ncols - c0, Tws, st));
+    SK_TRY(launch_wy_apply(Aug, s, p0 / kQrNb, p0 / kQrNb + 1, nbc, c0, ncols - c0, Tws, st, js, nj));
   }
   SK_CUDA(cudaGetLastError());
   return SK_OK;
@@ -690,7 +709,12 @@ __device__ __forceinline__ long long warp_scan_min(long long v) {
 
 __global__ void __launch_bounds__(kLsThreads)
 ls_solve_kernel(const double* __restrict__ Aug, const double* __restrict__ rdiag, const double* __restrict__ z,
-                int s, int d, double stab_tol, double* __restrict__ y, double* __restrict__ diag) {
+                int s, int d, double stab_tol, double* __restrict__ y, double* __restrict__ diag, JobSlab js) {
+  Aug = at_job(Aug, js);
+  rdiag = at_job(rdiag, js);
+  z = at_job(z, js);
+  y = at_job(y, js);
+  diag = at_job(diag, js);
   extern __shared__ double zz[];  // d right-hand side entries, then the 32 x d block of R
   double* Rb = zz + d;             // Rb[c * d + t] = R[t, i0 + c]
   __shared__ long long wmax[kLsThreads / 32], wmin[kLsThreads / 32];
@@ -812,31 +836,31 @@ ls_solve_kernel(const double* __restrict__ Aug, const double* __restrict__ rdiag
 }
 
 sk_status enqueue_ls_solve(const double* Aug, const double* rdiag, int s, int d, double stab_tol, double* y,
-                           double* diag, cudaStream_t st) {
-  return enqueue_ls_solve_z(Aug, rdiag, Aug + (size_t)d * s, s, d, stab_tol, y, diag, st);
+                           double* diag, cudaStream_t st, const JobSlab& js, int nj) {
+  return enqueue_ls_solve_z(Aug, rdiag, Aug + (size_t)d * s, s, d, stab_tol, y, diag, st, js, nj);
 }
 
 sk_status enqueue_ls_solve_z(const double* Aug, const double* rdiag, const double* z, int s, int d, double stab_tol,
-                             double* y, double* diag, cudaStream_t st) {
+                             double* y, double* diag, cudaStream_t st, const JobSlab& js, int nj) {
   const size_t smem = (size_t)d * 33 * sizeof(double);
   if (d < 1 || smem > (size_t)kDynSmemLimit) { set_error("ls_solve: d out of range"); return SK_EINVAL; }
   SK_CUDA(cudaFuncSetAttribute(ls_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kDynSmemLimit));
-  ls_solve_kernel<<<1, kLsThreads, smem, st>>>(Aug, rdiag, z, s, d, stab_tol, y, diag);
+  ls_solve_kernel<<<dim3(1, nj), kLsThreads, smem, st>>>(Aug, rdiag, z, s, d, stab_tol, y, diag, js);
   SK_CUDA(cudaGetLastError());
   return SK_OK;
 }
 
 sk_status enqueue_hbar_product(const double* SB, const double* Hbar, int s, int d, int k, const int* stop,
-                               double* Aug, cudaStream_t st) {
-  return enqueue_hbar_product_cols(SB, Hbar, s, d, k, stop, 0, d, Aug, st);
+                               double* Aug, cudaStream_t st, const JobSlab& js, int nj) {
+  return enqueue_hbar_product_cols(SB, Hbar, s, d, k, stop, 0, d, Aug, st, js, nj);
 }
 
 sk_status enqueue_hbar_product_cols(const double* SB, const double* Hbar, int s, int d, int k, const int* stop,
-                                    int c0, int c1, double* Aug, cudaStream_t st) {
+                                    int c0, int c1, double* Aug, cudaStream_t st, const JobSlab& js, int nj) {
   if (c0 < 0 || c1 > d || c0 >= c1) { set_error("hbar_product: bad column range"); return SK_EINVAL; }
   int blocks = (int)(((int64_t)s * (c1 - c0) + 255) / 256);
   if (blocks > 4 * num_sms()) blocks = 4 * num_sms();
-  hbar_product_kernel<<<blocks, 256, 0, st>>>(SB, Hbar, s, d, k, stop, c0, c1, Aug);
+  hbar_product_kernel<<<dim3(blocks, nj), 256, 0, st>>>(SB, Hbar, s, d, k, stop, c0, c1, Aug, js);
   SK_CUDA(cudaGetLastError());
   return SK_OK;
 }

@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "grouped.cuh"
 
 namespace sk {
 
@@ -401,17 +402,19 @@ __device__ __forceinline__ void seg_acc(double (&acc)[8], int k, const unsigned 
   acc[2 * k + 1] = fma(sd, x.y, acc[2 * k + 1]);
 }
 
+// Body of the row-owner gather for column tile `tile` and chunk group `g`
+// (blockIdx.x and blockIdx.y of a single launch).
 template <typename T>
-__global__ void __launch_bounds__(kRowsMaxS)
-gather_rows_kernel(const T* __restrict__ B, int64_t ldb, int ncols, int64_t n, int s, int zeta, int nchunks,
-                   int chunks_per_group, const uint32_t* __restrict__ rowptr, const uint16_t* __restrict__ entries,
-                   double* __restrict__ partial) {
+__device__ __forceinline__ void gather_rows_body(const T* __restrict__ B, int64_t ldb, int ncols, int64_t n, int s,
+                                                 int zeta, int nchunks, int chunks_per_group,
+                                                 const uint32_t* __restrict__ rowptr,
+                                                 const uint16_t* __restrict__ entries, double* __restrict__ partial,
+                                                 int tile, int g) {
   constexpr int E = (int)sizeof(T);
   constexpr int W = RowsW<T>::value;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const size_t buf_bytes = rows_buf_bytes(s, zeta);
-  const int col0 = blockIdx.x * W;
-  const int g = blockIdx.y;
+  const int col0 = tile * W;
   const int c_begin = g * chunks_per_group;
   const int c_end = min(nchunks, c_begin + chunks_per_group);
   const int nt = blockDim.x;
@@ -520,6 +523,15 @@ gather_rows_kernel(const T* __restrict__ B, int64_t ldb, int ncols, int64_t n, i
   }
 }
 
+template <typename T>
+__global__ void __launch_bounds__(kRowsMaxS)
+gather_rows_kernel(const T* __restrict__ B, int64_t ldb, int ncols, int64_t n, int s, int zeta, int nchunks,
+                   int chunks_per_group, const uint32_t* __restrict__ rowptr, const uint16_t* __restrict__ entries,
+                   double* __restrict__ partial) {
+  gather_rows_body<T>(B, ldb, ncols, n, s, zeta, nchunks, chunks_per_group, rowptr, entries, partial, blockIdx.x,
+                      blockIdx.y);
+}
+
 // One column (the sketched residual g = S r): thread r owns sketch row r and
 // sums in a register over all chunks of its group; the chunk of the vector
 // is contiguous, so it is staged with 16-byte asynchronous copies (double
@@ -528,13 +540,12 @@ __host__ __device__ static inline size_t col_buf_bytes(int s, int zeta) {
   return (size_t)kChunk * sizeof(double) + entries_bytes(zeta) + (size_t)rp_stride(s) * sizeof(uint32_t);
 }
 
-__global__ void __launch_bounds__(kRowsMaxS)
-gather_col_kernel(const double* __restrict__ x, int64_t n, int s, int zeta, int nchunks, int chunks_per_group,
-                  const uint32_t* __restrict__ rowptr, const uint16_t* __restrict__ entries,
-                  double* __restrict__ partial) {
+__device__ __forceinline__ void gather_col_body(const double* __restrict__ x, int64_t n, int s, int zeta, int nchunks,
+                                                int chunks_per_group, const uint32_t* __restrict__ rowptr,
+                                                const uint16_t* __restrict__ entries, double* __restrict__ partial,
+                                                int g) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const size_t buf_bytes = col_buf_bytes(s, zeta);
-  const int g = blockIdx.x;
   const int c_begin = g * chunks_per_group;
   const int c_end = min(nchunks, c_begin + chunks_per_group);
   const int nt = blockDim.x;
@@ -587,14 +598,55 @@ gather_col_kernel(const double* __restrict__ x, int64_t n, int s, int zeta, int 
   if (r < s) partial[(int64_t)g * s + r] = acc;
 }
 
-__global__ void reduce_partials_kernel(const double* __restrict__ partial, int ngroups, int ncols, int s,
-                                       double scale, double* __restrict__ SB) {
+__global__ void __launch_bounds__(kRowsMaxS)
+gather_col_kernel(const double* __restrict__ x, int64_t n, int s, int zeta, int nchunks, int chunks_per_group,
+                  const uint32_t* __restrict__ rowptr, const uint16_t* __restrict__ entries,
+                  double* __restrict__ partial) {
+  gather_col_body(x, n, s, zeta, nchunks, chunks_per_group, rowptr, entries, partial, blockIdx.x);
+}
+
+// Each output entry sums its groups' partials in group order (the result
+// does not depend on the grid).
+__device__ __forceinline__ void reduce_partials_body(const double* __restrict__ partial, int ngroups, int ncols, int s,
+                                                     double scale, double* __restrict__ SB) {
   const int64_t total = (int64_t)ncols * s;
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
     double a = 0;
     for (int g = 0; g < ngroups; ++g) a += partial[(int64_t)g * total + q];
     SB[q] = a * scale;
   }
+}
+
+__global__ void reduce_partials_kernel(const double* __restrict__ partial, int ngroups, int ncols, int s,
+                                       double scale, double* __restrict__ SB) {
+  reduce_partials_body(partial, ngroups, ncols, s, scale, SB);
+}
+
+// ---- grouped sketches (batched solver): map[blockIdx.x] = {slot, local block} --
+template <typename T>
+__global__ void __launch_bounds__(kRowsMaxS)
+g_gather_rows_kernel(const GJob* __restrict__ jobs, const int2* __restrict__ map, int ncols, int s, int zeta) {
+  const int2 m = map[blockIdx.x];
+  const GJob& J = jobs[m.x];
+  const int nt = J.rows_ntiles;
+  gather_rows_body<T>(static_cast<const T*>(J.bp.B), J.bp.ldb, ncols, J.bp.n, s, zeta, J.nchunks, J.rows_cpg,
+                      J.rowptr, J.entries, J.rows_part, m.y % nt, m.y / nt);
+}
+
+__global__ void __launch_bounds__(kRowsMaxS)
+g_gather_col_kernel(const GJob* __restrict__ jobs, const int2* __restrict__ map, int s, int zeta) {
+  const int2 m = map[blockIdx.x];
+  const GJob& J = jobs[m.x];
+  gather_col_body(J.bp.r, J.bp.n, s, zeta, J.nchunks, J.col_cpg, J.rowptr, J.entries, J.col_part, m.y);
+}
+
+// blockIdx.y = slot ids[blockIdx.y]: rows = 1 reduces the basis sketch into
+// SB, rows = 0 the residual's into g.
+__global__ void g_reduce_kernel(const GJob* __restrict__ jobs, const int* __restrict__ ids, int ncols, int s,
+                                double scale, int rows) {
+  const GJob& J = jobs[ids[blockIdx.y]];
+  if (rows) reduce_partials_body(J.rows_part, J.rows_ngroups, ncols, s, scale, J.SB);
+  else reduce_partials_body(J.col_part, J.col_ngroups, 1, s, scale, J.g);
 }
 
 template <typename T, int W>
@@ -810,6 +862,55 @@ static sk_status noalloc_scratch_ptr(unsigned char** out) {
     ptrs[dev] = (unsigned char*)p;
   }
   *out = ptrs[dev];
+  return SK_OK;
+}
+
+
+void sketch_shapes(const SketchPlan& p, int ncols, sk_dtype dt, int* rows_ntiles, int* rows_ngroups, int* rows_cpg,
+                   int* col_ngroups, int* col_cpg) {
+  const GatherShape gr = gather_shape(p, ncols, dt, true);
+  *rows_ntiles = gr.rows ? gr.ntiles : 0;  // 0: not the row-owner kernel (the grouped path needs it)
+  *rows_ngroups = gr.ngroups;
+  *rows_cpg = gr.cpg;
+  const GatherShape gc = gather_shape(p, 1, SK_F64, false);
+  *col_ngroups = gc.col ? gc.ngroups : 0;
+  *col_cpg = gc.cpg;
+}
+
+sk_status enqueue_sketch_rows_grouped(const GJob* jobs, const int2* map, int nmap, const int* ids, int nj, sk_dtype dt,
+                                      int ncols, int s, int zeta, cudaStream_t st) {
+  if (nmap <= 0 || nj <= 0) return SK_OK;
+  const size_t smem = 2 * rows_buf_bytes(s, zeta);
+  const int threads = (s + 31) / 32 * 32;
+  if (dt == SK_F64) {
+    SK_CUDA(cudaFuncSetAttribute(g_gather_rows_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, kDynSmemLimit));
+    g_gather_rows_kernel<double><<<nmap, threads, smem, st>>>(jobs, map, ncols, s, zeta);
+  } else if (dt == SK_F32) {
+    SK_CUDA(cudaFuncSetAttribute(g_gather_rows_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, kDynSmemLimit));
+    g_gather_rows_kernel<float><<<nmap, threads, smem, st>>>(jobs, map, ncols, s, zeta);
+  } else {
+    set_error("grouped sketch: FP32 or FP64 basis expected");
+    return SK_EINVAL;
+  }
+  SK_CUDA(cudaGetLastError());
+  int rb = (int)(((int64_t)ncols * s + 255) / 256);
+  if (rb > 4 * num_sms()) rb = 4 * num_sms();
+  g_reduce_kernel<<<dim3(rb, nj), 256, 0, st>>>(jobs, ids, ncols, s, 1.0 / std::sqrt((double)zeta), 1);
+  SK_CUDA(cudaGetLastError());
+  return SK_OK;
+}
+
+sk_status enqueue_sketch_col_grouped(const GJob* jobs, const int2* map, int nmap, const int* ids, int nj, int s,
+                                     int zeta, cudaStream_t st) {
+  if (nmap <= 0 || nj <= 0) return SK_OK;
+  const size_t smem = 2 * col_buf_bytes(s, zeta);
+  SK_CUDA(cudaFuncSetAttribute(g_gather_col_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kDynSmemLimit));
+  g_gather_col_kernel<<<nmap, (s + 31) / 32 * 32, smem, st>>>(jobs, map, s, zeta);
+  SK_CUDA(cudaGetLastError());
+  int rb = (s + 255) / 256;
+  if (rb > 4 * num_sms()) rb = 4 * num_sms();
+  g_reduce_kernel<<<dim3(rb, nj), 256, 0, st>>>(jobs, ids, 1, s, 1.0 / std::sqrt((double)zeta), 0);
+  SK_CUDA(cudaGetLastError());
   return SK_OK;
 }
 

@@ -23,6 +23,7 @@
 #include "basis.cuh"
 #include "common.cuh"
 #include "dense.cuh"
+#include "grouped.cuh"
 #include "srr.cuh"
 
 namespace sk {
@@ -55,7 +56,7 @@ __device__ __forceinline__ void gload_rows(const T* __restrict__ col, int64_t i,
   }
 }
 
-static int vec_grid(int64_t n) {
+int vec_grid(int64_t n) {
   int64_t g = (n + kVecThreads * 4 - 1) / (kVecThreads * 4);
   const int64_t gmax = 2 * num_sms();
   if (g > gmax) g = gmax;
@@ -63,42 +64,55 @@ static int vec_grid(int64_t n) {
   return (int)g;
 }
 
-// r = b - A x and ||r||^2 (last-block reduction into *rho2); NaN -> *nanflag.
-__global__ void __launch_bounds__(kVecThreads)
-residual_kernel(OpView<double> A, const double* __restrict__ b, const double* __restrict__ x, double* __restrict__ r,
-                double* __restrict__ partial, unsigned* __restrict__ counter, double* __restrict__ rho2) {
+// r = b - A x and ||r||^2 (last-block reduction into *rho2).  Block `bid`
+// of `nb` (the grid, or one job's blocks of a grouped launch).
+__device__ __forceinline__ void residual_body(const OpView<double>& A, const double* __restrict__ b,
+                                              const double* __restrict__ x, double* __restrict__ r,
+                                              double* __restrict__ partial, unsigned* __restrict__ counter,
+                                              double* __restrict__ rho2, int bid, int nb) {
   __shared__ double red[kVecThreads / 32];
   double acc[1] = {0.0};
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < A.n; i += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t i = bid * (int64_t)blockDim.x + threadIdx.x; i < A.n; i += (int64_t)nb * blockDim.x) {
     const double v = b[i] - A.apply(x, i);
     r[i] = v;
     acc[0] += v * v;
   }
   block_sum_k<1>(acc, red);
-  if (threadIdx.x == 0) partial[blockIdx.x] = acc[0];
-  if (!last_block_arrived(counter)) return;
+  if (threadIdx.x == 0) partial[bid] = acc[0];
+  if (!last_block_arrived_n(counter, (unsigned)nb)) return;
   if (threadIdx.x == 0) {
     double t = 0;
-    for (int q = 0; q < (int)gridDim.x; ++q) t += __ldcg(partial + q);
+    for (int q = 0; q < nb; ++q) t += __ldcg(partial + q);
     *rho2 = t;
+  }
+}
+
+__global__ void __launch_bounds__(kVecThreads)
+residual_kernel(OpView<double> A, const double* __restrict__ b, const double* __restrict__ x, double* __restrict__ r,
+                double* __restrict__ partial, unsigned* __restrict__ counter, double* __restrict__ rho2) {
+  residual_body(A, b, x, r, partial, counter, rho2, blockIdx.x, gridDim.x);
+}
+
+__device__ __forceinline__ void norm2_body(const double* __restrict__ v, int64_t n, double* __restrict__ partial,
+                                           unsigned* __restrict__ counter, double* __restrict__ out, int bid, int nb) {
+  __shared__ double red[kVecThreads / 32];
+  double acc[1] = {0.0};
+  for (int64_t i = bid * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)nb * blockDim.x)
+    acc[0] += v[i] * v[i];
+  block_sum_k<1>(acc, red);
+  if (threadIdx.x == 0) partial[bid] = acc[0];
+  if (!last_block_arrived_n(counter, (unsigned)nb)) return;
+  if (threadIdx.x == 0) {
+    double t = 0;
+    for (int q = 0; q < nb; ++q) t += __ldcg(partial + q);
+    *out = t;
   }
 }
 
 __global__ void __launch_bounds__(kVecThreads)
 norm2_kernel(const double* __restrict__ v, int64_t n, double* __restrict__ partial, unsigned* __restrict__ counter,
              double* __restrict__ out) {
-  __shared__ double red[kVecThreads / 32];
-  double acc[1] = {0.0};
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    acc[0] += v[i] * v[i];
-  block_sum_k<1>(acc, red);
-  if (threadIdx.x == 0) partial[blockIdx.x] = acc[0];
-  if (!last_block_arrived(counter)) return;
-  if (threadIdx.x == 0) {
-    double t = 0;
-    for (int q = 0; q < (int)gridDim.x; ++q) t += __ldcg(partial + q);
-    *out = t;
-  }
+  norm2_body(v, n, partial, counter, out, blockIdx.x, gridDim.x);
 }
 
 __global__ void init_stop_kernel(int* stop, int value, int* nanflag) {
@@ -112,14 +126,14 @@ __global__ void init_stop_kernel(int* stop, int value, int* nanflag) {
 // bits, added to x in FP64.  G = 4 consecutive rows per thread (16-byte
 // loads) when the leading dimension and n allow it.
 template <typename T, int G>
-__global__ void __launch_bounds__(kVecThreads)
-update_kernel(double* __restrict__ x, const T* __restrict__ B, int64_t ldb, int64_t n, int d,
-              const double* __restrict__ y, const double* __restrict__ diag) {
+__device__ __forceinline__ void update_body(double* __restrict__ x, const T* __restrict__ B, int64_t ldb, int64_t n,
+                                            int d, const double* __restrict__ y, const double* __restrict__ diag,
+                                            int bid, int nb) {
   extern __shared__ double ys[];  // d doubles (+ 2d floats for the pair path)
   const int width = (int)diag[2];
   for (int j = threadIdx.x; j < width; j += blockDim.x) ys[j] = y[j];
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x * G;
-  const int64_t i_begin = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * G;
+  const int64_t stride = (int64_t)nb * blockDim.x * G;
+  const int64_t i_begin = ((int64_t)bid * blockDim.x + threadIdx.x) * G;
   if constexpr (!std::is_same<T, double>::value) {
     float* yh = (float*)(ys + d);
     float* yl = yh + d;
@@ -173,14 +187,76 @@ update_kernel(double* __restrict__ x, const T* __restrict__ B, int64_t ldb, int6
 }
 
 template <typename T, int G>
-static sk_status launch_update(double* x, const T* B, int64_t ldb, int64_t n, int d, const double* y,
-                               const double* diag, cudaStream_t st) {
-  const size_t smem = (size_t)d * sizeof(double) + (size_t)2 * d * sizeof(float);
+__global__ void __launch_bounds__(kVecThreads)
+update_kernel(double* __restrict__ x, const T* __restrict__ B, int64_t ldb, int64_t n, int d,
+              const double* __restrict__ y, const double* __restrict__ diag) {
+  update_body<T, G>(x, B, ldb, n, d, y, diag, blockIdx.x, gridDim.x);
+}
+
+// ---- grouped vector kernels (batched solver): map[blockIdx.x] = {slot, block} --
+__global__ void __launch_bounds__(kVecThreads)
+g_residual_kernel(const GJob* __restrict__ jobs, const int2* __restrict__ map) {
+  const int2 m = map[blockIdx.x];
+  const GJob& J = jobs[m.x];
+  residual_body(J.Ad, J.b, J.x, const_cast<double*>(J.bp.r), J.vpart, J.vcnt, const_cast<double*>(J.bp.rho2), m.y, J.vgrid);
+}
+
+__global__ void __launch_bounds__(kVecThreads)
+g_norm2_kernel(const GJob* __restrict__ jobs, const int2* __restrict__ map) {
+  const int2 m = map[blockIdx.x];
+  const GJob& J = jobs[m.x];
+  norm2_body(J.b, J.bp.n, J.vpart, J.vcnt + 1, J.bn2, m.y, J.vgrid);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kVecThreads)
+g_update_kernel(const GJob* __restrict__ jobs, const int2* __restrict__ map, int d) {
+  const int2 m = map[blockIdx.x];
+  const GJob& J = jobs[m.x];
+  const T* B = static_cast<const T*>(J.bp.B);
+  if (J.uvec) update_body<T, 4>(J.x, B, J.bp.ldb, J.bp.n, d, J.y, J.out + 1, m.y, J.ugrid);
+  else update_body<T, 1>(J.x, B, J.bp.ldb, J.bp.n, d, J.y, J.out + 1, m.y, J.ugrid);
+}
+
+int update_grid(int64_t n, int G) {
   int64_t g = (n + (int64_t)kVecThreads * G - 1) / ((int64_t)kVecThreads * G);
   if (g > 16 * num_sms()) g = 16 * num_sms();
   if (g < 1) g = 1;
+  return (int)g;
+}
+
+sk_status enqueue_vec_grouped(GroupedVec which, const GJob* jobs, const int2* map, int nmap, sk_dtype dt, int d,
+                              cudaStream_t st) {
+  if (nmap <= 0) return SK_OK;
+  if (which == GV_RESIDUAL) {
+    g_residual_kernel<<<nmap, kVecThreads, 0, st>>>(jobs, map);
+  } else if (which == GV_NORM_B) {
+    g_norm2_kernel<<<nmap, kVecThreads, 0, st>>>(jobs, map);
+  } else {
+    const size_t smem = (size_t)d * sizeof(double) + (size_t)2 * d * sizeof(float);
+    if (dt == SK_F64) {
+      SK_CUDA(cudaFuncSetAttribute(g_update_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, kDynSmemLimit));
+      g_update_kernel<double><<<nmap, kVecThreads, smem, st>>>(jobs, map, d);
+    } else if (dt == SK_F32) {
+      SK_CUDA(cudaFuncSetAttribute(g_update_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, kDynSmemLimit));
+      g_update_kernel<float><<<nmap, kVecThreads, smem, st>>>(jobs, map, d);
+    } else {
+      SK_CUDA(cudaFuncSetAttribute(g_update_kernel<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   kDynSmemLimit));
+      g_update_kernel<__nv_bfloat16><<<nmap, kVecThreads, smem, st>>>(jobs, map, d);
+    }
+  }
+  SK_CUDA(cudaGetLastError());
+  return SK_OK;
+}
+
+template <typename T, int G>
+static sk_status launch_update(double* x, const T* B, int64_t ldb, int64_t n, int d, const double* y,
+                               const double* diag, cudaStream_t st) {
+  const size_t smem = (size_t)d * sizeof(double) + (size_t)2 * d * sizeof(float);
+  const int g = update_grid(n, G);
   SK_CUDA(cudaFuncSetAttribute(update_kernel<T, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, kDynSmemLimit));
-  update_kernel<T, G><<<(int)g, kVecThreads, smem, st>>>(x, B, ldb, n, d, y, diag);
+  update_kernel<T, G><<<g, kVecThreads, smem, st>>>(x, B, ldb, n, d, y, diag);
   SK_CUDA(cudaGetLastError());
   return SK_OK;
 }
@@ -953,6 +1029,18 @@ extern "C" sk_status sgmres_solve_batched(int nsys, const sk_op* const* A, int n
   sk_opts o;
   if (opts) o = *opts;
   else sk_opts_default(&o);
+  bool grouped = false;
+  {
+    sk_opts ro;
+    resolve_opts(&o, &ro, d);
+    std::string why;
+    const bool ok = grouped_supported(ro, d, s, &why);
+    if (o.batch_mode == 1 && !ok) {
+      set_error("invalid argument: grouped batches (batch_mode = 1) need %s", why.c_str());
+      return SK_EINVAL;
+    }
+    grouped = o.batch_mode != 2 && ok;
+  }
   cudaStream_t st = (cudaStream_t)stream;
   int dev = 0;
   SK_CUDA(cudaGetDevice(&dev));
@@ -963,8 +1051,10 @@ extern "C" sk_status sgmres_solve_batched(int nsys, const sk_op* const* A, int n
       SK_TRY(make_view(A[i], &Af, st));
     }
   }
-  // Per-job graph instantiation serialises the host threads (hundreds of
-  // kernel nodes per cycle for each small job), so batched jobs launch eagerly.
+  if (grouped) return sgmres_batched_grouped(nsys, A, nrhs, b, x, d, k, s, tol, o, per_job, job_info, info, st);
+  // Worker threads: per-job graph instantiation serialises the host threads
+  // (hundreds of kernel nodes per cycle for each small job), so these jobs
+  // launch eagerly.
   o.use_graph = 0;
   int workers = o.batch_workers > 0 ? o.batch_workers : 16;
   if (workers > njobs) workers = njobs;

@@ -90,6 +90,18 @@ def test_invalid_arguments_rejected_on_host(native):
     o3.iter_chunk, o3.basis_kind, o3.cheb_c, o3.cheb_dx = 16, 1, 4.0, 4.0
     assert lib.sgmres_solve(h, dummy, dummy, 10, 2, 40, 1e-6, C.byref(o3), C.byref(info), None) == native.SK_EINVAL
     assert b"truncated-Arnoldi" in lib.sk_last_error()
+    # batched: grouped by default where the options allow it; batch_mode = 1
+    # with an SRHT sketch is refused on the host (FP64 basis: no device work)
+    o4 = native.SkOpts()
+    lib.sk_opts_default(C.byref(o4))
+    assert o4.batch_mode == 0 and o4.batch_elems == 0
+    o4.batch_mode, o4.sketch = 1, native.SK_SRHT
+    PA = (C.c_void_p * 1)(h)
+    PB = (C.c_void_p * 1)(dummy)
+    st = (C.c_int * 1)()
+    assert lib.sgmres_solve_batched(1, PA, 1, PB, PB, 10, 2, 40, 1e-6, C.byref(o4), st, None, C.byref(info),
+                                    None) == native.SK_EINVAL
+    assert b"grouped" in lib.sk_last_error() and b"sparse sign" in lib.sk_last_error()
     lib.sk_op_destroy(hT)
     lib.sk_op_destroy(h)
 

@@ -44,6 +44,47 @@ def test_operator_apply_matches_assembled_matrices(skg):
     assert np.allclose(opc.apply(torch.tensor(x, device="cuda")).cpu().numpy(), Av @ x, rtol=0, atol=1e-12)
 
 
+def _stencil_np(x2, coef):
+    # 5-point product on an ny x nx grid (row-major, zero outside), written
+    # with array shifts: y = cP x + cE x[:, i+1] + cW x[:, i-1] + cN x[j+1] + cS x[j-1]
+    cP, cE, cW, cN, cS = coef
+    y = cP * x2
+    y[:, :-1] += cE * x2[:, 1:]
+    y[:, 1:] += cW * x2[:, :-1]
+    y[:-1, :] += cN * x2[1:, :]
+    y[1:, :] += cS * x2[:-1, :]
+    return y
+
+
+def test_stencil_grid_index_math(skg):
+    # the kernels find a cell's grid row by multiplying with a precomputed
+    # reciprocal of nx; over grids up to 2^24 cells and widths that are
+    # prime, odd, a power of two, 1 and the whole row, every product matches
+    # the stencil evaluated on the 2-D array (FP64 and the FP32 basis path)
+    import torch
+    rng = np.random.default_rng(3)
+    coef = (4.1, -0.7, -1.3, -0.9, -1.1)
+    for nx, ny in ((4093, 4099), (1, 4097), (4096, 4096), (3, 1 << 20), (1 << 20, 3), (12345, 7)):
+        x2 = rng.standard_normal((ny, nx))
+        ref = _stencil_np(x2, coef).ravel()
+        op = skg.Op.stencil5(nx, ny, coef)
+        y = op.apply(torch.tensor(x2.ravel(), device="cuda")).cpu().numpy()
+        assert np.max(np.abs(y - ref)) <= 1e-12 * (1 + np.max(np.abs(ref))), (nx, ny)
+    # the basis passes (vector path when nx % 4 == 0, scalar otherwise):
+    # b_1 = (A b_0 - h b_0) / nu is A r up to the combination with r
+    for nx, ny in ((4093, 1031), (2048, 2049)):
+        r = rng.standard_normal(nx * ny)
+        out = skg.trunc_arnoldi_basis(skg.Op.stencil5(nx, ny, coef), torch.tensor(r, device="cuda"), 1, 1,
+                                      dtype=torch.float64)
+        B = out["B"].cpu().numpy()
+        H = out["Hbar"].cpu().numpy()
+        Ar = _stencil_np(r.reshape(ny, nx), coef).ravel()
+        rn = np.linalg.norm(r)
+        lhs = Ar / rn
+        rhs = H[0, 0] * B[:, 0] + H[1, 0] * B[:, 1]
+        assert np.linalg.norm(lhs - rhs) <= 1e-12 * np.linalg.norm(lhs), (nx, ny)
+
+
 @pytest.mark.parametrize("k", [1, 2, 4])
 def test_basis_fp64_matches_oracle(skg, k):
     import torch

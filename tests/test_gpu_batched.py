@@ -20,10 +20,16 @@ def _rel(A, f, x):
     return np.linalg.norm(f - A @ x) / np.linalg.norm(f)
 
 
-@pytest.mark.parametrize("dtype", ["f64", "f32"])
-def test_batched_equals_single_solves(skg, dtype):
-    # every job of the batch runs the same kernels as a single solve: the
-    # solutions agree bit for bit, and all reach tol
+@pytest.mark.parametrize("dtype,mode,elems", [("f64", "workers", 0), ("f32", "workers", 0),
+                                              ("f64", "grouped", 0), ("f32", "grouped", 0),
+                                              ("f32", "grouped", 5000)])
+def test_batched_equals_single_solves(skg, dtype, mode, elems):
+    # every job of the batch runs the same kernel bodies with the same block
+    # shapes as a single solve: the solutions agree bit for bit, and all
+    # reach tol.  Grouped: every launch serves all resident jobs (jobs of
+    # 24^2 .. 64^2 cells, vector and scalar stencil paths mixed); elems =
+    # 5000 admits one or two jobs at a time, so jobs start at different
+    # cycles of the batch.
     import torch
     tdt = torch.float64 if dtype == "f64" else torch.float32
     sides = [24, 64, 40, 33, 48]
@@ -37,14 +43,60 @@ def test_batched_equals_single_solves(skg, dtype):
         fs.append(f)
         bs.append([torch.tensor(v, device="cuda") for v in f])
     d, k, s, tol = 30, 2, 60, 1e-8
-    xs, stat, info = skg.sgmres_solve_batched(ops, bs, d, k, s, tol, basis=tdt, batch_workers=3)
+    xs, stat, info = skg.sgmres_solve_batched(ops, bs, d, k, s, tol, basis=tdt, batch_workers=3, batch_mode=mode,
+                                              batch_elems=elems)
     assert all(st == 0 for st in stat), stat
     for i in range(len(ops)):
         for r in range(2):
             x1, i1 = skg.sgmres_solve(ops[i], bs[i][r], d, k, s, tol, basis=tdt)
             assert torch.equal(x1, xs[i][r])
             assert _rel(mats[i], fs[i][r], xs[i][r].cpu().numpy()) <= tol
+            ji = info["jobs"][i * 2 + r]
+            assert ji["cycles"] == i1["cycles"] and ji["relres"] == i1["relres"]
+            assert ji["width"] == i1["width"] and ji["d_used"] == i1["d_used"]
     assert info["relres"] <= tol
+    if mode == "grouped" and elems == 0:
+        # all ten jobs resident: one launch per phase serves them all, far
+        # fewer launches than the jobs' (shared) launches summed
+        assert info["launches"] < 0.5 * sum(j["launches"] for j in info["jobs"])
+
+
+def test_grouped_edge_jobs(skg):
+    # one grouped batch holding: a zero right-hand side (x = 0 at once, no
+    # cycle), a job whose initial guess already meets tol (no cycle), jobs
+    # stopped by maxit (ENOCONV, the cycles' x kept), and a CSR operator next
+    # to stencils; each job's status, x and diagnostics equal a single solve's
+    import torch
+    N = 32
+    coef = synth.conv_diff_coef(N, 30.0)
+    A = operators.stencil5_matrix(N, N, coef).tocsr()
+    st_op = skg.Op.stencil5(N, N, coef)
+    csr_op = skg.Op.csr(torch.tensor(A.indptr, dtype=torch.int32, device="cuda"),
+                        torch.tensor(A.indices, dtype=torch.int32, device="cuda"),
+                        torch.tensor(A.data, dtype=torch.float64, device="cuda"))
+    f = torch.tensor(synth.randn(11, N * N), device="cuda")
+    xs_exact = torch.tensor(np.linalg.solve(A.toarray(), f.cpu().numpy()), device="cuda")
+    ops = [st_op, csr_op, st_op]
+    bs = [[torch.zeros(N * N, dtype=torch.float64, device="cuda"), f], [f, f], [f, f]]
+    x0s = [[torch.zeros_like(f), torch.zeros_like(f)], [xs_exact, torch.zeros_like(f)],
+           [torch.zeros_like(f), torch.zeros_like(f)]]
+    d, k, s, tol = 20, 2, 40, 1e-9
+    for basis in (torch.float64, torch.float32):
+        for maxit in (2, 10000):
+            xs, stat, info = skg.sgmres_solve_batched(ops, bs, d, k, s, tol, x0s=x0s, basis=basis, maxit=maxit,
+                                                      batch_mode="grouped")
+            for i in range(3):
+                for r in range(2):
+                    j = i * 2 + r
+                    x1, i1 = skg.sgmres_solve(ops[i], bs[i][r], d, k, s, tol, x0=x0s[i][r].clone(), basis=basis,
+                                              maxit=maxit)
+                    assert stat[j] == i1["status"], (i, r, maxit, stat[j], i1["status"])
+                    assert torch.equal(x1, xs[i][r]), (i, r, maxit)
+                    assert info["jobs"][j]["cycles"] == i1["cycles"]
+            assert stat[0] == 0 and info["jobs"][0]["cycles"] == 0 and torch.count_nonzero(xs[0][0]) == 0
+            assert stat[2] == 0 and info["jobs"][2]["cycles"] == 0
+            if maxit == 2:
+                assert stat[1] == 5 and info["jobs"][1]["cycles"] == 2
 
 
 def test_batched_workload_full(skg):
