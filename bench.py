@@ -32,7 +32,7 @@ METRIC = "sGMRES solves/s to 1e-6 rel. residual (chosen vs plain form); sketch G
 # DRAM bytes (read + write) of one Arnoldi step (its three launches), from
 # the ncu capture summarised in profiles/basis_dram_sgmres_scale_f32.md;
 # None for forms not captured (and to be reset whenever those kernels change).
-BASIS_TRAFFIC = {("f32", False): 25280256}
+BASIS_TRAFFIC = {("f32", False): 25287936}
 
 
 def _peaks():
@@ -353,17 +353,19 @@ def _bench_batched(skg, dev):
         g = torch.Generator(device=dev).manual_seed(synth.batch_rhs_seed(i, 0))
         bs.append([torch.randn(N * N, generator=g, dtype=torch.float64, device=dev) for _ in range(W["nrhs"])])
     kw = dict(zeta=W["zeta"], basis=torch.float32, maxit=500)
-    best, tun = skg.autotune_batch_workers(ops, bs, W["d"], W["k"], W["s"], W["tol"], candidates=(8, 16, 32),
-                                           sample=32, **kw)
+    best, tun = skg.autotune_batch(ops, bs, W["d"], W["k"], W["s"], W["tol"], candidates=(1 << 21, 1 << 22, 1 << 23),
+                                   sample=len(ops), **kw)
     torch.cuda.synchronize()
     t = time.perf_counter()
-    xs, stat, info = skg.sgmres_solve_batched(ops, bs, W["d"], W["k"], W["s"], W["tol"], batch_workers=best, **kw)
+    xs, stat, info = skg.sgmres_solve_batched(ops, bs, W["d"], W["k"], W["s"], W["tol"], batch_mode="grouped",
+                                              batch_elems=best, **kw)
     torch.cuda.synchronize()
     wall = max_over_ranks(time.perf_counter() - t, dev)
     conv = int(sum_over_ranks(sum(1 for st in stat if st == 0), dev))
     jobs = int(sum_over_ranks(len(stat), dev))
     return {"jobs": jobs, "converged_1e-6": conv, "wall_s": round(wall, 3), "ranks": ws,
-            "solves_per_s": round(conv / wall, 2), "workers": best,
+            "solves_per_s": round(conv / wall, 2), "mode": "grouped", "batch_elems": best,
+            "launches": info["launches"], "phases_ms": [round(v, 1) for v in info["ms"]],
             "autotune_s": {str(k): round(v, 3) for k, v in tun.items()}, "form": "FP32 basis, FP64 refinement",
             "maxit": 500}
 
@@ -506,10 +508,12 @@ def run_ours(args):
         "gpu_launches": int(sum(i["launches"] for i in infos)),
     }
     if not args.no_extras:
-        # the other forms of the same workload: SRHT sketch (FP32 basis) and BF16 basis
+        # the other forms of the same workload: SRHT sketch (FP32 basis), BF16
+        # basis, and iterative sGMRES (§5.2: chunks of 64 columns, early stop)
         forms = {}
         for fname, fkw in (("srht_f32", dict(kw, basis=torch.float32, sketch="srht")),
-                           ("bf16", dict(kw, basis=torch.bfloat16, sketch="sparse", maxit=400))):
+                           ("bf16", dict(kw, basis=torch.bfloat16, sketch="sparse", maxit=400)),
+                           ("iterative_f32", dict(kw, basis=torch.float32, sketch="sparse", iter_chunk=64))):
             x.zero_()
             skg.sgmres_solve(A, b, W["d"], W["k"], W["s"], W["tol"], x0=x, **fkw)
             barrier()
@@ -520,7 +524,7 @@ def run_ours(args):
             barrier()
             fms = e0.elapsed_time(e1)
             forms[fname] = {"solves_per_s": round(1000.0 / fms, 3), "ms": round(fms, 2), "cycles": finfo["cycles"],
-                            "relres": finfo["relres"], "status": finfo["status"]}
+                            "relres": finfo["relres"], "status": finfo["status"], "matvecs": finfo["matvecs"]}
         out["forms"] = forms
         out["sketch_apply"] = _bench_sketch(skg, dev, peak)
         out["srr"] = _bench_srr(skg, dev)
@@ -567,7 +571,7 @@ def run_case(args):
         for _ in range(2):
             x, info = skg.sgmres_solve(A, b, W["d"], W["k"], W["s"], 1e-300, maxit=1, **kw)
         torch.cuda.synchronize()
-        print("case cycle ms %.3f launches %d" % (info["ms"], info["launches"]))
+        print("case cycle ms %.3f launches %d" % (info["ms"][5], info["launches"]))
     else:
         g = torch.Generator(device=dev).manual_seed(0)
         B = torch.randn((args.cols, args.n), generator=g, device=dev, dtype=torch.float32).t()

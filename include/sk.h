@@ -225,7 +225,7 @@ typedef struct {
                               storage, s <= 640, iter_chunk = 0) */
   long long batch_elems;   /* grouped batches: jobs are admitted, largest first, while the resident
                               systems' sizes n sum to at most this (at least one job is resident);
-                              0 = 2^23 */
+                              0 = 2^22 */
 } sk_opts;
 
 void sk_opts_default(sk_opts* o);

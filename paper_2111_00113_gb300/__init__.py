@@ -217,7 +217,7 @@ def make_opts(basis=torch.float64, sketch="sparse", zeta=0, seed=7, stab_tol=0.0
     another instead of overlapping the sketch and QR of finished basis
     blocks with the basis passes.  batch_mode ("auto", "grouped",
     "workers") and batch_elems (resident elements of a grouped batch, 0 =
-    2^23) shape sgmres_solve_batched."""
+    2^22) shape sgmres_solve_batched."""
     o = N.SkOpts()
     N.lib.sk_opts_default(C.byref(o))
     o.sketch = _KIND[sketch]
@@ -327,7 +327,7 @@ def _batch_sample(ops, bs, sample):
     return [ops[i] for i in pick], [bs[i][:1] for i in pick]
 
 
-def autotune_batch(ops, bs, d, k, s, tol, candidates=(1 << 21, 1 << 22, 1 << 23), sample=96, **opts):
+def autotune_batch(ops, bs, d, k, s, tol, candidates=(1 << 21, 1 << 22, 1 << 23), sample=256, **opts):
     """Pick the grouped batch's resident-element budget (batch_elems) by
     timing a sample of the jobs (spread evenly over the size range, one
     right-hand side each).  Returns (best, {batch_elems: seconds})."""

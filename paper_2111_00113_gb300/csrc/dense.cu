@@ -592,7 +592,8 @@ static constexpr int kCheckThreads = 1024;
 
 __global__ void __launch_bounds__(kCheckThreads)
 prefix_check_kernel(const double* __restrict__ z, const double* __restrict__ rdiag, const int* __restrict__ stop,
-                    int s, int c0, int c1, double tau, double stab_tol, int* __restrict__ out) {
+                    int s, int c0, int c1, const double* __restrict__ tau_p, double stab_tol, int* __restrict__ out) {
+  const double tau = *tau_p;
   __shared__ double red[kCheckThreads / 32][2];
   __shared__ double wsum[kCheckThreads / 32];
   __shared__ long long wmx[kCheckThreads / 32], wmn[kCheckThreads / 32];
@@ -664,7 +665,7 @@ prefix_check_kernel(const double* __restrict__ z, const double* __restrict__ rdi
 }
 
 sk_status enqueue_prefix_check(const double* z, const double* rdiag, const int* stop, int s, int c0, int c1,
-                               double tau, double stab_tol, int* out, cudaStream_t st) {
+                               const double* tau, double stab_tol, int* out, cudaStream_t st) {
   if (c0 < 0 || c1 <= c0 || c1 - c0 > kCheckThreads || c1 > s) {
     set_error("prefix_check: bad column range");
     return SK_EINVAL;

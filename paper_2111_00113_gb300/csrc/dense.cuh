@@ -26,8 +26,10 @@ sk_status enqueue_ls_solve_z(const double* Aug, const double* rdiag, const doubl
                              double* y, double* diag, cudaStream_t st, const JobSlab& js = JobSlab(), int nj = 1);
 sk_status enqueue_qr_append(double* Aug, int s, int c0, int c1, int zc, double* rdiag, double* tau, double* Tws,
                             long long* launches, cudaStream_t st);
+// tau: device scalar (read when the check runs, so a captured chunk serves
+// every cycle)
 sk_status enqueue_prefix_check(const double* z, const double* rdiag, const int* stop, int s, int c0, int c1,
-                               double tau, double stab_tol, int* out, cudaStream_t st);
+                               const double* tau, double stab_tol, int* out, cudaStream_t st);
 
 // Eigenpairs of a d x d FP64 matrix (eig.cu).  M is overwritten by its
 // Hessenberg form and reflectors; tau needs 2d entries.  Yre/Yim (d x nev)

@@ -156,7 +156,7 @@ sk_status sgmres_batched_grouped(int nsys, const sk_op* const* A, int nrhs, cons
   SK_TRY(check_passes(o));
   const sk_dtype dt = o.basis;
   const int njobs = nsys * nrhs;
-  const long long cap = o.batch_elems > 0 ? o.batch_elems : (1ll << 23);
+  const long long cap = o.batch_elems > 0 ? o.batch_elems : (1ll << 22);
   auto job_n = [&](int q) { return A[q / nrhs]->n; };
   std::vector<int> order(njobs);
   for (int q = 0; q < njobs; ++q) order[q] = q;

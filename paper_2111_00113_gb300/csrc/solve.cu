@@ -488,8 +488,15 @@ struct SolveState {
   double* vec_part;
   unsigned* vec_cnt;
   double* out;      // device: [rho2, rhat, kappa, width]
-  double* h_out;    // pinned host copy (+ one int: the persistent kernel's error word)
+  double* h_out;    // pinned host copy, 8 doubles: [0..3] the cycle's scalars, [4] the persistent
+                    // kernel's error word, [5] the iterative cycle's tau, [6..7] its chunk check
   int* h_err;
+  // iterative cycles: one captured graph per chunk position (made on first
+  // use, replayed every cycle), its kernel count, the device tau it reads
+  cudaGraphExec_t* ig;
+  long long* ig_kernels;
+  int n_ig;
+  double* tau_dev;
   // pipelined cycle: side stream for the sketch and QR of finished basis
   // blocks, its fork/join events, one event per block, the basis priority
   bool pipe;
@@ -634,6 +641,8 @@ static sk_status enqueue_cycle_pipelined(SolveState& S, const sk_op* A, const Op
 // that one answer per chunk; the cycle ends there, or on the kappa estimate,
 // a breakdown or j = d, and the solve and the update use that prefix.
 // *used = the prefix solved, *built = the steps the basis ran.
+static long long count_kernel_nodes(cudaGraph_t g);
+
 static sk_status run_iterative_cycle(SolveState& S, const sk_op* A, const OpView<double>& Av, const double* b,
                                      double* x, double tau_rel, int* chk, cudaStream_t st, cudaEvent_t* ev,
                                      int* used, int* built, long long* launches) {
@@ -642,6 +651,8 @@ static sk_status run_iterative_cycle(SolveState& S, const sk_op* A, const OpView
   BasisParams& bp = S.bb.bp;
   long long nl = 0;
   SK_TRY(mark(ev, EV_START, st, false));
+  S.h_out[5] = tau_rel;  // the captured checks read it from the device
+  SK_CUDA(cudaMemcpyAsync(S.tau_dev, S.h_out + 5, sizeof(double), cudaMemcpyHostToDevice, st));
   SK_TRY(S.sketch.apply(S.r, S.n, 1, SK_F64, S.g, S.ws_r, st, false));
   nl += 2;
   SK_TRY(mark(ev, EV_G, st, false));
@@ -651,26 +662,45 @@ static sk_status run_iterative_cycle(SolveState& S, const sk_op* A, const OpView
   double* z = S.Aug + (size_t)d * s;
   SK_CUDA(cudaMemcpyAsync(z, S.g, sizeof(double) * s, cudaMemcpyDeviceToDevice, st));
   int dp = d, c1 = 0;
-  for (int c0 = 0; c0 < d; c0 = c1) {
+  int* h = reinterpret_cast<int*>(S.h_out + 6);
+  for (int ci = 0, c0 = 0; c0 < d; ++ci, c0 = c1) {
     c1 = c0 + chunk < d ? c0 + chunk : d;
-    bp.j_begin = c0;
-    bp.j_end = c1;
-    const sk_status bs = enqueue_basis(bp, A, st);
-    bp.j_begin = bp.j_end = 0;
-    SK_TRY(bs);
-    nl += (long long)(c1 - c0) * (S.o.cgs_passes + 1) + (c0 == 0 ? 1 : 0);
-    // the chunk's new basis columns: b_{c0+1} .. b_{c1} (0-based), and b_0 first
-    const int s0 = c0 == 0 ? 0 : c0 + 1;
-    SK_TRY(S.sketch.apply((const unsigned char*)bp.B + (size_t)s0 * bp.ldb * esz, bp.ldb, c1 + 1 - s0, S.o.basis,
-                          S.SB + (size_t)s0 * s, S.ws_B, st, true));
-    nl += 2;
-    SK_TRY(enqueue_hbar_product_cols(S.SB, bp.Hbar, s, d, S.bb.hbar_k(), bp.stop, c0, c1, S.Aug, st));
-    ++nl;
-    SK_TRY(enqueue_qr_append(S.Aug, s, c0, c1, d, S.rdiag, S.tau, S.Tws, &nl, st));
-    SK_TRY(enqueue_prefix_check(z, S.rdiag, bp.stop, s, c0, c1, tau_rel, S.o.stab_tol, chk, st));
-    ++nl;
-    int h[2] = {0, 0};
-    SK_CUDA(cudaMemcpyAsync(h, chk, sizeof(h), cudaMemcpyDeviceToHost, st));
+    if (!S.ig[ci]) {
+      // capture the chunk once: its basis steps, the sketch of its new
+      // columns, their columns of C, the QR append, the stop test and the
+      // copy of the test's word to the host
+      SK_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+      auto body = [&]() -> sk_status {
+        bp.j_begin = c0;
+        bp.j_end = c1;
+        const sk_status bs = enqueue_basis(bp, A, st);
+        bp.j_begin = bp.j_end = 0;
+        SK_TRY(bs);
+        // the chunk's new basis columns: b_{c0+1} .. b_{c1} (0-based), and b_0 first
+        const int s0 = c0 == 0 ? 0 : c0 + 1;
+        SK_TRY(S.sketch.apply((const unsigned char*)bp.B + (size_t)s0 * bp.ldb * esz, bp.ldb, c1 + 1 - s0,
+                              S.o.basis, S.SB + (size_t)s0 * s, S.ws_B, st, true));
+        SK_TRY(enqueue_hbar_product_cols(S.SB, bp.Hbar, s, d, S.bb.hbar_k(), bp.stop, c0, c1, S.Aug, st));
+        SK_TRY(enqueue_qr_append(S.Aug, s, c0, c1, d, S.rdiag, S.tau, S.Tws, nullptr, st));
+        SK_TRY(enqueue_prefix_check(z, S.rdiag, bp.stop, s, c0, c1, S.tau_dev, S.o.stab_tol, chk, st));
+        SK_CUDA(cudaMemcpyAsync(h, chk, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+        return SK_OK;
+      };
+      const sk_status bs = body();
+      cudaGraph_t g = nullptr;
+      const cudaError_t ce = cudaStreamEndCapture(st, &g);
+      if (bs != SK_OK) {
+        if (g) cudaGraphDestroy(g);
+        return bs;
+      }
+      if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamEndCapture");
+      const cudaError_t ie = cudaGraphInstantiate(&S.ig[ci], g, 0);
+      S.ig_kernels[ci] = count_kernel_nodes(g);
+      cudaGraphDestroy(g);
+      if (ie != cudaSuccess) return cuda_fail(ie, "cudaGraphInstantiate");
+    }
+    SK_CUDA(cudaGraphLaunch(S.ig[ci], st));
+    nl += S.ig_kernels[ci];
     SK_CUDA(cudaStreamSynchronize(st));
     if (h[0] > 0) {
       dp = h[0];
@@ -806,7 +836,26 @@ static sk_status sgmres_impl(const sk_op* A, const double* b, double* x, int d, 
     SK_TRY(sc.alloc(&S.ws_B, wsb));
   }
   int* chk = nullptr;
-  if (iter) SK_TRY(sc.alloc(&chk, 2));
+  if (iter) {
+    SK_TRY(sc.alloc(&chk, 2));
+    SK_TRY(sc.alloc(&S.tau_dev, 1));
+    S.n_ig = (d + S.o.iter_chunk - 1) / S.o.iter_chunk;
+    S.ig = new cudaGraphExec_t[S.n_ig];
+    S.ig_kernels = new long long[S.n_ig];
+    for (int q = 0; q < S.n_ig; ++q) {
+      S.ig[q] = nullptr;
+      S.ig_kernels[q] = 0;
+    }
+  }
+  struct IterGraphsFree {
+    SolveState* S;
+    ~IterGraphsFree() {
+      for (int q = 0; q < S->n_ig; ++q)
+        if (S->ig[q]) cudaGraphExecDestroy(S->ig[q]);
+      delete[] S->ig;
+      delete[] S->ig_kernels;
+    }
+  } igf{&S};
   SK_TRY(sc.alloc(&S.vec_part, vec_grid(S.n)));
   SK_TRY(sc.alloc(&S.vec_cnt, 2));
   SK_CUDA(cudaMemsetAsync(S.vec_cnt, 0, 2 * sizeof(unsigned), st));
@@ -814,7 +863,7 @@ static sk_status sgmres_impl(const sk_op* A, const double* b, double* x, int d, 
   SK_CUDA(cudaMemsetAsync(S.out, 0, 4 * sizeof(double), st));
   // pinned landing buffer for the per-cycle scalars (the caller's, or our own)
   if (h_pinned) S.h_out = h_pinned;
-  else SK_CUDA(cudaMallocHost((void**)&S.h_out, 5 * sizeof(double)));
+  else SK_CUDA(cudaMallocHost((void**)&S.h_out, 8 * sizeof(double)));
   S.h_err = (int*)(S.h_out + 4);
   *S.h_err = 0;
   struct HostFree { double* p; ~HostFree() { if (p) cudaFreeHost(p); } } hf{h_pinned ? nullptr : S.h_out};
@@ -869,15 +918,15 @@ static sk_status sgmres_impl(const sk_op* A, const double* b, double* x, int d, 
   long long kernels_per_cycle = 0;
   long long iter_launches = 0;
   long long iter_matvecs = 0;
+  // the legacy default stream cannot be captured: use a private stream then
+  if ((iter || S.o.use_graph) && (st == nullptr || st == cudaStreamLegacy)) {
+    SK_CUDA(cudaStreamCreateWithFlags(&own, cudaStreamNonBlocking));
+    cap = own;
+    SK_CUDA(cudaStreamSynchronize(st));
+  }
   if (iter) {
     // launches are counted per cycle by run_iterative_cycle
   } else if (S.o.use_graph) {
-    // the legacy default stream cannot be captured: use a private stream then
-    if (st == nullptr || st == cudaStreamLegacy) {
-      SK_CUDA(cudaStreamCreateWithFlags(&own, cudaStreamNonBlocking));
-      cap = own;
-      SK_CUDA(cudaStreamSynchronize(st));
-    }
     SK_CUDA(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
     sk_status cs = S.pipe ? enqueue_cycle_pipelined(S, A, Av, b, x, cap, ev, true)
                           : enqueue_cycle(S, A, Av, b, x, cap, ev, true);
