@@ -392,11 +392,16 @@ def run_ours(args):
     kw = dict(zeta=W["zeta"], seed=7, basis=form, sketch=args.sketch, persistent=args.persistent,
               pipeline=not args.no_pipeline)
     x = torch.zeros_like(b)
+    # a reusable solver per form (sketch plan, buffers and cycle graph built
+    # once, outside the timed region, as a server solving many right-hand
+    # sides keeps them); every timed solve runs all its cycles
+    plans = {}
 
     def solve(basis=form):
+        if basis not in plans:
+            plans[basis] = skg.SgmresPlan(A, W["d"], W["k"], W["s"], **dict(kw, basis=basis))
         x.zero_()
-        xx, info = skg.sgmres_solve(A, b, W["d"], W["k"], W["s"], W["tol"], x0=x, **dict(kw, basis=basis))
-        return xx, info
+        return plans[basis].solve(b, W["tol"], x0=x)
 
     for _ in range(args.warmup):
         xx, info = solve()
@@ -450,7 +455,7 @@ def run_ours(args):
     for _ in range(args.steps):
         db.copy_(hb, non_blocking=True)
         x.zero_()
-        xx, info = skg.sgmres_solve(A, db, W["d"], W["k"], W["s"], W["tol"], x0=x, **kw)
+        xx, info = plans[form].solve(db, W["tol"], x0=x)
         hx.copy_(xx, non_blocking=True)
     e1.record(stream)
     barrier()
@@ -458,6 +463,17 @@ def run_ours(args):
     e2e = {"value": job_rate(ws, args.steps, e2e_ms), "unit": "solves/s",
            "h2d_bytes_per_step": hb.numel() * hb.element_size(),
            "d2h_bytes_per_step": hx.numel() * hx.element_size()}
+    # one-shot calls (sgmres_solve: plan build, allocations and graph capture
+    # inside every call)
+    barrier()
+    e0.record(stream)
+    for _ in range(2):
+        x.zero_()
+        skg.sgmres_solve(A, b, W["d"], W["k"], W["s"], W["tol"], x0=x, **kw)
+    e1.record(stream)
+    barrier()
+    os_ms = max_over_ranks(e0.elapsed_time(e1), dev) / 2
+    one_shot = {"solves_per_s": round(job_rate(ws, 1, os_ms), 3), "ms": round(os_ms, 2)}
 
     last = infos[-1]
     cycles = last["cycles"]
@@ -497,6 +513,8 @@ def run_ours(args):
                    "cycle": "sequential" if (args.no_pipeline or args.persistent) else
                             "pipelined (block sketch + QR panels overlapped with the basis passes)",
                    "l2": "inputs larger than L2 (basis %.2f GB per cycle)" % (esz * n * (d + 1) / 1e9),
+                   "api": "SgmresPlan.solve (sgmres_plan_solve: the plan built once before the timed "
+                          "region; each solve copies b and x0 in, runs every cycle, copies x out)",
                    "parallelism": "replicas" if ws > 1 else "single GPU"},
         "converged": ok, "cycles": cycles, "relres": last["relres"],
         "phases_ms_per_step": dict(zip(["residual", "basis", "sketch", "small_solve", "update", "total"], phases)),
@@ -504,6 +522,7 @@ def run_ours(args):
         "plain": plain,
         "roofline": roofline,
         "e2e": e2e,
+        "one_shot": one_shot,
         "clocks": clk,
         "gpu_launches": int(sum(i["launches"] for i in infos)),
     }

@@ -279,6 +279,24 @@ sk_status trunc_arnoldi_basis(const sk_op* A, const double* r0, int d, int k, sk
 sk_status sgmres_solve(const sk_op* A, const double* b, double* x, int d, int k, int s, double tol,
                        const sk_opts* opts, sk_info* info, void* stream);
 
+/* Reusable solver for one operator and shape (not in the paper): the
+ * buffers, the sketch plan, the side streams and the captured cycle graph of
+ * sgmres_solve, built once by sgmres_plan_create and reused by every
+ * sgmres_plan_solve (which copies b and the initial guess x into the plan's
+ * own vectors, runs the cycles, and copies the iterate back into x whatever
+ * the status).  Each solve computes exactly what sgmres_solve computes on the
+ * same arguments; it skips the per-call setup (plan build, allocations, graph
+ * capture).  A must outlive the plan; one solve at a time per plan; the
+ * plan's device memory is released by sgmres_plan_destroy, which first waits
+ * for its streams.  Errors: as sgmres_solve; the create call validates d, k,
+ * s like sgmres_solve (SK_EINVAL) and returns SK_ENOMEM if the buffers do not
+ * fit. */
+typedef struct sk_solver sk_solver;
+sk_status sgmres_plan_create(const sk_op* A, int d, int k, int s, const sk_opts* opts, sk_solver** plan,
+                             void* stream);
+sk_status sgmres_plan_solve(sk_solver* plan, const double* b, double* x, double tol, sk_info* info, void* stream);
+void sgmres_plan_destroy(sk_solver* plan);
+
 /* Device workspace in bytes that sgmres_solve(A, ., ., d, k, s, ., opts)
  * allocates (stream-ordered, released before it returns), for callers that
  * budget memory: the basis n x (d+1) in the basis precision, the Arnoldi

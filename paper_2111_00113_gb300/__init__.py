@@ -290,6 +290,39 @@ def sgmres_solve(A, b, d, k, s, tol, x0=None, raise_on_noconv=False, **opts):
     return x, out
 
 
+class SgmresPlan:
+    """A reusable restarted-sGMRES solver for one operator and shape: the
+    sketch plan, buffers and captured cycle graph are built once; each
+    solve(b) computes what sgmres_solve(A, b, d, k, s, tol) computes, without
+    the per-call setup.  The operator must outlive the plan."""
+
+    def __init__(self, A, d, k, s, **opts):
+        self.A, self.n = A, A.n
+        self._h = C.c_void_p()
+        o = make_opts(**opts)
+        N.check(N.lib.sgmres_plan_create(A._h, d, k, s, C.byref(o), C.byref(self._h), _stream()))
+
+    def solve(self, b, tol, x0=None, raise_on_noconv=False):
+        b = _dev_f64(b, self.n)
+        x = torch.zeros_like(b) if x0 is None else _dev_f64(x0, self.n).clone()
+        info = N.SkInfo()
+        allow = (N.SK_OK,) if raise_on_noconv else (N.SK_OK, N.SK_ENOCONV)
+        st = N.check(N.lib.sgmres_plan_solve(self._h, _ptr(b), _ptr(x), float(tol), C.byref(info), _stream()),
+                     allow=allow)
+        out = info.as_dict()
+        out["status"] = st
+        return x, out
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            try:
+                N.lib.sgmres_plan_destroy(h)
+            except Exception:
+                pass
+            self._h = None
+
+
 def sgmres_solve_batched(ops, bs, d, k, s, tol, x0s=None, **opts):
     """Batched restarted sGMRES over independent jobs.
 

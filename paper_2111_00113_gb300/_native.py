@@ -19,6 +19,7 @@ EXPORTED = [
     "sk_op_destroy", "sketch_apply", "sketch_apply_noalloc", "sk_opts_default", "trunc_arnoldi_basis", "sgmres_solve", "srr_eigs",
     "sk_last_error", "sk_status_string", "sk_op_param_grad", "sgmres_solve_batched", "srr_basis", "srr_restarted",
     "sk_workspace_bytes", "sk_sketch_plan_create", "sk_sketch_plan_apply", "sk_sketch_plan_destroy",
+    "sgmres_plan_create", "sgmres_plan_solve", "sgmres_plan_destroy",
 ]
 
 
@@ -86,6 +87,9 @@ def _load():
         "sk_sketch_plan_create": (st, [C.POINTER(SkSketch), C.POINTER(P), P]),
         "sk_sketch_plan_apply": (st, [P, P, I64, I, I, P, P]),
         "sk_sketch_plan_destroy": (None, [P]),
+        "sgmres_plan_create": (st, [P, I, I, I, C.POINTER(SkOpts), C.POINTER(P), P]),
+        "sgmres_plan_solve": (st, [P, P, P, D, C.POINTER(SkInfo), P]),
+        "sgmres_plan_destroy": (None, [P]),
         "sk_last_error": (C.c_char_p, []),
         "sk_status_string": (C.c_char_p, [I]),
     }

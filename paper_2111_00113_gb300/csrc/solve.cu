@@ -747,16 +747,76 @@ static long long count_kernel_nodes(cudaGraph_t g) {
 
 }  // namespace sk
 
-// Restarted sGMRES after argument validation (also the per-job body of the
-// batched driver).
-static sk_status sgmres_impl(const sk_op* A, const double* b, double* x, int d, int k, int s, double tol,
-                             const sk_opts* opts, sk_info* info, cudaStream_t st, double* h_pinned = nullptr) {
+namespace sk {
+
+// One restarted-sGMRES configuration on one operator: its buffers, sketch
+// plan, side streams and (once captured) the cycle's graph.  sgmres_solve
+// builds one per call; sgmres_plan_create keeps one across calls.
+struct Solver {
   SolveState S;
-  std::memset(&S, 0, sizeof(S));
+  const sk_op* A = nullptr;
+  OpView<double> Av;
+  Scratch* sc = nullptr;       // the state's buffers, freed on the creation stream
+  cudaStream_t st0 = nullptr;  // creation stream
+  cudaStream_t last = nullptr; // stream of the last solve
+  bool iter = false;
+  int* chk = nullptr;
+  double* bn2d = nullptr;
+  bool own_pinned = false;
+  long long setup_launches = 0;  // plan build and FP32 operator copies
+  cudaGraphExec_t gexec = nullptr;
+  long long kernels_per_cycle = 0;
+  const double* gb = nullptr;  // the b and x the captured cycle reads and writes
+  double* gx = nullptr;
+  cudaStream_t own = nullptr;  // capturable stream when the caller passes the legacy stream
+  cudaEvent_t ev[EV_COUNT] = {};
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  double* hb = nullptr;        // plan handles: private b and x (the graph's operands)
+  double* hx = nullptr;
+
+  Solver() { std::memset(&S, 0, sizeof(S)); }
+  ~Solver();
+  sk_status setup(const sk_op* A_, int d, int k, int s, const sk_opts* opts, cudaStream_t st, double* h_pinned);
+  sk_status capture(const double* b, double* x, cudaStream_t cap);
+  sk_status run(const double* b, double* x, double tol, sk_info* info, cudaStream_t st);
+};
+
+Solver::~Solver() {
+  if (last) cudaStreamSynchronize(last);
+  if (st0) cudaStreamSynchronize(st0);
+  if (gexec) cudaGraphExecDestroy(gexec);
+  for (int q = 0; q < EV_COUNT; ++q)
+    if (ev[q]) cudaEventDestroy(ev[q]);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (own) cudaStreamDestroy(own);
+  if (S.side) cudaStreamDestroy(S.side);
+  if (S.qrs) cudaStreamDestroy(S.qrs);
+  if (S.fork) cudaEventDestroy(S.fork);
+  if (S.join) cudaEventDestroy(S.join);
+  const int nb = (S.d + 1 + kQrNb - 1) / kQrNb;
+  for (cudaEvent_t* e : {S.blk, S.skd}) {
+    if (!e) continue;
+    for (int t = 0; t < nb; ++t)
+      if (e[t]) cudaEventDestroy(e[t]);
+    delete[] e;
+  }
+  for (int q = 0; q < S.n_ig; ++q)
+    if (S.ig[q]) cudaGraphExecDestroy(S.ig[q]);
+  delete[] S.ig;
+  delete[] S.ig_kernels;
+  if (own_pinned && S.h_out) cudaFreeHost(S.h_out);
+  delete sc;  // stream-ordered frees on st0, after the synchronisations above
+}
+
+sk_status Solver::setup(const sk_op* A_, int d, int k, int s, const sk_opts* opts, cudaStream_t st,
+                        double* h_pinned) {
+  A = A_;
+  st0 = st;
   resolve_opts(opts, &S.o, d);
   SK_CHECK_ARG(S.o.basis == SK_F64 || S.o.basis == SK_F32 || S.o.basis == SK_BF16, "basis dtype");
   SK_TRY(check_passes(S.o));
-  const bool iter = S.o.iter_chunk != 0;
+  iter = S.o.iter_chunk != 0;
   if (iter) {
     SK_CHECK_ARG(S.o.iter_chunk > 0 && S.o.iter_chunk % kQrNb == 0 && S.o.iter_chunk <= 1024,
                  "iter_chunk must be a positive multiple of 16, at most 1024");
@@ -768,28 +828,12 @@ static sk_status sgmres_impl(const sk_op* A, const double* b, double* x, int d, 
   S.d = d;
   S.k = k;
   S.s = s;
-  if (info) std::memset(info, 0, sizeof(*info));
-  Scratch sc(st);
-  SK_TRY(S.bb.alloc(S.n, d, k, S.o.basis, S.o.cgs_passes, S.o.breakdown, sc, nullptr, A, S.o.persistent != 0));
-  SK_TRY(S.bb.set_kind(S.o, sc));
+  sc = new Scratch(st);
+  Scratch& scr = *sc;
+  SK_TRY(S.bb.alloc(S.n, d, k, S.o.basis, S.o.cgs_passes, S.o.breakdown, scr, nullptr, A, S.o.persistent != 0));
+  SK_TRY(S.bb.set_kind(S.o, scr));
   // the pipelined cycle: captured truncated-Arnoldi cycles of the 3-launch basis
   S.pipe = S.o.pipeline != 0 && S.o.use_graph && !iter && !S.bb.cheb() && !S.bb.persistent;
-  struct PipeFree {
-    SolveState* S;
-    ~PipeFree() {
-      if (S->side) cudaStreamDestroy(S->side);
-      if (S->qrs) cudaStreamDestroy(S->qrs);
-      if (S->fork) cudaEventDestroy(S->fork);
-      if (S->join) cudaEventDestroy(S->join);
-      const int nb = (S->d + 1 + kQrNb - 1) / kQrNb;
-      for (cudaEvent_t* e : {S->blk, S->skd}) {
-        if (!e) continue;
-        for (int t = 0; t < nb; ++t)
-          if (e[t]) cudaEventDestroy(e[t]);
-        delete[] e;
-      }
-    }
-  } pf{&S};
   if (S.pipe) {
     int least = 0, greatest = 0;
     SK_CUDA(cudaDeviceGetStreamPriorityRange(&least, &greatest));
@@ -813,17 +857,17 @@ static sk_status sgmres_impl(const sk_op* A, const double* b, double* x, int d, 
   sks.s = s;
   sks.zeta = S.o.zeta;
   sks.seed = S.o.seed;
-  SK_TRY(S.sketch.create(sks, sc, st));
-  SK_TRY(sc.alloc(&S.r, S.n));
+  SK_TRY(S.sketch.create(sks, scr, st));
+  SK_TRY(scr.alloc(&S.r, S.n));
   S.bb.bp.r = S.r;
-  SK_TRY(sc.alloc(&S.g, s));
-  SK_TRY(sc.alloc(&S.SB, (size_t)s * (d + 1)));
-  SK_TRY(sc.alloc(&S.Aug, (size_t)s * (d + 1)));
-  SK_TRY(sc.alloc(&S.rdiag, d));
-  SK_TRY(sc.alloc(&S.tau, d));
-  SK_TRY(sc.alloc(&S.Tws, (size_t)((d + kQrNb - 1) / kQrNb) * kQrNb * kQrNb));
-  SK_TRY(sc.alloc(&S.y, d));
-  SK_TRY(sc.alloc(&S.ws_r, S.sketch.ws(1, SK_F64, false)));
+  SK_TRY(scr.alloc(&S.g, s));
+  SK_TRY(scr.alloc(&S.SB, (size_t)s * (d + 1)));
+  SK_TRY(scr.alloc(&S.Aug, (size_t)s * (d + 1)));
+  SK_TRY(scr.alloc(&S.rdiag, d));
+  SK_TRY(scr.alloc(&S.tau, d));
+  SK_TRY(scr.alloc(&S.Tws, (size_t)((d + kQrNb - 1) / kQrNb) * kQrNb * kQrNb));
+  SK_TRY(scr.alloc(&S.y, d));
+  SK_TRY(scr.alloc(&S.ws_r, S.sketch.ws(1, SK_F64, false)));
   {
     // iterative cycles sketch 1..iter_chunk+1 columns at a time: room for
     // the largest of those shapes too
@@ -832,13 +876,11 @@ static sk_status sgmres_impl(const sk_op* A, const double* b, double* x, int d, 
       const size_t w = S.sketch.ws(c, S.o.basis, true);
       if (w > wsb) wsb = w;
     }
-
-    SK_TRY(sc.alloc(&S.ws_B, wsb));
+    SK_TRY(scr.alloc(&S.ws_B, wsb));
   }
-  int* chk = nullptr;
   if (iter) {
-    SK_TRY(sc.alloc(&chk, 2));
-    SK_TRY(sc.alloc(&S.tau_dev, 1));
+    SK_TRY(scr.alloc(&chk, 2));
+    SK_TRY(scr.alloc(&S.tau_dev, 1));
     S.n_ig = (d + S.o.iter_chunk - 1) / S.o.iter_chunk;
     S.ig = new cudaGraphExec_t[S.n_ig];
     S.ig_kernels = new long long[S.n_ig];
@@ -847,55 +889,98 @@ static sk_status sgmres_impl(const sk_op* A, const double* b, double* x, int d, 
       S.ig_kernels[q] = 0;
     }
   }
-  struct IterGraphsFree {
-    SolveState* S;
-    ~IterGraphsFree() {
-      for (int q = 0; q < S->n_ig; ++q)
-        if (S->ig[q]) cudaGraphExecDestroy(S->ig[q]);
-      delete[] S->ig;
-      delete[] S->ig_kernels;
-    }
-  } igf{&S};
-  SK_TRY(sc.alloc(&S.vec_part, vec_grid(S.n)));
-  SK_TRY(sc.alloc(&S.vec_cnt, 2));
+  SK_TRY(scr.alloc(&S.vec_part, vec_grid(S.n)));
+  SK_TRY(scr.alloc(&S.vec_cnt, 2));
   SK_CUDA(cudaMemsetAsync(S.vec_cnt, 0, 2 * sizeof(unsigned), st));
-  SK_TRY(sc.alloc(&S.out, 4));
+  SK_TRY(scr.alloc(&S.out, 4));
   SK_CUDA(cudaMemsetAsync(S.out, 0, 4 * sizeof(double), st));
+  SK_TRY(scr.alloc(&bn2d, 1));
   // pinned landing buffer for the per-cycle scalars (the caller's, or our own)
   if (h_pinned) S.h_out = h_pinned;
-  else SK_CUDA(cudaMallocHost((void**)&S.h_out, 8 * sizeof(double)));
+  else {
+    SK_CUDA(cudaMallocHost((void**)&S.h_out, 8 * sizeof(double)));
+    own_pinned = true;
+  }
   S.h_err = (int*)(S.h_out + 4);
   *S.h_err = 0;
-  struct HostFree { double* p; ~HostFree() { if (p) cudaFreeHost(p); } } hf{h_pinned ? nullptr : S.h_out};
-  OpView<double> Av;
   make_view(A, &Av);
   if (S.o.basis != SK_F64) {
     // the op's FP32 parameter copies are allocated here, before any capture
     OpView<float> Af;
     SK_TRY(make_view(A, &Af, st));
   }
-  // kernels launched before the cycle loop: sketch plan (1, or 1 for SRHT
-  // signs), FP32 operator copies, ||b||^2, the initial residual
-  long long pre_launches = 1 + 2;
-  if (S.o.basis != SK_F64) pre_launches += (A->shift ? 1 : 0) + (A->theta ? 1 : 0) + (A->val ? 1 : 0);
+  // kernels launched here: the sketch plan (1, or 1 for SRHT signs) and the
+  // FP32 operator copies
+  setup_launches = 1;
+  if (S.o.basis != SK_F64) setup_launches += (A->shift ? 1 : 0) + (A->theta ? 1 : 0) + (A->val ? 1 : 0);
+  for (int q = 0; q < EV_COUNT; ++q) SK_CUDA(cudaEventCreate(&ev[q]));
+  SK_CUDA(cudaEventCreate(&e0));
+  SK_CUDA(cudaEventCreate(&e1));
+  // the legacy default stream cannot be captured: a private stream then
+  if ((iter || S.o.use_graph) && (st == nullptr || st == cudaStreamLegacy))
+    SK_CUDA(cudaStreamCreateWithFlags(&own, cudaStreamNonBlocking));
+  if (!iter && !S.o.use_graph) {
+    const long long basis_kernels = S.bb.cheb() ? (long long)d + 2 : (long long)d * (S.o.cgs_passes + 1);
+    kernels_per_cycle = 5 + 3 + basis_kernels + 2 + 1 + 2 * ((d + kQrNb - 1) / kQrNb) + 1 + 1 + 1 + (S.bb.cheb() ? 1 : 0);
+  }
+  return SK_OK;
+}
 
+// Capture one cycle reading b and writing x (replaced if the operands change).
+sk_status Solver::capture(const double* b, double* x, cudaStream_t cap) {
+  if (gexec && gb == b && gx == x) return SK_OK;
+  if (gexec) {
+    cudaGraphExecDestroy(gexec);
+    gexec = nullptr;
+  }
+  cudaGraph_t graph = nullptr;
+  SK_CUDA(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+  const sk_status cs = S.pipe ? enqueue_cycle_pipelined(S, A, Av, b, x, cap, ev, true)
+                              : enqueue_cycle(S, A, Av, b, x, cap, ev, true);
+  const cudaError_t ce = cudaStreamEndCapture(cap, &graph);
+  if (cs != SK_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return cs;
+  }
+  if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamEndCapture");
+  const cudaError_t ie = cudaGraphInstantiate(&gexec, graph, 0);
+  kernels_per_cycle = count_kernel_nodes(graph);
+  cudaGraphDestroy(graph);
+  if (ie != cudaSuccess) {
+    gexec = nullptr;
+    return cuda_fail(ie, "cudaGraphInstantiate");
+  }
+  gb = b;
+  gx = x;
+  return SK_OK;
+}
+
+sk_status Solver::run(const double* b, double* x, double tol, sk_info* info, cudaStream_t st) {
+  const int d = S.d;
+  if (info) std::memset(info, 0, sizeof(*info));
+  cudaStream_t cap = st;
+  if (own && (st == nullptr || st == cudaStreamLegacy)) {
+    cap = own;
+    SK_CUDA(cudaStreamSynchronize(st));
+  }
+  last = cap;
   // ||b||^2 and the initial residual
-  double* bn2d = nullptr;
-  SK_TRY(sc.alloc(&bn2d, 1));
-  norm2_kernel<<<vec_grid(S.n), kVecThreads, 0, st>>>(b, S.n, S.vec_part, S.vec_cnt + 1, bn2d);
+  norm2_kernel<<<vec_grid(S.n), kVecThreads, 0, cap>>>(b, S.n, S.vec_part, S.vec_cnt + 1, bn2d);
   SK_CUDA(cudaGetLastError());
-  double bn2 = 0;
-  SK_CUDA(cudaMemcpyAsync(&bn2, bn2d, sizeof(double), cudaMemcpyDeviceToHost, st));
-  SK_TRY(enqueue_residual(S, Av, b, x, st));
-  SK_CUDA(cudaMemcpyAsync(S.h_out, S.bb.bp.rho2, sizeof(double), cudaMemcpyDeviceToHost, st));
-  SK_CUDA(cudaStreamSynchronize(st));
+  SK_CUDA(cudaMemcpyAsync(S.h_out + 5, bn2d, sizeof(double), cudaMemcpyDeviceToHost, cap));
+  SK_TRY(enqueue_residual(S, Av, b, x, cap));
+  SK_CUDA(cudaMemcpyAsync(S.h_out, S.bb.bp.rho2, sizeof(double), cudaMemcpyDeviceToHost, cap));
+  SK_CUDA(cudaStreamSynchronize(cap));
+  const long long pre_launches = setup_launches + 2;  // the setup's launches count once
+  setup_launches = 0;
+  const double bn2 = S.h_out[5];
   if (!std::isfinite(bn2) || !std::isfinite(S.h_out[0])) { set_error("NaN/Inf in b or x"); return SK_ENAN; }
   const double bnorm = std::sqrt(bn2);
   double relres = bnorm > 0 ? std::sqrt(S.h_out[0]) / bnorm : 0.0;
   if (info) info->relres = relres;
   if (bnorm == 0) {
-    SK_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * S.n, st));
-    SK_CUDA(cudaStreamSynchronize(st));
+    SK_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * S.n, cap));
+    SK_CUDA(cudaStreamSynchronize(cap));
     if (info) { info->relres = 0; info->launches = pre_launches; }
     return SK_OK;
   }
@@ -903,49 +988,9 @@ static sk_status sgmres_impl(const sk_op* A, const double* b, double* x, int d, 
     if (info) info->launches = pre_launches;
     return SK_OK;
   }
-
-  cudaGraphExec_t gexec = nullptr;
-  cudaGraph_t graph = nullptr;
-  struct GraphFree {
-    cudaGraphExec_t* e; cudaGraph_t* g;
-    ~GraphFree() { if (*e) cudaGraphExecDestroy(*e); if (*g) cudaGraphDestroy(*g); }
-  } gf{&gexec, &graph};
-  cudaStream_t cap = st;
-  cudaStream_t own = nullptr;
-  cudaEvent_t ev[EV_COUNT];
-  for (int q = 0; q < EV_COUNT; ++q) SK_CUDA(cudaEventCreate(&ev[q]));
-  struct EvsFree { cudaEvent_t* e; ~EvsFree() { for (int q = 0; q < EV_COUNT; ++q) cudaEventDestroy(e[q]); } } evf{ev};
-  long long kernels_per_cycle = 0;
+  if (!iter && S.o.use_graph) SK_TRY(capture(b, x, cap));
   long long iter_launches = 0;
   long long iter_matvecs = 0;
-  // the legacy default stream cannot be captured: use a private stream then
-  if ((iter || S.o.use_graph) && (st == nullptr || st == cudaStreamLegacy)) {
-    SK_CUDA(cudaStreamCreateWithFlags(&own, cudaStreamNonBlocking));
-    cap = own;
-    SK_CUDA(cudaStreamSynchronize(st));
-  }
-  if (iter) {
-    // launches are counted per cycle by run_iterative_cycle
-  } else if (S.o.use_graph) {
-    SK_CUDA(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
-    sk_status cs = S.pipe ? enqueue_cycle_pipelined(S, A, Av, b, x, cap, ev, true)
-                          : enqueue_cycle(S, A, Av, b, x, cap, ev, true);
-    cudaError_t ce = cudaStreamEndCapture(cap, &graph);
-    if (cs != SK_OK) { if (own) cudaStreamDestroy(own); return cs; }
-    if (ce != cudaSuccess) { if (own) cudaStreamDestroy(own); return cuda_fail(ce, "cudaStreamEndCapture"); }
-    ce = cudaGraphInstantiate(&gexec, graph, 0);
-    if (ce != cudaSuccess) { if (own) cudaStreamDestroy(own); return cuda_fail(ce, "cudaGraphInstantiate"); }
-    kernels_per_cycle = count_kernel_nodes(graph);
-  } else {
-    const long long basis_kernels = S.bb.cheb() ? (long long)d + 2 : (long long)d * (S.o.cgs_passes + 1);
-    kernels_per_cycle = 5 + 3 + basis_kernels + 2 + 1 + 2 * ((d + kQrNb - 1) / kQrNb) + 1 + 1 + 1 + (S.bb.cheb() ? 1 : 0);
-  }
-  struct StreamFree { cudaStream_t s; ~StreamFree() { if (s) cudaStreamDestroy(s); } } sf{own};
-
-  cudaEvent_t e0, e1;
-  SK_CUDA(cudaEventCreate(&e0));
-  SK_CUDA(cudaEventCreate(&e1));
-  struct EvFree { cudaEvent_t a, b; ~EvFree() { cudaEventDestroy(a); cudaEventDestroy(b); } } ef{e0, e1};
   SK_CUDA(cudaEventRecord(e0, cap));
   sk_status result = SK_ENOCONV;
   int cycles = 0;
@@ -1004,7 +1049,24 @@ static sk_status sgmres_impl(const sk_op* A, const double* b, double* x, int d, 
   return result;
 }
 
-// Device workspace of one sgmres_solve call: the buffers sgmres_impl
+}  // namespace sk
+
+// A reusable solver: the library object behind sgmres_plan_*.
+struct sk_solver {
+  sk::Solver core;
+};
+
+// Restarted sGMRES after argument validation (also the per-job body of the
+// batched driver's worker threads).
+static sk_status sgmres_impl(const sk_op* A, const double* b, double* x, int d, int k, int s, double tol,
+                             const sk_opts* opts, sk_info* info, cudaStream_t st, double* h_pinned = nullptr) {
+  sk::Solver sv;
+  SK_TRY(sv.setup(A, d, k, s, opts, st, h_pinned));
+  return sv.run(b, x, tol, info, st);
+}
+
+
+// Device workspace of one sgmres_solve call: the buffers Solver::setup
 // allocates, in the same order, each rounded up to 256 bytes.
 extern "C" size_t sk_workspace_bytes(const sk_op* A, int d, int k, int s, const sk_opts* opts) {
   if (!A || d < 1 || k < 1 || k > d || k > kMaxK || s < d + 1 || d > 768) return 0;
@@ -1042,7 +1104,7 @@ extern "C" size_t sk_workspace_bytes(const sk_op* A, int d, int k, int s, const 
   size_t wsb = ws(d + 1, o.basis, true);
   for (int c = 1; iter && c <= o.iter_chunk + 1 && c <= d + 1; ++c) wsb = std::max(wsb, ws(c, o.basis, true));
   t += r(wsb * 8);
-  if (iter) t += r(2 * sizeof(int));
+  if (iter) t += r(2 * sizeof(int)) + r(8);  // the chunk check and the device tau
   t += r((size_t)vec_grid(n) * 8) + r(2 * sizeof(unsigned)) + r(4 * 8) + r(8);
   return t;
 }
@@ -1057,6 +1119,53 @@ extern "C" sk_status sgmres_solve(const sk_op* A, const double* b, double* x, in
   SK_CHECK_ARG(d <= 768, "d <= 768");
   return sgmres_impl(A, b, x, d, k, s, tol, opts, info, (cudaStream_t)stream);
 }
+
+extern "C" sk_status sgmres_plan_create(const sk_op* A, int d, int k, int s, const sk_opts* opts, sk_solver** out,
+                                        void* stream) {
+  SK_CHECK_ARG(A != nullptr && out != nullptr, "NULL argument");
+  *out = nullptr;
+  SK_CHECK_ARG(d >= 1 && k >= 1 && k <= d, "need d >= 1 and 1 <= k <= d");
+  SK_CHECK_ARG(k <= kMaxK, "k <= 16 supported");
+  SK_CHECK_ARG(s >= d + 1, "need s >= d + 1");
+  SK_CHECK_ARG(d <= 768, "d <= 768");
+  sk_solver* p = new (std::nothrow) sk_solver;
+  if (!p) { set_error("out of host memory"); return SK_ENOMEM; }
+  cudaStream_t st = (cudaStream_t)stream;
+  sk_status r = p->core.setup(A, d, k, s, opts, st, nullptr);
+  if (r == SK_OK) r = p->core.sc->alloc(&p->core.hb, (size_t)A->n);
+  if (r == SK_OK) r = p->core.sc->alloc(&p->core.hx, (size_t)A->n);
+  if (r == SK_OK) {
+    const cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) r = cuda_fail(e, "cudaStreamSynchronize");
+  }
+  if (r != SK_OK) {
+    delete p;
+    return r;
+  }
+  *out = p;
+  return SK_OK;
+}
+
+extern "C" sk_status sgmres_plan_solve(sk_solver* p, const double* b, double* x, double tol, sk_info* info,
+                                       void* stream) {
+  SK_CHECK_ARG(p != nullptr && b != nullptr && x != nullptr, "NULL argument");
+  SK_CHECK_ARG(tol > 0, "tol > 0");
+  cudaStream_t st = (cudaStream_t)stream;
+  Solver& c = p->core;
+  const size_t bytes = sizeof(double) * (size_t)c.S.n;
+  SK_CUDA(cudaMemcpyAsync(c.hb, b, bytes, cudaMemcpyDeviceToDevice, st));
+  SK_CUDA(cudaMemcpyAsync(c.hx, x, bytes, cudaMemcpyDeviceToDevice, st));
+  const sk_status r = c.run(c.hb, c.hx, tol, info, st);
+  std::string msg = r != SK_OK ? sk_last_error() : std::string();
+  // x receives the last iterate whatever the status
+  cudaStream_t done = c.last ? c.last : st;
+  SK_CUDA(cudaMemcpyAsync(x, c.hx, bytes, cudaMemcpyDeviceToDevice, done));
+  SK_CUDA(cudaStreamSynchronize(done));
+  if (r != SK_OK) set_error("%s", msg.c_str());
+  return r;
+}
+
+extern "C" void sgmres_plan_destroy(sk_solver* p) { delete p; }
 
 // ----------------------------------------------------------------------------
 // Batched sGMRES: many independent (system, right-hand side) jobs of uneven

@@ -102,6 +102,42 @@ def test_pipelined_cycle_equals_sequential(skg, dtype, kind, d):
         assert ip["relres"] == is_["relres"]
 
 
+@pytest.mark.parametrize("opts", [dict(basis="f32"), dict(basis="f64", pipeline=False), dict(basis="bf16"),
+                                  dict(basis="f32", iter_chunk=16), dict(basis="f32", sketch="srht")])
+def test_plan_handle_equals_one_shot_solves(skg, opts):
+    # one SgmresPlan (sketch plan, buffers and cycle graph built once)
+    # solves several right-hand sides and initial guesses in a row; each
+    # solve equals a fresh sgmres_solve bit for bit (x, cycles, residual),
+    # including a zero right-hand side and an initial guess that already
+    # meets tol (no cycle), and a maxit-limited run that stops unconverged
+    import torch
+    N = 64
+    coef, A, f = _problem(N, 30.0, 12)
+    op = skg.Op.stencil5(N, N, coef)
+    tdt = {"f64": torch.float64, "f32": torch.float32, "bf16": torch.bfloat16}[opts["basis"]]
+    kw = dict(opts, basis=tdt, seed=5)
+    d, k, s = 40, 2, 80
+    rng = np.random.default_rng(7)
+    rhs = [torch.tensor(f, device="cuda"), torch.tensor(rng.standard_normal(N * N), device="cuda"),
+           torch.zeros(N * N, dtype=torch.float64, device="cuda")]
+    plan = skg.SgmresPlan(op, d, k, s, **kw)
+    for tol in (1e-8, 1e-10):
+        for b in rhs:
+            x1, i1 = skg.sgmres_solve(op, b, d, k, s, tol, **kw)
+            x2, i2 = plan.solve(b, tol)
+            assert torch.equal(x1, x2), (tol, float((x1 - x2).abs().max()))
+            assert i1["cycles"] == i2["cycles"] and i1["relres"] == i2["relres"] and i1["status"] == i2["status"]
+    # an initial guess that meets tol: no cycle, x returned as given
+    xg, _ = skg.sgmres_solve(op, rhs[0], d, k, s, 1e-9, **kw)
+    x3, i3 = plan.solve(rhs[0], 1e-6, x0=xg)
+    assert i3["cycles"] == 0 and torch.equal(x3, xg)
+    # maxit: a plan built for one cycle stops unconverged like sgmres_solve
+    short = skg.SgmresPlan(op, d, k, s, **dict(kw, maxit=1))
+    x4, i4 = short.solve(rhs[1], 1e-12)
+    x5, i5 = skg.sgmres_solve(op, rhs[1], d, k, s, 1e-12, **dict(kw, maxit=1))
+    assert i4["status"] == i5["status"] == 5 and torch.equal(x4, x5)
+
+
 def test_initial_guess_and_zero_rhs(skg):
     import torch
     N = 32
