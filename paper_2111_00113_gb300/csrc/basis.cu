@@ -16,9 +16,11 @@
 // The Arnoldi coefficients are kept: A b_j = sum_q (h1+h2)_q b_{j-q} +
 // nu_j b_{j+1}, i.e. AB_d = B_{d+1} Hbar with Hbar (d+1) x d, k+1 diagonals.
 //
-// Constant-coefficient stencils on grids with nx % 4 == 0 take a vector
-// path: each thread handles 4 consecutive cells of one grid row with 16-byte
-// loads; everything else takes the scalar path.
+// Constant-coefficient stencils with n % 4 == 0 take a vector path: each
+// thread handles groups of 4 consecutive cells with 16-byte loads (when
+// nx % 4 == 0 the group lies in one grid row and its north and south
+// neighbours are aligned groups too; otherwise those are single loads and a
+// group may wrap into the next row); everything else takes the scalar path.
 #include <cmath>
 
 #include "basis.cuh"
@@ -78,8 +80,8 @@ __device__ __forceinline__ void gstore(T* p, int64_t i, const C (&v)[G]) {
 }
 
 // m[0..G) = (A x)[i0..i0+G); G = 4 only for constant-coefficient stencils
-// with nx % 4 == 0 (the 4 cells share one grid row).
-template <int G, typename T, typename C>
+// with n % 4 == 0 (see the vector path above).
+template <int G, bool ROWS, typename T, typename C>
 __device__ __forceinline__ void op_apply(const OpView<C>& A, const T* __restrict__ x, int64_t i0, C (&m)[G]) {
   if constexpr (G == 4) {
     int ix0;
@@ -88,19 +90,44 @@ __device__ __forceinline__ void op_apply(const OpView<C>& A, const T* __restrict
     const int iy = (int)iy64;
     C xc[4], up[4], dn[4];
     ld4(x + i0, xc);
-    const C w = ix0 > 0 ? to_c(x[i0 - 1]) : (C)0;
-    const C e = ix0 + 4 < A.nx ? to_c(x[i0 + 4]) : (C)0;
-    if (iy + 1 < A.ny) ld4(x + i0 + A.nx, up);
-    else up[0] = up[1] = up[2] = up[3] = 0;
-    if (iy > 0) ld4(x + i0 - A.nx, dn);
-    else dn[0] = dn[1] = dn[2] = dn[3] = 0;
     // explicit fused multiply-adds, left to right: the rounding does not
     // depend on how the compiler contracts the sum in a given kernel
     const C cP = A.cP, cE = A.cE, cW = A.cW, cN = A.cN, cS = A.cS;
-    m[0] = fma(cS, dn[0], fma(cN, up[0], fma(cW, w, fma(cE, xc[1], cP * xc[0]))));
-    m[1] = fma(cS, dn[1], fma(cN, up[1], fma(cW, xc[0], fma(cE, xc[2], cP * xc[1]))));
-    m[2] = fma(cS, dn[2], fma(cN, up[2], fma(cW, xc[1], fma(cE, xc[3], cP * xc[2]))));
-    m[3] = fma(cS, dn[3], fma(cN, up[3], fma(cW, xc[2], fma(cE, e, cP * xc[3]))));
+    if constexpr (ROWS) {
+      // the four cells share one grid row; north and south are aligned groups
+      const C w = ix0 > 0 ? to_c(x[i0 - 1]) : (C)0;
+      const C e = ix0 + 4 < A.nx ? to_c(x[i0 + 4]) : (C)0;
+      if (iy + 1 < A.ny) ld4(x + i0 + A.nx, up);
+      else up[0] = up[1] = up[2] = up[3] = 0;
+      if (iy > 0) ld4(x + i0 - A.nx, dn);
+      else dn[0] = dn[1] = dn[2] = dn[3] = 0;
+      m[0] = fma(cS, dn[0], fma(cN, up[0], fma(cW, w, fma(cE, xc[1], cP * xc[0]))));
+      m[1] = fma(cS, dn[1], fma(cN, up[1], fma(cW, xc[0], fma(cE, xc[2], cP * xc[1]))));
+      m[2] = fma(cS, dn[2], fma(cN, up[2], fma(cW, xc[1], fma(cE, xc[3], cP * xc[2]))));
+      m[3] = fma(cS, dn[3], fma(cN, up[3], fma(cW, xc[2], fma(cE, e, cP * xc[3]))));
+    } else {
+      // any other width (n % 4 == 0): the group may run into the next grid
+      // row; cell q sits at (ix0 + q, iy) or, past the row's end, at
+      // (ix0 + q - nx, iy + 1); north and south are unaligned single loads,
+      // and a neighbour outside the grid contributes zero
+      const int64_t n = A.n;
+      const C w = i0 > 0 ? to_c(x[i0 - 1]) : (C)0;
+      const C e = i0 + 4 < n ? to_c(x[i0 + 4]) : (C)0;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        int cx = ix0 + q, cy = iy;
+        if (cx >= A.nx) {
+          cx -= A.nx;
+          cy += 1;
+        }
+        const int64_t i = i0 + q;
+        const C xe = (cx + 1 < A.nx) ? (q < 3 ? xc[q + 1] : e) : (C)0;
+        const C xw = (cx > 0) ? (q > 0 ? xc[q - 1] : w) : (C)0;
+        const C xn = (cy + 1 < A.ny) ? to_c(x[i + A.nx]) : (C)0;
+        const C xs = (cy > 0) ? to_c(x[i - A.nx]) : (C)0;
+        m[q] = fma(cS, xs, fma(cN, xn, fma(cW, xw, fma(cE, xe, cP * xc[q]))));
+      }
+    }
     if (A.shift) {
       C sh[4];
       ld4(A.shift + i0, sh);
@@ -163,7 +190,7 @@ __device__ __forceinline__ void pdl_wait() {
 // The passes' bodies take the block index `bid` of `nb` blocks that cover
 // the vector: the whole grid of a single-system launch, or one job's blocks
 // of a grouped launch.
-template <typename T, int KM, int G, bool STORE_M>
+template <typename T, int KM, int G, bool STORE_M, bool ROWS>
 __device__ __forceinline__ void form_body(const BasisParams& p, const OpView<typename Compute<T>::type>& A, int c,
                                           int bid, int nb) {
   constexpr int kIter = IterOf<G>::value;
@@ -203,7 +230,7 @@ __device__ __forceinline__ void form_body(const BasisParams& p, const OpView<typ
       if constexpr (STORE_M) {
         if (!m_late) gload<G>(p.M, i, m[it]);
       } else {
-        op_apply<G>(A, bj, i, m[it]);
+        op_apply<G, ROWS>(A, bj, i, m[it]);
       }
 #pragma unroll
       for (int q = 0; q < KM; ++q)
@@ -243,15 +270,15 @@ __device__ __forceinline__ void form_body(const BasisParams& p, const OpView<typ
   }
 }
 
-template <typename T, int KM, int G, bool STORE_M>
+template <typename T, int KM, int G, bool STORE_M, bool ROWS>
 __global__ void __launch_bounds__(kBasisThreads)
 form_kernel(BasisParams p, OpView<typename Compute<T>::type> A, int c) {
-  form_body<T, KM, G, STORE_M>(p, A, c, blockIdx.x, gridDim.x);
+  form_body<T, KM, G, STORE_M, ROWS>(p, A, c, blockIdx.x, gridDim.x);
 }
 
 // PASS = 1: dots with m (and m stored if STORE_M);  PASS = 2: dots with
 // w = m - W h1.
-template <typename T, int KM, int G, bool STORE_M, int PASS>
+template <typename T, int KM, int G, bool STORE_M, int PASS, bool ROWS>
 __device__ __forceinline__ void dots_body(const BasisParams& p, const OpView<typename Compute<T>::type>& A, int j,
                                           int bid, int nb) {
   constexpr int kIter = IterOf<G>::value;
@@ -277,7 +304,7 @@ __device__ __forceinline__ void dots_body(const BasisParams& p, const OpView<typ
 #pragma unroll
       for (int q = (PASS == 1 ? 1 : 0); q < KM; ++q)
         if (q < kw) gload<G>(bcol<T>(p.B, p.ldb, j - q), i, bw[it][q]);
-      if (PASS == 2 && !STORE_M) op_apply<G>(A, bj, i, m[it]);
+      if (PASS == 2 && !STORE_M) op_apply<G, ROWS>(A, bj, i, m[it]);
     }
   }
   pdl_wait();
@@ -298,7 +325,7 @@ __device__ __forceinline__ void dots_body(const BasisParams& p, const OpView<typ
     if (i < n) {
       if (PASS == 1) {
         gload<G>(bj, i, bw[it][0]);
-        op_apply<G>(A, bj, i, m[it]);
+        op_apply<G, ROWS>(A, bj, i, m[it]);
         if (STORE_M) {
           double md[G];
 #pragma unroll
@@ -375,10 +402,10 @@ __device__ __forceinline__ void dots_body(const BasisParams& p, const OpView<typ
   if (brk) *p.stop = j + 1;
 }
 
-template <typename T, int KM, int G, bool STORE_M, int PASS>
+template <typename T, int KM, int G, bool STORE_M, int PASS, bool ROWS>
 __global__ void __launch_bounds__(kBasisThreads)
 dots_kernel(BasisParams p, OpView<typename Compute<T>::type> A, int j) {
-  dots_body<T, KM, G, STORE_M, PASS>(p, A, j, blockIdx.x, gridDim.x);
+  dots_body<T, KM, G, STORE_M, PASS, ROWS>(p, A, j, blockIdx.x, gridDim.x);
 }
 
 // ---- grouped passes (batched solver) -------------------------------------------
@@ -394,8 +421,9 @@ g_form_kernel(const GJob* __restrict__ jobs, const int2* __restrict__ map, int c
   const GJob& J = jobs[m.x];
   const BasisParams& p = J.bp;
   const OpView<C>& A = job_view<C>(J);
-  if (J.vec) form_body<T, KM, 4, STORE_M>(p, A, c, m.y, p.nblk);
-  else form_body<T, KM, 1, STORE_M>(p, A, c, m.y, p.nblk);
+  if (J.vec == 1) form_body<T, KM, 4, STORE_M, true>(p, A, c, m.y, p.nblk);
+  else if (J.vec == 2) form_body<T, KM, 4, STORE_M, false>(p, A, c, m.y, p.nblk);
+  else form_body<T, KM, 1, STORE_M, true>(p, A, c, m.y, p.nblk);
 }
 
 template <typename T, int KM, bool STORE_M, int PASS>
@@ -406,8 +434,9 @@ g_dots_kernel(const GJob* __restrict__ jobs, const int2* __restrict__ map, int j
   const GJob& J = jobs[m.x];
   const BasisParams& p = J.bp;
   const OpView<C>& A = job_view<C>(J);
-  if (J.vec) dots_body<T, KM, 4, STORE_M, PASS>(p, A, j, m.y, p.nblk);
-  else dots_body<T, KM, 1, STORE_M, PASS>(p, A, j, m.y, p.nblk);
+  if (J.vec == 1) dots_body<T, KM, 4, STORE_M, PASS, true>(p, A, j, m.y, p.nblk);
+  else if (J.vec == 2) dots_body<T, KM, 4, STORE_M, PASS, false>(p, A, j, m.y, p.nblk);
+  else dots_body<T, KM, 1, STORE_M, PASS, true>(p, A, j, m.y, p.nblk);
 }
 
 // prio != 0 gives the launch that priority (the pipelined cycle raises the
@@ -452,6 +481,7 @@ template <typename T, int G>
 __global__ void __launch_bounds__(kBasisThreads)
 cheb_kernel(BasisParams p, OpView<typename Compute<T>::type> A, int c) {
   constexpr int kIter = IterOf<G>::value;
+  constexpr bool ROWS = true;  // the Chebyshev basis takes the vector path only when nx % 4 == 0
   using C = typename Compute<T>::type;
   __shared__ C red[2 * (kBasisThreads / 32)];
   const int64_t n = p.n;
@@ -481,7 +511,7 @@ cheb_kernel(BasisParams p, OpView<typename Compute<T>::type> A, int c) {
     const int64_t i = i_begin + it * stride;
     if (i < n) {
       C m[G], x1[G], v[G];
-      op_apply<G>(A, v1, i, m);
+      op_apply<G, ROWS>(A, v1, i, m);
       gload<G>(v1, i, x1);
 #pragma unroll
       for (int e = 0; e < G; ++e) v[e] = ((m[e] - cc * x1[e]) - be * x2[it][e]) * al;
@@ -532,7 +562,7 @@ template <typename T, int G>
 static sk_status enqueue_cheb_t(const BasisParams& p, const OpView<typename Compute<T>::type>& A, cudaStream_t st) {
   using C = typename Compute<T>::type;
   const int g = p.nblk;
-  SK_CUDA(launch_pdl(form_kernel<T, 2, G, false>, g, st, false, p.prio, p, A, 0));  // v_0 = r/||r||
+  SK_CUDA(launch_pdl(form_kernel<T, 2, G, false, true>, g, st, false, p.prio, p, A, 0));  // v_0 = r/||r||
   for (int c = 1; c <= p.d; ++c) SK_CUDA(launch_pdl(cheb_kernel<T, G>, g, st, true, p.prio, p, A, c));
   cheb_finalize_kernel<C><<<p.d + 1, kBasisThreads, 0, st>>>(p, g);
   SK_CUDA(cudaGetLastError());
@@ -572,31 +602,41 @@ sk_status enqueue_cheb_normalize(const BasisParams& p, cudaStream_t st) {
   return SK_OK;
 }
 
-template <typename T, int KM, int G, bool SM>
+template <typename T, int KM, int G, bool SM, bool ROWS>
 static sk_status enqueue_basis_t(const BasisParams& p, const OpView<typename Compute<T>::type>& A, cudaStream_t st) {
   const int g = p.nblk;
   // steps [j_begin, j_end) (j_end = 0: all d); the first launch follows
   // memset/plain nodes or other kernels: no programmatic edge
   const int jb = p.j_begin, je = p.j_end > 0 ? p.j_end : p.d;
-  if (jb == 0) SK_CUDA(launch_pdl(form_kernel<T, KM, G, SM>, g, st, false, p.prio, p, A, 0));
+  if (jb == 0) SK_CUDA(launch_pdl(form_kernel<T, KM, G, SM, ROWS>, g, st, false, p.prio, p, A, 0));
   for (int j = jb; j < je; ++j) {
-    SK_CUDA(launch_pdl(dots_kernel<T, KM, G, SM, 1>, g, st, jb == 0 || j > jb || p.pdl_resume, p.prio, p, A, j));
-    if (p.passes == 2) SK_CUDA(launch_pdl(dots_kernel<T, KM, G, SM, 2>, g, st, true, p.prio, p, A, j));
-    SK_CUDA(launch_pdl(form_kernel<T, KM, G, SM>, g, st, true, p.prio, p, A, j + 1));
+    SK_CUDA(launch_pdl(dots_kernel<T, KM, G, SM, 1, ROWS>, g, st, jb == 0 || j > jb || p.pdl_resume, p.prio, p, A,
+                       j));
+    if (p.passes == 2) SK_CUDA(launch_pdl(dots_kernel<T, KM, G, SM, 2, ROWS>, g, st, true, p.prio, p, A, j));
+    SK_CUDA(launch_pdl(form_kernel<T, KM, G, SM, ROWS>, g, st, true, p.prio, p, A, j + 1));
   }
   return SK_OK;
 }
 
-template <typename T, int G, bool SM, typename C>
+template <typename T, int G, bool SM, bool ROWS, typename C>
 static sk_status enqueue_basis_k(const BasisParams& p, const OpView<C>& A, cudaStream_t st) {
-  if (p.k <= 2) return enqueue_basis_t<T, 2, G, SM>(p, A, st);
-  if (p.k <= 4) return enqueue_basis_t<T, 4, G, SM>(p, A, st);
-  if (p.k <= 8) return enqueue_basis_t<T, 8, G, SM>(p, A, st);
-  return enqueue_basis_t<T, 16, G, SM>(p, A, st);
+  if (p.k <= 2) return enqueue_basis_t<T, 2, G, SM, ROWS>(p, A, st);
+  if (p.k <= 4) return enqueue_basis_t<T, 4, G, SM, ROWS>(p, A, st);
+  if (p.k <= 8) return enqueue_basis_t<T, 8, G, SM, ROWS>(p, A, st);
+  return enqueue_basis_t<T, 16, G, SM, ROWS>(p, A, st);
+}
+
+// vector path with cells in one row (nx % 4 == 0), vector path across rows,
+// or the scalar path
+template <typename T, bool SM, typename C>
+static sk_status enqueue_basis_v(const BasisParams& p, const OpView<C>& A, bool vec, bool rows, cudaStream_t st) {
+  if (vec && rows) return enqueue_basis_k<T, 4, SM, true>(p, A, st);
+  if (vec) return enqueue_basis_k<T, 4, SM, false>(p, A, st);
+  return enqueue_basis_k<T, 1, SM, true>(p, A, st);
 }
 
 bool basis_vector_path(const sk_op* op, int64_t ldb, const void* B) {
-  return op->kind == OP_STENCIL5 && op->nx % 4 == 0 && ldb % 8 == 0 && op->n < (1ll << 31) &&
+  return op->kind == OP_STENCIL5 && op->n % 4 == 0 && ldb % 8 == 0 && op->n < (1ll << 31) &&
          ((uintptr_t)B % 16) == 0;
 }
 
@@ -642,34 +682,35 @@ sk_status enqueue_basis_grouped(const GJob* jobs, const int2* map, int nmap, sk_
 sk_status enqueue_basis(const BasisParams& p, const sk_op* op, cudaStream_t st) {
   if (p.k > kMaxK) { set_error("k <= %d supported", kMaxK); return SK_EINVAL; }
   const bool vec = basis_vector_path(op, p.ldb, p.B) && (p.r == nullptr || ((uintptr_t)p.r % 16) == 0);
+  const bool rows = op->nx % 4 == 0;
   BasisParams q = p;
   q.nblk = basis_grid(p.n, vec ? 4 : 1);
   if (q.nblk > p.nblk_cap) { set_error("basis: partial buffer too small"); return SK_EINVAL; }
   const BasisParams& pp = q;
   if (p.kind == SK_BASIS_CHEBYSHEV) {
     if (!p.sigma || !p.cheb_part || !(p.cheb_rho > 0)) { set_error("Chebyshev basis: workspace or rho missing"); return SK_EINVAL; }
+    const bool cvec = vec && rows;
+    q.nblk = basis_grid(p.n, cvec ? 4 : 1);
     if (p.dtype == SK_F64) {
       OpView<double> A;
       make_view(op, &A);
-      return vec ? enqueue_cheb_t<double, 4>(pp, A, st) : enqueue_cheb_t<double, 1>(pp, A, st);
+      return cvec ? enqueue_cheb_t<double, 4>(pp, A, st) : enqueue_cheb_t<double, 1>(pp, A, st);
     }
     OpView<float> A;
     SK_TRY(make_view(op, &A, st));
-    if (p.dtype == SK_F32) return vec ? enqueue_cheb_t<float, 4>(pp, A, st) : enqueue_cheb_t<float, 1>(pp, A, st);
-    return vec ? enqueue_cheb_t<__nv_bfloat16, 4>(pp, A, st) : enqueue_cheb_t<__nv_bfloat16, 1>(pp, A, st);
+    if (p.dtype == SK_F32) return cvec ? enqueue_cheb_t<float, 4>(pp, A, st) : enqueue_cheb_t<float, 1>(pp, A, st);
+    return cvec ? enqueue_cheb_t<__nv_bfloat16, 4>(pp, A, st) : enqueue_cheb_t<__nv_bfloat16, 1>(pp, A, st);
   }
   if (p.dtype == SK_F64) {
     OpView<double> A;
     make_view(op, &A);
     if (!p.M) { set_error("FP64 basis needs the m workspace"); return SK_EINVAL; }
-    return vec ? enqueue_basis_k<double, 4, true>(pp, A, st) : enqueue_basis_k<double, 1, true>(pp, A, st);
+    return enqueue_basis_v<double, true>(pp, A, vec, rows, st);
   }
   OpView<float> A;
   SK_TRY(make_view(op, &A, st));
-  if (p.dtype == SK_F32)
-    return vec ? enqueue_basis_k<float, 4, false>(pp, A, st) : enqueue_basis_k<float, 1, false>(pp, A, st);
-  return vec ? enqueue_basis_k<__nv_bfloat16, 4, false>(pp, A, st)
-             : enqueue_basis_k<__nv_bfloat16, 1, false>(pp, A, st);
+  if (p.dtype == SK_F32) return enqueue_basis_v<float, false>(pp, A, vec, rows, st);
+  return enqueue_basis_v<__nv_bfloat16, false>(pp, A, vec, rows, st);
 }
 
 }  // namespace sk

@@ -17,7 +17,7 @@ struct GJob {
   BasisParams bp;        // the job's basis build (pointers into its buffers and slab)
   OpView<float> Af;      // operator views (FP32 one only for FP32/BF16 bases)
   OpView<double> Ad;
-  int vec;               // basis vector path (4 cells per thread)
+  int vec;               // basis path: 1 = 4 cells of one row, 2 = 4 cells across rows, 0 = scalar
   int vgrid;             // blocks of the residual and norm kernels
   int ugrid, uvec;       // blocks of the update kernel; 4 rows per thread if uvec
   const double* b;

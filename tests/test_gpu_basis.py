@@ -70,9 +70,10 @@ def test_stencil_grid_index_math(skg):
         op = skg.Op.stencil5(nx, ny, coef)
         y = op.apply(torch.tensor(x2.ravel(), device="cuda")).cpu().numpy()
         assert np.max(np.abs(y - ref)) <= 1e-12 * (1 + np.max(np.abs(ref))), (nx, ny)
-    # the basis passes (vector path when nx % 4 == 0, scalar otherwise):
+    # the basis passes (vector path with the cells of a group in one row when
+    # nx % 4 == 0, across rows when only n % 4 == 0, scalar otherwise):
     # b_1 = (A b_0 - h b_0) / nu is A r up to the combination with r
-    for nx, ny in ((4093, 1031), (2048, 2049)):
+    for nx, ny in ((4093, 1031), (2048, 2049), (1022, 1024), (6, 50)):
         r = rng.standard_normal(nx * ny)
         out = skg.trunc_arnoldi_basis(skg.Op.stencil5(nx, ny, coef), torch.tensor(r, device="cuda"), 1, 1,
                                       dtype=torch.float64)

@@ -27,12 +27,12 @@ def test_batched_equals_single_solves(skg, dtype, mode, elems):
     # every job of the batch runs the same kernel bodies with the same block
     # shapes as a single solve: the solutions agree bit for bit, and all
     # reach tol.  Grouped: every launch serves all resident jobs (jobs of
-    # 24^2 .. 64^2 cells, vector and scalar stencil paths mixed); elems =
+    # 24^2 .. 64^2 cells, the three stencil paths mixed); elems =
     # 5000 admits one or two jobs at a time, so jobs start at different
     # cycles of the batch.
     import torch
     tdt = torch.float64 if dtype == "f64" else torch.float32
-    sides = [24, 64, 40, 33, 48]
+    sides = [24, 64, 34, 33, 48]   # 34: the vector path across grid rows; 33: the scalar path
     pes = [5.0, 40.0, 80.0, 20.0, 10.0]
     ops, bs, mats, fs = [], [], [], []
     for i, (N, Pe) in enumerate(zip(sides, pes)):
