@@ -16,11 +16,12 @@
 // The Arnoldi coefficients are kept: A b_j = sum_q (h1+h2)_q b_{j-q} +
 // nu_j b_{j+1}, i.e. AB_d = B_{d+1} Hbar with Hbar (d+1) x d, k+1 diagonals.
 //
-// Constant-coefficient stencils with n % 4 == 0 take a vector path: each
-// thread handles groups of 4 consecutive cells with 16-byte loads (when
-// nx % 4 == 0 the group lies in one grid row and its north and south
-// neighbours are aligned groups too; otherwise those are single loads and a
-// group may wrap into the next row); everything else takes the scalar path.
+// Constant-coefficient stencils take a vector path: each thread handles
+// groups of 4 consecutive cells with 16-byte loads.  When nx % 4 == 0 the
+// group lies in one grid row and its north and south neighbours are aligned
+// groups too; otherwise those are single loads, a group may wrap into the
+// next row, and when n % 4 != 0 the last group reads zeros past n and writes
+// nothing there.  Other operators take the scalar path.
 #include <cmath>
 
 #include "basis.cuh"
@@ -79,8 +80,34 @@ __device__ __forceinline__ void gstore(T* p, int64_t i, const C (&v)[G]) {
   else p[i] = from_c<T>(v[0]);
 }
 
+// GUARD: the vector path across rows also serves n % 4 != 0; its last group
+// (the one holding n - 1) reads zeros and writes nothing past n.
+template <int G, bool GUARD, typename T, typename C>
+__device__ __forceinline__ void gload_n(const T* p, int64_t i, int64_t n, C (&v)[G]) {
+  if constexpr (GUARD) {
+    if (i + G > n) {
+#pragma unroll
+      for (int e = 0; e < G; ++e) v[e] = (i + e < n) ? to_c(p[i + e]) : (C)0;
+      return;
+    }
+  }
+  gload<G>(p, i, v);
+}
+template <int G, bool GUARD, typename T, typename C>
+__device__ __forceinline__ void gstore_n(T* p, int64_t i, int64_t n, const C (&v)[G]) {
+  if constexpr (GUARD) {
+    if (i + G > n) {
+#pragma unroll
+      for (int e = 0; e < G; ++e)
+        if (i + e < n) p[i + e] = from_c<T>(v[e]);
+      return;
+    }
+  }
+  gstore<G>(p, i, v);
+}
+
 // m[0..G) = (A x)[i0..i0+G); G = 4 only for constant-coefficient stencils
-// with n % 4 == 0 (see the vector path above).
+// (see the vector path above).
 template <int G, bool ROWS, typename T, typename C>
 __device__ __forceinline__ void op_apply(const OpView<C>& A, const T* __restrict__ x, int64_t i0, C (&m)[G]) {
   if constexpr (G == 4) {
@@ -106,7 +133,7 @@ __device__ __forceinline__ void op_apply(const OpView<C>& A, const T* __restrict
       m[2] = fma(cS, dn[2], fma(cN, up[2], fma(cW, xc[1], fma(cE, xc[3], cP * xc[2]))));
       m[3] = fma(cS, dn[3], fma(cN, up[3], fma(cW, xc[2], fma(cE, e, cP * xc[3]))));
     } else {
-      // any other width (n % 4 == 0): the group may run into the next grid
+      // any other width: the group may run into the next grid
       // row; cell q sits at (ix0 + q, iy) or, past the row's end, at
       // (ix0 + q - nx, iy + 1); north and south are unaligned single loads,
       // and a neighbour outside the grid contributes zero
@@ -130,9 +157,17 @@ __device__ __forceinline__ void op_apply(const OpView<C>& A, const T* __restrict
     }
     if (A.shift) {
       C sh[4];
-      ld4(A.shift + i0, sh);
+      if constexpr (ROWS) ld4(A.shift + i0, sh);
+      else gload_n<4, true>(A.shift, i0, A.n, sh);
 #pragma unroll
       for (int q = 0; q < 4; ++q) m[q] = fma(sh[q], xc[q], m[q]);
+    }
+    if constexpr (!ROWS) {
+      // cells past n (the last group when n % 4 != 0) contribute nothing; x's
+      // column padding read there is never used
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (i0 + q >= A.n) m[q] = 0;
     }
   } else {
     m[0] = A.apply(x, i0);
@@ -194,6 +229,7 @@ template <typename T, int KM, int G, bool STORE_M, bool ROWS>
 __device__ __forceinline__ void form_body(const BasisParams& p, const OpView<typename Compute<T>::type>& A, int c,
                                           int bid, int nb) {
   constexpr int kIter = IterOf<G>::value;
+  constexpr bool GUARD = G == 4 && !ROWS;
   using C = typename Compute<T>::type;
   T* out = bcol<T>(p.B, p.ldb, c);
   const int64_t n = p.n;
@@ -210,8 +246,8 @@ __device__ __forceinline__ void form_body(const BasisParams& p, const OpView<typ
     for (int64_t i = i_begin; i < n; i += stride) {
       C v[G];
 #pragma unroll
-      for (int q = 0; q < G; ++q) v[q] = (C)(p.r[i + q] * inv);
-      gstore<G>(out, i, v);
+      for (int q = 0; q < G; ++q) v[q] = (!GUARD || i + q < n) ? (C)(p.r[i + q] * inv) : (C)0;
+      gstore_n<G, GUARD>(out, i, n, v);
     }
     return;
   }
@@ -228,13 +264,13 @@ __device__ __forceinline__ void form_body(const BasisParams& p, const OpView<typ
     const int64_t i = i_begin + it * stride;
     if (i < n) {
       if constexpr (STORE_M) {
-        if (!m_late) gload<G>(p.M, i, m[it]);
+        if (!m_late) gload_n<G, GUARD>(p.M, i, n, m[it]);
       } else {
         op_apply<G, ROWS>(A, bj, i, m[it]);
       }
 #pragma unroll
       for (int q = 0; q < KM; ++q)
-        if (q < kw) gload<G>(bcol<T>(p.B, p.ldb, j - q), i, bw[it][q]);
+        if (q < kw) gload_n<G, GUARD>(bcol<T>(p.B, p.ldb, j - q), i, n, bw[it][q]);
     }
   }
   pdl_wait();
@@ -244,7 +280,7 @@ __device__ __forceinline__ void form_body(const BasisParams& p, const OpView<typ
 #pragma unroll
     for (int it = 0; it < kIter; ++it) {
       const int64_t i = i_begin + it * stride;
-      if (i < n) gload<G>(p.M, i, m[it]);
+      if (i < n) gload_n<G, GUARD>(p.M, i, n, m[it]);
     }
   }
   const C* cf = coef_row<C>(p, j);
@@ -265,7 +301,7 @@ __device__ __forceinline__ void form_body(const BasisParams& p, const OpView<typ
       }
 #pragma unroll
       for (int e = 0; e < G; ++e) m[it][e] *= inv;
-      gstore<G>(out, i, m[it]);
+      gstore_n<G, GUARD>(out, i, n, m[it]);
     }
   }
 }
@@ -282,6 +318,7 @@ template <typename T, int KM, int G, bool STORE_M, int PASS, bool ROWS>
 __device__ __forceinline__ void dots_body(const BasisParams& p, const OpView<typename Compute<T>::type>& A, int j,
                                           int bid, int nb) {
   constexpr int kIter = IterOf<G>::value;
+  constexpr bool GUARD = G == 4 && !ROWS;
   using C = typename Compute<T>::type;
   __shared__ C red[(KM + 1) * (kBasisThreads / 32)];
   const int kw = min(p.k, j + 1);
@@ -303,7 +340,7 @@ __device__ __forceinline__ void dots_body(const BasisParams& p, const OpView<typ
     if (i < n) {
 #pragma unroll
       for (int q = (PASS == 1 ? 1 : 0); q < KM; ++q)
-        if (q < kw) gload<G>(bcol<T>(p.B, p.ldb, j - q), i, bw[it][q]);
+        if (q < kw) gload_n<G, GUARD>(bcol<T>(p.B, p.ldb, j - q), i, n, bw[it][q]);
       if (PASS == 2 && !STORE_M) op_apply<G, ROWS>(A, bj, i, m[it]);
     }
   }
@@ -324,16 +361,16 @@ __device__ __forceinline__ void dots_body(const BasisParams& p, const OpView<typ
     const int64_t i = i_begin + it * stride;
     if (i < n) {
       if (PASS == 1) {
-        gload<G>(bj, i, bw[it][0]);
+        gload_n<G, GUARD>(bj, i, n, bw[it][0]);
         op_apply<G, ROWS>(A, bj, i, m[it]);
         if (STORE_M) {
           double md[G];
 #pragma unroll
           for (int e = 0; e < G; ++e) md[e] = (double)m[it][e];
-          gstore<G>(p.M, i, md);
+          gstore_n<G, GUARD>(p.M, i, n, md);
         }
       } else if (STORE_M) {
-        gload<G>(p.M, i, m[it]);
+        gload_n<G, GUARD>(p.M, i, n, m[it]);
       }
       if (PASS == 2) {
 #pragma unroll
@@ -636,7 +673,7 @@ static sk_status enqueue_basis_v(const BasisParams& p, const OpView<C>& A, bool 
 }
 
 bool basis_vector_path(const sk_op* op, int64_t ldb, const void* B) {
-  return op->kind == OP_STENCIL5 && op->n % 4 == 0 && ldb % 8 == 0 && op->n < (1ll << 31) &&
+  return op->kind == OP_STENCIL5 && ldb % 8 == 0 && op->n < (1ll << 31) &&
          ((uintptr_t)B % 16) == 0;
 }
 

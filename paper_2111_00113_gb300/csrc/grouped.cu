@@ -298,7 +298,7 @@ sk_status sgmres_batched_grouped(int nsys, const sk_op* const* A, int nrhs, cons
     PlanEntry* pe = nullptr;
     SK_TRY(plan_for(n, &pe));
     const int64_t ldb = ((n + 7) / 8) * 8;
-    const int vec_guess = (op->kind == OP_STENCIL5 && n % 4 == 0 && n < (1ll << 31)) ? 1 : 0;
+    const int vec_guess = (op->kind == OP_STENCIL5 && n < (1ll << 31)) ? 1 : 0;
     const int nblk = basis_grid(n, vec_guess ? 4 : 1);
     VecLayout v;
     size_t off = 0;
