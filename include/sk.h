@@ -214,10 +214,11 @@ typedef struct {
                               values with sigma_1 / sigma_i <= srr_trunc_tol, and the eigenproblem
                               (U_r^T S A B V_r) z = theta Sigma_r z */
   int pipeline;            /* sgmres_solve with a captured cycle (use_graph), the truncated-Arnoldi
-                              basis and 3 launches per step: 1 (default) = sketch each finished
-                              block of 16 basis columns and add the panels it completes to the QR
-                              of S A B on a second, lower-priority stream while the basis passes
-                              continue (same arithmetic, overlapped); 0 = one phase after another */
+                              basis with 3 launches per step or the Chebyshev basis: 1 (default) =
+                              sketch each finished block of 16 basis columns (Chebyshev: after its
+                              column norms) and add the panels it completes to the QR of S A B on
+                              a second, lower-priority stream while the basis passes continue (same
+                              arithmetic, overlapped); 0 = one phase after another */
   int batch_mode;          /* sgmres_solve_batched: 0 (default) = grouped where supported, else
                               worker threads; 1 = grouped (SK_EINVAL where unsupported); 2 = worker
                               threads.  Grouped: every launch advances one phase of all resident

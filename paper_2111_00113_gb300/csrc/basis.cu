@@ -573,9 +573,9 @@ cheb_kernel(BasisParams p, OpView<typename Compute<T>::type> A, int c) {
 // order), column j of Hbar = H_v[:, j] / sigma_j.  A zero or non-finite norm
 // ends the basis at j columns.
 template <typename C>
-__global__ void __launch_bounds__(kBasisThreads) cheb_finalize_kernel(BasisParams p, int nblk) {
+__global__ void __launch_bounds__(kBasisThreads) cheb_finalize_kernel(BasisParams p, int nblk, int j0) {
   __shared__ C red[kBasisThreads / 32];
-  const int j = blockIdx.x;
+  const int j = j0 + blockIdx.x;
   const C* part = reinterpret_cast<const C*>(p.cheb_part) + (int64_t)j * p.nblk_cap;
   C t[1] = {0};
   for (int b = threadIdx.x; b < nblk; b += blockDim.x) t[0] += part[b];
@@ -599,12 +599,20 @@ template <typename T, int G>
 static sk_status enqueue_cheb_t(const BasisParams& p, const OpView<typename Compute<T>::type>& A, cudaStream_t st) {
   using C = typename Compute<T>::type;
   const int g = p.nblk;
-  SK_CUDA(launch_pdl(form_kernel<T, 2, G, false, true>, g, st, false, p.prio, p, A, 0));  // v_0 = r/||r||
-  for (int c = 1; c <= p.d; ++c) SK_CUDA(launch_pdl(cheb_kernel<T, G>, g, st, true, p.prio, p, A, c));
-  cheb_finalize_kernel<C><<<p.d + 1, kBasisThreads, 0, st>>>(p, g);
-  SK_CUDA(cudaGetLastError());
+  // steps [j_begin, j_end) form v_{j_begin+1} .. v_{j_end} (j_end = 0: all d;
+  // then the norms are finalised here too, else by enqueue_cheb_finalize)
+  const int jb = p.j_begin, je = p.j_end > 0 ? p.j_end : p.d;
+  if (jb == 0)
+    SK_CUDA(launch_pdl(form_kernel<T, 2, G, false, true>, g, st, false, p.prio, p, A, 0));  // v_0 = r/||r||
+  for (int c = jb + 1; c <= je; ++c)
+    SK_CUDA(launch_pdl(cheb_kernel<T, G>, g, st, jb == 0 || c > jb + 1 || p.pdl_resume, p.prio, p, A, c));
+  if (p.j_end == 0) {
+    cheb_finalize_kernel<C><<<p.d + 1, kBasisThreads, 0, st>>>(p, g, 0);
+    SK_CUDA(cudaGetLastError());
+  }
   return SK_OK;
 }
+
 
 // Unit columns for callers of the basis itself: B[:, j] /= sigma_j and
 // Hbar[i, j] *= sigma_i (Hbar then relates the unit columns).
@@ -627,6 +635,17 @@ __global__ void cheb_scale_hbar_kernel(BasisParams p) {
     const int i = q % (p.d + 1);
     if (i < *p.stop) p.Hbar[q] *= p.sigma[i];
   }
+}
+
+sk_status enqueue_cheb_finalize(const BasisParams& p, const sk_op* op, int j0, int j1, cudaStream_t st) {
+  if (j1 <= j0) return SK_OK;
+  const bool cvec = basis_vector_path(op, p.ldb, p.B) && (p.r == nullptr || ((uintptr_t)p.r % 16) == 0) &&
+                    op->nx % 4 == 0;
+  const int g = basis_grid(p.n, cvec ? 4 : 1);
+  if (p.dtype == SK_F64) cheb_finalize_kernel<double><<<j1 - j0, kBasisThreads, 0, st>>>(p, g, j0);
+  else cheb_finalize_kernel<float><<<j1 - j0, kBasisThreads, 0, st>>>(p, g, j0);
+  SK_CUDA(cudaGetLastError());
+  return SK_OK;
 }
 
 sk_status enqueue_cheb_normalize(const BasisParams& p, cudaStream_t st) {

@@ -60,6 +60,10 @@ sk_status enqueue_basis_persistent(const BasisParams& bp, const sk_op* op, Persi
 int basis_grid(int64_t n, int G);
 bool basis_vector_path(const sk_op* op, int64_t ldb, const void* B);
 sk_status enqueue_basis(const BasisParams& p, const sk_op* op, cudaStream_t st);
+// Chebyshev, a build in step ranges (j_end > 0): sigma_j and column j of
+// Hbar for j in [j0, j1), once the steps forming v_j (and v_1, for j = 0)
+// have run.
+sk_status enqueue_cheb_finalize(const BasisParams& p, const sk_op* op, int j0, int j1, cudaStream_t st);
 // Chebyshev: rescale B's columns to unit norm and Hbar to the unit basis
 // (diag(sigma) Hbar), for callers that want the normalised basis itself.
 sk_status enqueue_cheb_normalize(const BasisParams& p, cudaStream_t st);

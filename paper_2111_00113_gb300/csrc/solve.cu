@@ -594,9 +594,14 @@ static sk_status enqueue_cycle_pipelined(SolveState& S, const sk_op* A, const Op
     prev = je;
     if (rs != SK_OK) break;
     SK_CUDA(cudaEventRecord(S.blk[t], st));
-    // side: sketch of the block's columns
+    // side: (Chebyshev: the block's column norms and Hbar columns, then) the
+    // sketch of the block's columns
     SK_CUDA(cudaStreamWaitEvent(sd, S.blk[t], 0));
     const int c0 = kQrNb * t, c1 = std::min(c0 + kQrNb, d + 1);
+    if (S.bb.cheb()) {
+      rs = enqueue_cheb_finalize(bp, A, c0, c1, sd);
+      if (rs != SK_OK) break;
+    }
     rs = S.sketch.apply((const unsigned char*)bp.B + (size_t)c0 * bp.ldb * esz, bp.ldb, c1 - c0, S.o.basis,
                         S.SB + (size_t)c0 * s, S.ws_B, sd, true);
     if (rs != SK_OK) break;
@@ -623,6 +628,10 @@ static sk_status enqueue_cycle_pipelined(SolveState& S, const sk_op* A, const Op
   SK_CUDA(cudaStreamWaitEvent(st, S.join, 0));
   SK_TRY(mark(ev, EV_SB, st, capturing));
   SK_TRY(enqueue_ls_solve(S.Aug, S.rdiag, s, d, S.o.stab_tol, S.y, S.out + 1, st));
+  if (S.bb.cheb()) {
+    scale_y_kernel<<<1, 256, 0, st>>>(S.y, bp.sigma, d);
+    SK_CUDA(cudaGetLastError());
+  }
   SK_TRY(mark(ev, EV_SMALL, st, capturing));
   SK_TRY(enqueue_update(x, bp.B, bp.ldb, S.n, d, S.o.basis, S.y, S.out + 1, st));
   SK_TRY(mark(ev, EV_UPDATE, st, capturing));
@@ -832,8 +841,8 @@ sk_status Solver::setup(const sk_op* A_, int d, int k, int s, const sk_opts* opt
   Scratch& scr = *sc;
   SK_TRY(S.bb.alloc(S.n, d, k, S.o.basis, S.o.cgs_passes, S.o.breakdown, scr, nullptr, A, S.o.persistent != 0));
   SK_TRY(S.bb.set_kind(S.o, scr));
-  // the pipelined cycle: captured truncated-Arnoldi cycles of the 3-launch basis
-  S.pipe = S.o.pipeline != 0 && S.o.use_graph && !iter && !S.bb.cheb() && !S.bb.persistent;
+  // the pipelined cycle: captured cycles of the 3-launch Arnoldi basis or the Chebyshev basis
+  S.pipe = S.o.pipeline != 0 && S.o.use_graph && !iter && !S.bb.persistent;
   if (S.pipe) {
     int least = 0, greatest = 0;
     SK_CUDA(cudaDeviceGetStreamPriorityRange(&least, &greatest));

@@ -138,6 +138,26 @@ def test_plan_handle_equals_one_shot_solves(skg, opts):
     assert i4["status"] == i5["status"] == 5 and torch.equal(x4, x5)
 
 
+@pytest.mark.parametrize("dtype,d,N", [("f32", 75, 96), ("f64", 40, 96), ("f32", 33, 61)])
+def test_pipelined_chebyshev_cycle_equals_sequential(skg, dtype, d, N):
+    # the Chebyshev basis in the pipelined cycle: each block's column norms
+    # and Hbar columns are finalised on the sketch stream before its sketch;
+    # the iterates equal the sequential cycle's bit for bit (N = 61: the
+    # scalar recurrence path, 33 columns: a last block of one column)
+    import torch
+    coef, A, f = _problem(N, 5.0, 3)
+    op = skg.Op.stencil5(N, N, coef)
+    b = torch.tensor(f, device="cuda")
+    tdt = {"f64": torch.float64, "f32": torch.float32}[dtype]
+    kw = dict(basis=tdt, zeta=hashing.default_zeta(d), seed=5, cheb=(4.0, 4.0, 1.0))
+    xp = xs = None
+    for c in range(3):
+        xp, ip = skg.sgmres_solve(op, b, d, 2, 2 * d, 1e-300, x0=xp, maxit=1, pipeline=True, **kw)
+        xs, is_ = skg.sgmres_solve(op, b, d, 2, 2 * d, 1e-300, x0=xs, maxit=1, pipeline=False, **kw)
+        assert torch.equal(xp, xs), (c, float((xp - xs).abs().max()))
+        assert ip["relres"] == is_["relres"]
+
+
 def test_initial_guess_and_zero_rhs(skg):
     import torch
     N = 32
