@@ -578,7 +578,9 @@ def run_case(args):
       cycle   one warm-up restart cycle, then one more, of the scale workload
               (FP32 basis; --no-pipeline for the sequential cycle);
       sketch  a reusable sparse-sign plan applied twice to a --n x --cols
-              FP32 block (s = 600, zeta = 12)."""
+              FP32 block (s = 600, zeta = 12);
+      srr     two sketched Rayleigh-Ritz calls (Algorithm 2) on the 512^2
+              eig workload, FP64 basis (d = 200, k = 4, s = 400)."""
     import torch
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
@@ -591,6 +593,17 @@ def run_case(args):
             x, info = skg.sgmres_solve(A, b, W["d"], W["k"], W["s"], 1e-300, maxit=1, **kw)
         torch.cuda.synchronize()
         print("case cycle ms %.3f launches %d" % (info["ms"][5], info["launches"]))
+    elif args.case == "srr":
+        import synth
+        W = synth.WORKLOADS["eig"]
+        N = W["N"]
+        shift = torch.tensor(synth.uniform(W["shift_seed"], N * N), device=dev)
+        op = skg.Op.stencil5(N, N, synth.conv_diff_coef(N, W["Pe"]), shift)
+        w1 = torch.tensor(synth.randn(synth.SRR_START_SEED, N * N), device=dev)
+        for _ in range(2):
+            r = skg.srr_eigs(op, w1, W["nev"], W["d"], W["k"], W["s"], zeta=W["zeta"], basis=torch.float64)
+        torch.cuda.synchronize()
+        print("case srr ms %.2f nconv %d" % (r["info"]["ms"][5], r["nconv"]))
     else:
         g = torch.Generator(device=dev).manual_seed(0)
         B = torch.randn((args.cols, args.n), generator=g, device=dev, dtype=torch.float32).t()
@@ -618,7 +631,7 @@ def build_parser():
                     help="run each cycle's phases one after another (no sketch/QR overlap with the basis)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the sketch, sRR, batched and Laplacian measurements")
-    ap.add_argument("--case", choices=["cycle", "sketch"],
+    ap.add_argument("--case", choices=["cycle", "sketch", "srr"],
                     help="run one small piece of the path for a profiler capture and exit")
     ap.add_argument("--n", type=int, default=1 << 18, help="rows of the --case sketch block")
     ap.add_argument("--cols", type=int, default=301, help="columns of the --case sketch block")
