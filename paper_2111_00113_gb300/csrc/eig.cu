@@ -2,8 +2,8 @@
 // M-hat (d x d, FP64, d <= 232): Algorithm 2's "solve eigenvalue problem"
 // step, written for one GPU.
 //
-//   1. Householder reduction to upper Hessenberg form H = P^T M P (one CTA;
-//      reflectors kept below the subdiagonal).
+//   1. Householder reduction to upper Hessenberg form H = P^T M P (an 8-CTA
+//      cluster; reflectors kept below the subdiagonal).
 //   2. Eigenvalues of H by the implicit double-shift QR iteration (Golub &
 //      Van Loan, Algorithms 7.5.1 and 7.5.2), eigenvalues only, run by one
 //      warp on H packed by columns in shared memory (francis_kernel).
@@ -12,8 +12,11 @@
 //      partial pivoting between adjacent rows (one CTA per eigenvalue), then
 //      back-transformed with the Householder reflectors of step 1.
 #include <cmath>
+#include <cooperative_groups.h>
 
 #include "common.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace sk {
 
@@ -31,66 +34,83 @@ __device__ __forceinline__ double block_sum_d(double v, double* sh) {
 }
 
 // ---- 1. Hessenberg reduction (in place, global memory, ld = n) ---------------------
+// On an 8-CTA cluster: the FP64 updates of a step are spread over 8 SMs (one
+// SM's FP64 rate bounded a one-CTA reduction at ~11 ms for n = 200).  Step
+// k: every CTA forms the reflector of column k itself (same loads, same
+// fixed-order sum, so the same bits everywhere); CTA q owns the columns j with
+// j % 8 == q and applies the left update to them alone; for the right update
+// each CTA sums H[:, j] v_j over its columns, the eight partial vectors are
+// read through distributed shared memory and added in rank order, and each
+// CTA updates its columns; a second cluster barrier publishes column k + 1.
+static constexpr int kHessCluster = 8;
+
 __global__ void __launch_bounds__(kEigThreads)
-hessenberg_kernel(double* __restrict__ H, int n, double* __restrict__ tau) {
+hessenberg_cluster_kernel(double* __restrict__ H, int n, double* __restrict__ tau) {
+  cg::cluster_group cluster = cg::this_cluster();
+  const int q = (int)cluster.block_rank();
   __shared__ double sh[32];
-  __shared__ double w[kEigMaxN];
-  __shared__ double s_sc[2];
+  __shared__ double v[kEigMaxN];
+  __shared__ double wpart[kEigMaxN];  // this CTA's sum of H[:, j] v_j over its columns
+  __shared__ double s_sc[3];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  cluster.sync();  // every CTA of the cluster has started before the first remote read
   for (int k = 0; k + 2 < n; ++k) {
-    // reflector for x = H[k+1:n, k]
+    // reflector for x = H[k+1:n, k] (v in shared memory, v_i for i >= k+1)
     double part = 0;
-    for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) part += H[i + (int64_t)k * n] * H[i + (int64_t)k * n];
+    for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) {
+      const double x = __ldcg(H + i + (int64_t)k * n);
+      v[i] = x;
+      part += x * x;
+    }
     const double nrm2 = block_sum_d(part, sh);
-    // the reflector's scalars once (FP64 sqrt and divide are slow here), broadcast
     if (threadIdx.x == 0) {
-      const double x0 = H[k + 1 + (int64_t)k * n];
+      const double x0 = v[k + 1];
       const double nrm = sqrt(nrm2);
       const double alpha = x0 >= 0 ? -nrm : nrm;
       const double v0 = x0 - alpha;
       const double vtv = nrm2 - x0 * x0 + v0 * v0;
       s_sc[0] = vtv > 0 ? 2.0 / vtv : 0.0;
       s_sc[1] = alpha;
-      H[k + 1 + (int64_t)k * n] = v0;  // v stored in H[k+1:, k]; H[k+1,k] := alpha below
-      tau[k] = s_sc[0];
+      s_sc[2] = v0;
+      v[k + 1] = v0;
     }
     __syncthreads();
-    const double t = s_sc[0], alpha = s_sc[1];
-    const double* v = H + (int64_t)k * n;  // v[i] for i >= k+1
-    // left: H[k+1:, k+1:] -= t v (v^T H[k+1:, k+1:]); one warp per column
-    {
-      const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-      for (int j = k + 1 + wid; j < n; j += nw) {
-        double a = 0;
-        for (int i = k + 1 + lane; i < n; i += 32) a += v[i] * H[i + (int64_t)j * n];
-        a = warp_sum(a);
-        if (lane == 0) w[j] = a * t;
-      }
+    const double t = s_sc[0];
+    // this CTA's first column right of k
+    const int j0 = k + 1 + ((q - (k + 1)) % kHessCluster + kHessCluster) % kHessCluster;
+    // left: H[k+1:, j] -= t v (v^T H[k+1:, j]) for this CTA's columns, a warp per column
+    for (int j = j0 + wid * kHessCluster; j < n; j += nw * kHessCluster) {
+      double* col = H + (int64_t)j * n;
+      double a = 0;
+      for (int i = k + 1 + lane; i < n; i += 32) a += v[i] * col[i];
+      a = warp_sum(a) * t;
+      for (int i = k + 1 + lane; i < n; i += 32) col[i] -= v[i] * a;
     }
-    __syncthreads();
-    for (int q = threadIdx.x; q < (n - k - 1) * (n - k - 1); q += blockDim.x) {
-      const int j = k + 1 + q / (n - k - 1), i = k + 1 + q % (n - k - 1);
-      H[i + (int64_t)j * n] -= v[i] * w[j];
-    }
-    __syncthreads();
-    // right: H[:, k+1:] -= t (H[:, k+1:] v) v^T
+    __syncthreads();  // this CTA's left-updated columns, before its own sums read them
+    // right: w = t H[:, k+1:] v; this CTA's part over its columns, every row
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
-      double a[4] = {0, 0, 0, 0};  // four independent chains (FP64 FMA latency ~64 cycles)
-      int j = k + 1;
-      for (; j + 3 < n; j += 4) {
+      double a[4] = {0, 0, 0, 0};  // four independent chains (FP64 FMA latency)
+      int u = 0;
+      for (int j = j0; j < n; j += kHessCluster, u = (u + 1) & 3) a[u] += H[i + (int64_t)j * n] * v[j];
+      wpart[i] = (a[0] + a[1]) + (a[2] + a[3]);
+    }
+    cluster.sync();  // every CTA's partial sums (and left updates) are complete
+    const double* wp[kHessCluster];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) a[u] += H[i + (int64_t)(j + u) * n] * v[j + u];
-      }
-      for (; j < n; ++j) a[0] += H[i + (int64_t)j * n] * v[j];
-      w[i] = ((a[0] + a[1]) + (a[2] + a[3])) * t;
+    for (int r = 0; r < kHessCluster; ++r) wp[r] = cluster.map_shared_rank(wpart, r);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      double a = 0;
+#pragma unroll
+      for (int r = 0; r < kHessCluster; ++r) a += wp[r][i];
+      const double wi = a * t;
+      for (int j = j0; j < n; j += kHessCluster) H[i + (int64_t)j * n] -= wi * v[j];
     }
-    __syncthreads();
-    for (int q = threadIdx.x; q < n * (n - k - 1); q += blockDim.x) {
-      const int j = k + 1 + q / n, i = q % n;
-      H[i + (int64_t)j * n] -= w[i] * v[j];
+    if (q == 0 && threadIdx.x == 0) {
+      H[k + 1 + (int64_t)k * n] = v[k + 1];  // v_0 (v kept in H[k+1:, k]); every CTA has read column k
+      tau[k] = t;
+      tau[n + k] = s_sc[1];  // subdiagonal entry H[k+1, k]
     }
-    __syncthreads();
-    if (threadIdx.x == 0) tau[n + k] = alpha;  // subdiagonal entry H[k+1, k]
-    __syncthreads();
+    cluster.sync();  // right updates done (column k + 1 among them); wpart is free again
   }
 }
 
@@ -548,8 +568,21 @@ invit_kernel(const double* __restrict__ Hg, const double* __restrict__ tau, int 
 sk_status enqueue_eig(double* M, int n, int nev, double* tau, double* wr, double* wi, int* sel, double* Wre,
                       double* Wim, double* Yre, double* Yim, int* status, cudaStream_t st) {
   if (n > kFrancisMaxN || n < 3) { set_error("eigensolver supports 3 <= d <= %d", kFrancisMaxN); return SK_EINVAL; }
-  hessenberg_kernel<<<1, kEigThreads, 0, st>>>(M, n, tau);
-  SK_CUDA(cudaGetLastError());
+  {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(kHessCluster);
+    cfg.blockDim = dim3(kEigThreads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = kHessCluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    SK_CUDA(cudaLaunchKernelEx(&cfg, hessenberg_cluster_kernel, M, n, tau));
+  }
   // one attribute value for every launch (graph capture keeps launch sizes)
   SK_CUDA(cudaFuncSetAttribute(francis_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)francis_smem_bytes(kFrancisMaxN) + 16));
