@@ -32,7 +32,7 @@ METRIC = "sGMRES solves/s to 1e-6 rel. residual (chosen vs plain form); sketch G
 # DRAM bytes (read + write) of one Arnoldi step (its three launches), from
 # the ncu capture summarised in profiles/basis_dram_sgmres_scale_f32.md;
 # None for forms not captured (and to be reset whenever those kernels change).
-BASIS_TRAFFIC = {("f32", False): 25287936}
+BASIS_TRAFFIC = {("f32", False): 25295872}
 
 
 def _peaks():
