@@ -527,18 +527,20 @@ def run_ours(args):
         "gpu_launches": int(sum(i["launches"] for i in infos)),
     }
     if not args.no_extras:
-        # the other forms of the same workload: SRHT sketch (FP32 basis), BF16
-        # basis, and iterative sGMRES (§5.2: chunks of 64 columns, early stop)
+        # the other forms of the same workload, each through its own reusable
+        # solver like the headline: SRHT sketch (FP32 basis), BF16 basis, and
+        # iterative sGMRES (§5.2: chunks of 64 columns, early stop)
         forms = {}
         for fname, fkw in (("srht_f32", dict(kw, basis=torch.float32, sketch="srht")),
                            ("bf16", dict(kw, basis=torch.bfloat16, sketch="sparse", maxit=400)),
                            ("iterative_f32", dict(kw, basis=torch.float32, sketch="sparse", iter_chunk=64))):
+            fplan = skg.SgmresPlan(A, W["d"], W["k"], W["s"], **fkw)
             x.zero_()
-            skg.sgmres_solve(A, b, W["d"], W["k"], W["s"], W["tol"], x0=x, **fkw)
+            fplan.solve(b, W["tol"], x0=x)
             barrier()
             e0.record(stream)
             x.zero_()
-            _, finfo = skg.sgmres_solve(A, b, W["d"], W["k"], W["s"], W["tol"], x0=x, **fkw)
+            _, finfo = fplan.solve(b, W["tol"], x0=x)
             e1.record(stream)
             barrier()
             fms = e0.elapsed_time(e1)
