@@ -76,6 +76,21 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
     assert capsys.readouterr().out == ""
 
 
+def test_gpu_count_must_match_the_launched_ranks(monkeypatch, capsys):
+    # `bench.py --gpus 2` started as one process (not through torch.distributed.run)
+    # refuses to run rather than report one GPU's rate as two GPUs'; the check
+    # comes before any device work, so it runs on the CPU
+    sys.path.insert(0, ROOT)
+    import bench
+    monkeypatch.setenv("RANK", "0")
+    monkeypatch.setenv("WORLD_SIZE", "1")
+    monkeypatch.setenv("LOCAL_RANK", "0")
+    args = bench.build_parser().parse_args(["--gpus", "2", "--steps", "1", "--warmup", "0"])
+    assert bench.run_ours(args) == 2
+    err = capsys.readouterr().err
+    assert "--gpus 2" in err and "torch.distributed.run" in err
+
+
 def test_reference_arm_json_line_contract():
     # the reference arm (the FP64 oracle on host cores) runs without a GPU:
     # one JSON line with the contract's keys, its own cpu_baseline and an e2e
