@@ -582,7 +582,9 @@ def run_case(args):
       sketch  a reusable sparse-sign plan applied twice to a --n x --cols
               FP32 block (s = 600, zeta = 12);
       srr     two sketched Rayleigh-Ritz calls (Algorithm 2) on the 512^2
-              eig workload, FP64 basis (d = 200, k = 4, s = 400)."""
+              eig workload, FP64 basis (d = 200, k = 4, s = 400);
+      batched a grouped batched solve of the batched workload's first 64
+              systems (one right-hand side each, at most 3 cycles)."""
     import torch
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
@@ -595,6 +597,20 @@ def run_case(args):
             x, info = skg.sgmres_solve(A, b, W["d"], W["k"], W["s"], 1e-300, maxit=1, **kw)
         torch.cuda.synchronize()
         print("case cycle ms %.3f launches %d" % (info["ms"][5], info["launches"]))
+    elif args.case == "batched":
+        import synth
+        W = synth.WORKLOADS["batched"]
+        sides, pes = synth.batch_systems(W["seed"], W["nsys"])
+        ops, bs = [], []
+        for i in range(64):
+            N = int(sides[i])
+            ops.append(skg.Op.stencil5(N, N, synth.conv_diff_coef(N, pes[i])))
+            g = torch.Generator(device=dev).manual_seed(synth.batch_rhs_seed(i, 0))
+            bs.append([torch.randn(N * N, generator=g, dtype=torch.float64, device=dev)])
+        xs, stat, info = skg.sgmres_solve_batched(ops, bs, W["d"], W["k"], W["s"], W["tol"], zeta=W["zeta"],
+                                                  basis=torch.float32, maxit=3, batch_mode="grouped")
+        torch.cuda.synchronize()
+        print("case batched launches %d wall ms %.1f" % (info["launches"], info["ms"][5]))
     elif args.case == "srr":
         import synth
         W = synth.WORKLOADS["eig"]
@@ -633,7 +649,7 @@ def build_parser():
                     help="run each cycle's phases one after another (no sketch/QR overlap with the basis)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the sketch, sRR, batched and Laplacian measurements")
-    ap.add_argument("--case", choices=["cycle", "sketch", "srr"],
+    ap.add_argument("--case", choices=["cycle", "sketch", "srr", "batched"],
                     help="run one small piece of the path for a profiler capture and exit")
     ap.add_argument("--n", type=int, default=1 << 18, help="rows of the --case sketch block")
     ap.add_argument("--cols", type=int, default=301, help="columns of the --case sketch block")
